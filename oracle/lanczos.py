@@ -1,0 +1,462 @@
+"""CPU oracle for the randomized small-block Lanczos null-space method.
+
+TEST INFRASTRUCTURE ONLY.  This module is the plain, slow, single-threaded FP64
+restatement of the method against which the CUDA library is checked.  Only
+tests/, the smoke check and the bench's CPU-baseline / reference leg may import
+it; the product path never does.  It shares no code with the CUDA library.
+
+It follows Kressner & Shao, "On a randomized small-block Lanczos method for
+large-scale null space computations":
+  * Eq. (defB) and Alg. 1 line 1: B = A^T A + eps*D (mode "normal"), or
+    B = A + eps*D for a symmetric positive semi-definite A (mode "spd", Sec. 5.1);
+    D diagonal with i.i.d. U[0,1] entries; B is only applied, Bx = A^T(Ax) + eps*(Dx).
+  * Alg. 1 line 2 / Alg. 2 lines 2, 4: Gaussian start block Omega, Q_1 = orth(Omega).
+  * Alg. 2 lines 6-8 (first step of a cycle, full projection against Z_{l0+1})
+    and lines 9-12 (three-term block recurrence, QR, partial reorthogonalization).
+  * Sec. 4.2: the W (omega) recurrence bounding ||Q_k^T Q_{l+1}||, with
+    u_d = d sqrt(n) u ||B|| (Eq. defmprd) and threshold u_RO = sqrt(u).
+  * Sec. 4.1 and Alg. 2 lines 13-17: thick restart keeping the smallest Ritz
+    pairs; T has the arrow + block-tridiagonal form of Eq. (defT).
+  * Alg. 2 line 14 and Remark cormain: Ritz values below 3*eps count as null.
+  * Sec. 4.3: stop when no Ritz value converged within s matvecs, s estimated
+    from the observed convergence speed (matvecs per d newly converged values).
+  * Remark after Alg. 1: an extraction step without the perturbation; here a
+    final FP64 projection of every basis vector onto null(A) by CG (CGLS in the
+    normal mode) followed by a Rayleigh-Ritz step on (AX)^T (AX).
+
+Readings of points the paper leaves open (each is also listed in the design doc):
+  R1  the recurrence subtracts Q_{l-1} Gamma_{l-1}^T (Eq. laniterfp), not Gamma_{l-1};
+  R2  W is strictly upper triangular: w_{i,j} = 0 whenever i >= j, and the three
+      cases of Sec. 4.2 fill entries 1..l of column l+1;
+  R3  in case 1 the coefficients are w_{k,l} (||Theta_k|| + ||Xi_l||) and
+      w_{l0+1,l} ||F_k|| (the derivation, Sec. 4.2, uses ||Q_k^T Q_l|| and the
+      block Q_{l0+1} that carries the restart coupling F);
+  R4  ||Gamma_l^{-1}|| = 1 / sigma_min(Gamma_l);
+  R5  converged Ritz pairs (Ritz value < 3 eps and Ritz residual
+      ||Gamma_l V_Z(last block, i)|| <= tol * ||B||) are locked: moved to a set X
+      that the active basis is kept orthogonal to.  Each locked vector k carries a
+      W row with case 1 using ||Theta_k|| = theta_k and, since its residual
+      direction is no longer part of the basis, the full residual rho_k in place
+      of w_{l0+1,l} ||F_k||;
+  R6  reorthogonalization (CGS2) is against [X, Z_{l-1}]; the X part is done
+      only when an X row exceeds u_RO, the Z part only when a Z row does, and only
+      the rows that were reorthogonalized are reset to u_d;
+  R7  retained count l0 d = d * floor((N_unlocked + dimK) / (2d)) clamped to
+      [d, dimK - 2d] (Alg. 2 line 14 counted in vectors);
+  R8  after restart F = R Gamma_l V_Z(last block, kept) where R is the factor of the
+      re-orthogonalization QR of Q_{l+1} (Alg. 2 line 17, printed index garbled);
+  R9  ||B|| in u_d is the bound ||A||_1 ||A||_inf + eps (normal) or ||A||_inf + eps (spd);
+  R10 u = 2^-52 (the paper quotes 2.22e-16);
+  R11 stopping: s = (stamp_last - stamp_first) / max(1, (locked - first batch)/d),
+      floored at dimK; stop when no Ritz value below 3 eps is left unlocked, no
+      lock happened for more than stop_factor * s matvecs and the last cycle
+      locked nothing;
+  R12 breakdown (sigma_min(Gamma) <= 100 u_d): the block is replaced by a fresh
+      Gaussian block (Philox stream 2+k) orthogonalized against [X, Z], and
+      Gamma is set to zero.
+"""
+
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from .philox import perturbation_diagonal, start_block, gaussian
+
+U_FP64 = 2.0**-52
+
+
+# ----------------------------------------------------------------------------
+# small dense helpers (library primitives: QR, SVD, symmetric eigensolver)
+# ----------------------------------------------------------------------------
+
+def qr_pos(Y: np.ndarray):
+    """Thin QR with a non-negative diagonal in R (so the factorization is unique)."""
+    Q, R = np.linalg.qr(Y)
+    s = np.sign(np.diag(R))
+    s[s == 0] = 1.0
+    return Q * s, R * s[:, None]
+
+
+def smin(G: np.ndarray) -> float:
+    return float(np.linalg.svd(G, compute_uv=False)[-1])
+
+
+def norm2(G: np.ndarray) -> float:
+    if G.size == 0:
+        return 0.0
+    return float(np.linalg.svd(G, compute_uv=False)[0])
+
+
+# ----------------------------------------------------------------------------
+# the operator B (Eq. defB, Sec. 5.1)
+# ----------------------------------------------------------------------------
+
+class Operator:
+    def __init__(self, A: sp.csr_matrix, mode: str, eps: float, Dvec: np.ndarray):
+        assert mode in ("normal", "spd")
+        self.A = sp.csr_matrix(A, dtype=np.float64)
+        self.At = self.A.T.tocsr() if mode == "normal" else None
+        self.mode = mode
+        self.eps = float(eps)
+        self.D = np.asarray(Dvec, dtype=np.float64)
+        self.n = self.A.shape[1]
+
+    def apply(self, X: np.ndarray) -> np.ndarray:
+        """B X = A^T (A X) + eps D X  (or A X + eps D X in spd mode)."""
+        if self.mode == "normal":
+            Y = self.At @ (self.A @ X)
+        else:
+            Y = self.A @ X
+        return Y + self.eps * self.D[:, None] * X
+
+    def apply_A(self, X):
+        return self.A @ X
+
+    def norm_bound(self) -> float:
+        """Reading R9: cheap rigorous upper bound on ||B||_2."""
+        absA = abs(self.A)
+        ninf = float(absA.sum(axis=1).max()) if self.A.nnz else 0.0
+        if self.mode == "normal":
+            n1 = float(absA.sum(axis=0).max()) if self.A.nnz else 0.0
+            return n1 * ninf + self.eps
+        return ninf + self.eps
+
+
+def norm2_A(A: sp.csr_matrix, mode: str) -> float:
+    """||A||_2 from a library Lanczos (ARPACK) call."""
+    A = sp.csr_matrix(A, dtype=np.float64)
+    if A.nnz == 0:
+        return 0.0
+    if min(A.shape) <= 64:
+        return float(np.linalg.norm(A.toarray(), 2))
+    if mode == "spd":
+        return float(abs(spla.eigsh(A, k=1, which="LA", return_eigenvectors=False, tol=1e-8)[0]))
+    At = A.T.tocsr()
+    op = spla.LinearOperator((A.shape[1], A.shape[1]), matvec=lambda x: At @ (A @ x), dtype=np.float64)
+    return float(np.sqrt(spla.eigsh(op, k=1, which="LA", return_eigenvectors=False, tol=1e-8)[0]))
+
+
+# ----------------------------------------------------------------------------
+# Alg. 2 with locking
+# ----------------------------------------------------------------------------
+
+class Result(dict):
+    __getattr__ = dict.__getitem__
+
+
+def lanczos_nullspace(A, mode: str, d: int, restart_len: int, tol: float = 1e-10,
+                      eps: float = 1e-3, seed: int = 0, max_matvec: int = 200000,
+                      stop_factor: float = 2.0, reorth: str = "partial",
+                      restart: bool = True, refine: bool = True, refine_tol: float = 1e-10,
+                      refine_maxit: int = 500, final_rr: bool = True,
+                      u: float = U_FP64, D: np.ndarray | None = None,
+                      Omega: np.ndarray | None = None, record: bool = False,
+                      probe=None) -> Result:
+    """Null space of A by Alg. 2 (restarted, partially reorthogonalized small-block Lanczos).
+
+    reorth: "partial" (Sec. 4.2), "full" (every new block projected against the whole
+    basis, used for Alg. 1) or "none" (used to test the W bounds).
+    restart=False runs Alg. 1: one cycle of restart_len/d block steps, no locking; the
+    caller gets T, its eigenpairs and the basis.
+    probe(j, Z, X, col, colX, d) is called after each new W column (before any
+    reorthogonalization) so tests can compare the bounds with the true inner products;
+    record=True also keeps the quantities of the last cycle before each restart.
+    """
+    A = sp.csr_matrix(A, dtype=np.float64)
+    n = A.shape[1]
+    R = int(restart_len)
+    if d < 1 or R % d or R < 3 * d:
+        raise ValueError("restart_len must be a multiple of d and at least 3d")
+    if D is None:
+        D = perturbation_diagonal(seed, n)
+    op = Operator(A, mode, eps, D)
+    normB = op.norm_bound()
+    u_d = d * np.sqrt(n) * u * normB  # Eq. (defmprd)
+    u_ro = np.sqrt(u)  # Sec. 4.2
+    bd_tol = 100.0 * u_d  # reading R12
+    nb = R // d  # blocks of the basis before restart
+
+    X = np.zeros((n, 0))  # locked vectors
+    x_theta = np.zeros(0)
+    x_rho = np.zeros(0)
+    Z = np.zeros((n, R + d))  # basis blocks Q_1..Q_{nb+1}; block b = columns b*d:(b+1)*d
+    Xi = [None] * nb
+    Gam = [None] * nb
+    st = dict(matvecs=0, restarts=0, reorth_X=0, reorth_Z=0, breakdowns=0, lock_events=[],
+              theta_max=0.0, history=[])
+
+    def apply_B(Q):
+        st["matvecs"] += Q.shape[1]
+        return op.apply(Q)
+
+    def project(W, parts):
+        """CGS2 of W against the column sets in parts (classical Gram-Schmidt, twice)."""
+        for _ in range(2):
+            coefs = [V.T @ W for V in parts if V.shape[1]]
+            for V, C in zip([V for V in parts if V.shape[1]], coefs):
+                W = W - V @ C
+        return W
+
+    def qr_or_replace(Y, parts):
+        """QR of Y; on breakdown replace Y by a fresh random block (reading R12)."""
+        Q, Rf = qr_pos(Y)
+        if smin(Rf) > bd_tol:
+            return Q, Rf
+        st["breakdowns"] += 1
+        Yr = gaussian(seed, 2 + st["breakdowns"] - 1, n * d).reshape(n, d)
+        Yr = project(Yr, parts)
+        Q, _ = qr_pos(Yr)
+        return Q, np.zeros((d, d))
+
+    # Alg. 2 line 4
+    Om = start_block(seed, n, d) if Omega is None else np.asarray(Omega, dtype=np.float64)
+    Z[:, 0:d], _ = qr_pos(Om)
+
+    k0 = 0  # retained Ritz vectors (multiple of d)
+    Theta = np.zeros(0)
+    F = np.zeros((d, 0))
+    converged = False
+    last_cycle = None
+
+    while True:
+        r0 = k0 // d
+        blk = lambda b: Z[:, b * d:(b + 1) * d]  # noqa: E731
+        # ---- Alg. 2 lines 6-8: first step of the cycle -------------------------
+        Qp = apply_B(blk(r0))
+        Xi[r0] = 0.5 * ((blk(r0).T @ Qp) + (blk(r0).T @ Qp).T)
+        Qp = project(Qp, [X, Z[:, :(r0 + 1) * d]])
+        Qn, Gam[r0] = qr_or_replace(Qp, [X, Z[:, :(r0 + 1) * d]])
+        Z[:, (r0 + 1) * d:(r0 + 2) * d] = Qn
+        # W: columns r0 and r0+1 start at u_d (Sec. 4.2, last paragraph)
+        W = np.zeros((nb + 1, nb + 1))
+        WX = np.zeros((X.shape[1], nb + 1))
+        W[:r0, r0] = u_d
+        W[:r0 + 1, r0 + 1] = u_d
+        WX[:, r0] = u_d
+        WX[:, r0 + 1] = u_d
+        Wrec = [] if record else None
+        # ---- Alg. 2 lines 9-12: inner loop ------------------------------------
+        for j in range(r0 + 1, nb):
+            Qp = apply_B(blk(j)) - blk(j - 1) @ Gam[j - 1].T  # reading R1
+            Xi_raw = blk(j).T @ Qp
+            Xi[j] = 0.5 * (Xi_raw + Xi_raw.T)
+            Qn, Gam[j] = qr_or_replace(Qp - blk(j) @ Xi[j], [X, Z[:, :(j + 1) * d]])
+            Z[:, (j + 1) * d:(j + 2) * d] = Qn
+            if reorth == "full":
+                Z[:, (j + 1) * d:(j + 2) * d], _ = qr_pos(project(Qn, [X, Z[:, :(j + 1) * d]]))
+                continue
+            if reorth == "none" and not record:
+                continue
+            # W recurrence, column j+1 (Sec. 4.2 cases 1-3 with readings R2-R5)
+            bd_hit = not Gam[j].any()
+            g = np.inf if bd_hit else 1.0 / smin(Gam[j])
+            nXi_j = norm2(Xi[j])
+            nG_jm1 = norm2(Gam[j - 1])
+            w = lambda a, c: W[a, c] if a < c else 0.0  # noqa: E731  (reading R2)
+            newcol = np.zeros(nb + 1)
+            for b in range(0, j + 1):
+                if b < r0:  # case 1: retained Ritz block
+                    th = float(np.max(np.abs(Theta[b * d:(b + 1) * d])))
+                    nF = norm2(F[:, b * d:(b + 1) * d])
+                    val = w(b, j) * (th + nXi_j) + w(r0, j) * nF + w(b, j - 1) * nG_jm1 + 2 * u_d
+                elif b == r0:  # case 2
+                    s = sum(w(i, j) * norm2(F[:, i * d:(i + 1) * d]) for i in range(r0))
+                    val = (w(b, j) * (norm2(Xi[b]) + nXi_j) + s + w(b + 1, j) * norm2(Gam[b])
+                           + w(b, j - 1) * nG_jm1 + 2 * u_d)
+                else:  # case 3
+                    val = (w(b, j) * (norm2(Xi[b]) + nXi_j) + w(b + 1, j) * norm2(Gam[b])
+                           + w(b - 1, j) * norm2(Gam[b - 1]) + w(b, j - 1) * nG_jm1 + 2 * u_d)
+                newcol[b] = g * val
+            newX = g * (WX[:, j] * (x_theta + nXi_j) + x_rho + WX[:, j - 1] * nG_jm1 + 2 * u_d)
+            if bd_hit:  # the replacement block was fully orthogonalized
+                newcol[:j + 1] = u_d
+                newX[:] = u_d
+            W[:, j + 1] = newcol
+            WX[:, j + 1] = newX
+            if probe is not None:
+                probe(j, Z, X, newcol, newX, d)
+            if record:
+                Wrec.append((j + 1, newcol.copy(), newX.copy()))
+            if reorth == "none":
+                continue
+            trig_Z = bool(np.any(newcol[:j + 1] > u_ro))
+            trig_X = bool(np.any(newX > u_ro))
+            if trig_Z or trig_X:
+                partsj = ([X] if trig_X else []) + ([Z[:, :j * d]] if trig_Z else [])
+                Z[:, j * d:(j + 1) * d], _ = qr_pos(project(blk(j), partsj))
+                partsj1 = ([X] if trig_X else []) + ([Z[:, :(j + 1) * d]] if trig_Z else [])
+                Z[:, (j + 1) * d:(j + 2) * d], _ = qr_pos(project(blk(j + 1), partsj1))
+                if trig_Z:
+                    st["reorth_Z"] += 1
+                    W[:j, j] = u_d
+                    W[:j + 1, j + 1] = u_d
+                if trig_X:
+                    st["reorth_X"] += 1
+                    WX[:, j] = u_d
+                    WX[:, j + 1] = u_d
+        # ---- Alg. 2 line 13: T of Eq. (defT) and its eigendecomposition -------
+        T = np.zeros((R, R))
+        T[:k0, :k0] = np.diag(Theta)
+        T[k0:k0 + d, :k0] = F
+        T[:k0, k0:k0 + d] = F.T
+        for b in range(r0, nb):
+            T[b * d:(b + 1) * d, b * d:(b + 1) * d] = Xi[b]
+            if b + 1 < nb:
+                T[(b + 1) * d:(b + 2) * d, b * d:(b + 1) * d] = Gam[b]
+                T[b * d:(b + 1) * d, (b + 1) * d:(b + 2) * d] = Gam[b].T
+        theta, VZ = np.linalg.eigh(T)  # ascending
+        resid = np.linalg.norm(Gam[nb - 1] @ VZ[R - d:R, :], axis=0)
+        st["theta_max"] = max(st["theta_max"], float(theta[-1]))
+        small = theta < 3 * eps
+        if record and restart:
+            st.setdefault("cycles", []).append(dict(T=T, Z=Z[:, :R].copy(), Qnext=Z[:, R:R + d].copy(),
+                                                    Gamma_last=Gam[nb - 1].copy(), X=X.copy(),
+                                                    x_rho=x_rho.copy(), k0=k0))
+        if not restart:
+            last_cycle = dict(T=T, theta=theta, VZ=VZ, resid=resid, Z=Z[:, :R].copy(),
+                              Qnext=Z[:, R:R + d].copy(), Gamma_last=Gam[nb - 1].copy(), W=W, WX=WX,
+                              Wrec=Wrec)
+            break
+        st["restarts"] += 1
+        # ---- locking (reading R5) ---------------------------------------------
+        cand = np.nonzero(small & (resid <= tol * normB))[0]
+        ghosts = np.zeros(0, dtype=np.int64)
+        nlock = 0
+        if cand.size:
+            Xc = Z[:, :R] @ VZ[:, cand]
+            P = project(Xc, [X])
+            good = np.linalg.norm(P, axis=0) >= 0.5 * np.linalg.norm(Xc, axis=0)
+            ghosts = cand[~good]
+            if good.any():
+                Xn, _ = qr_pos(P[:, good])
+                X = np.concatenate([X, Xn], axis=1)
+                x_theta = np.concatenate([x_theta, theta[cand[good]]])
+                x_rho = np.concatenate([x_rho, resid[cand[good]]])
+                nlock = int(good.sum())
+                st["lock_events"].append((st["matvecs"], nlock))
+            cand = cand[good]
+        taken = np.zeros(R, dtype=bool)
+        taken[cand] = True
+        taken[ghosts] = True
+        n_unl = int(small.sum()) - int(taken[small].sum())
+        # ---- Alg. 2 lines 14-17: thick restart ---------------------------------
+        avail = np.nonzero(~taken)[0]
+        k0 = d * ((n_unl + R) // (2 * d))
+        k0 = min(max(k0, d), R - 2 * d, d * (avail.size // d))
+        keep = avail[:k0]
+        Znew = Z[:, :R] @ VZ[:, keep]
+        q = project(Z[:, R:R + d], [X, Znew])
+        Qr, Rr = qr_pos(q)
+        if smin(Rr) <= bd_tol:
+            Qr, Rr = qr_or_replace(q, [X, Znew])
+        F = Rr @ Gam[nb - 1] @ VZ[R - d:R, keep]  # reading R8
+        Theta = theta[keep].copy()
+        Z[:, :k0] = Znew
+        Z[:, k0:k0 + d] = Qr
+        Z[:, k0 + d:] = 0.0
+        st["history"].append(dict(matvecs=st["matvecs"], locked=X.shape[1], n_small=int(small.sum()),
+                                  n_unlocked=n_unl, k0=k0, theta0=float(theta[0])))
+        # ---- termination (Sec. 4.3, reading R11) --------------------------------
+        ev = st["lock_events"]
+        if len(ev) >= 2:
+            later = sum(k for _, k in ev[1:])
+            s = (ev[-1][0] - ev[0][0]) / max(1.0, later / d)
+        else:
+            s = float(R)
+        s = max(s, float(R))
+        since = st["matvecs"] - (ev[-1][0] if ev else 0)
+        if n_unl == 0 and nlock == 0 and since > stop_factor * s:
+            converged = True
+            break
+        if st["matvecs"] >= max_matvec:
+            break
+
+    res = Result(stats=st, normB=normB, u_d=u_d, u_ro=u_ro, D=D, eps=eps)
+    if not restart:
+        res.update(last_cycle)
+        return res
+    res["converged"] = converged
+    res["X_lanczos"] = X.copy()
+    res["x_theta"] = x_theta
+    res["x_rho"] = x_rho
+    if refine and X.shape[1]:
+        normA = norm2_A(A, mode)
+        Xr, info = refine_null(A, mode, X, refine_tol * normA, refine_maxit)
+        Xr, _ = qr_pos(Xr)
+        if final_rr:  # Rayleigh-Ritz without the perturbation (Remark after Alg. 1)
+            AX = A @ Xr
+            G = Xr.T @ AX if mode == "spd" else AX.T @ AX
+            _, U = np.linalg.eigh(0.5 * (G + G.T))
+            Xr = Xr @ U
+        res["X"] = Xr
+        res["refine"] = info
+        res["normA"] = normA
+    else:
+        res["X"] = X
+    res["N"] = X.shape[1]
+    return res
+
+
+# ----------------------------------------------------------------------------
+# FP64 refinement (projection of every locked vector onto null(A))
+# ----------------------------------------------------------------------------
+
+def refine_null(A, mode: str, X: np.ndarray, abs_tol: float, maxit: int = 500):
+    """x <- x - delta with A delta = A x (CG, spd) or min ||A delta - A x|| (CGLS, normal).
+
+    The right-hand side lies in range(A) (range(A^T A) for CGLS), so x - delta tends
+    to the orthogonal projection of x onto null(A).  Columns are independent; each
+    stops once its residual ||A (x - delta)|| <= abs_tol.
+    """
+    A = sp.csr_matrix(A, dtype=np.float64)
+    At = A.T.tocsr()
+    X = np.array(X, dtype=np.float64, copy=True)
+    k = X.shape[1]
+    delta = np.zeros_like(X)
+    active = np.ones(k, dtype=bool)
+    iters = np.zeros(k, dtype=np.int64)
+    if mode == "spd":
+        r = A @ X
+        p = r.copy()
+        rr = np.einsum("ij,ij->j", r, r)
+        for it in range(maxit):
+            active &= np.sqrt(rr) > abs_tol
+            if not active.any():
+                break
+            Ap = A @ p
+            pAp = np.einsum("ij,ij->j", p, Ap)
+            alpha = np.where(active, rr / np.where(pAp > 0, pAp, 1.0), 0.0)
+            delta += p * alpha
+            r -= Ap * alpha
+            rr_new = np.einsum("ij,ij->j", r, r)
+            beta = np.where(active, rr_new / np.where(rr > 0, rr, 1.0), 0.0)
+            p = np.where(active, r + p * beta, p)
+            rr = np.where(active, rr_new, rr)
+            iters += active
+    else:
+        r = A @ X  # m x k residual A (x - delta)
+        s = At @ r
+        p = s.copy()
+        gam = np.einsum("ij,ij->j", s, s)
+        rn = np.sqrt(np.einsum("ij,ij->j", r, r))
+        for it in range(maxit):
+            active &= rn > abs_tol
+            if not active.any():
+                break
+            q = A @ p
+            qq = np.einsum("ij,ij->j", q, q)
+            alpha = np.where(active, gam / np.where(qq > 0, qq, 1.0), 0.0)
+            delta += p * alpha
+            r -= q * alpha
+            s = At @ r
+            gam_new = np.einsum("ij,ij->j", s, s)
+            beta = np.where(active, gam_new / np.where(gam > 0, gam, 1.0), 0.0)
+            p = np.where(active, s + p * beta, p)
+            gam = np.where(active, gam_new, gam)
+            rn = np.where(active, np.sqrt(np.einsum("ij,ij->j", r, r)), rn)
+            iters += active
+    Xr = X - delta
+    res = np.linalg.norm(A @ Xr, axis=0)
+    return Xr, dict(iters=iters, residual=res, failed=int((res > abs_tol * 1.01).sum()))
