@@ -1,0 +1,196 @@
+/*
+ * nullspace.h -- C ABI of the GB300 (sm_103a) null-space library.
+ *
+ * The library computes an orthonormal basis of the null space of a sparse
+ * matrix A (m x n, m >= n, CSR) with the randomized small-block Lanczos method
+ * of Kressner & Shao ("On a randomized small-block Lanczos method for
+ * large-scale null space computations"), Alg. 2 (restart + partial
+ * reorthogonalization), extended by locking of converged null vectors and a
+ * final FP64 projection onto null(A).
+ *
+ * Conventions shared by every call
+ *   - Every call returns ns_status; nothing aborts or exits.  CUDA failures map
+ *     to NS_ERR_CUDA and their text is kept for ns_last_error().
+ *   - Input arrays are borrowed for the duration of the call and copied; the
+ *     library never keeps a caller pointer.  Outputs go to caller-owned memory.
+ *   - Host pointers are plain C arrays.  "Device" pointers are CUDA global memory
+ *     of the current device.  Flags named *_on_device select which one is given.
+ *   - A handle is not thread-safe; distinct handles are independent.
+ *   - All GPU work of a handle runs on the stream given in ns_env (or the legacy
+ *     default stream).  Calls return after that work completed unless stated.
+ *   - The library needs a CUDA device of compute capability 10.3 (GB300); it has
+ *     no CPU fallback and returns NS_ERR_CUDA when no such device is present.
+ */
+#ifndef NULLSPACE_H
+#define NULLSPACE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  NS_OK = 0,
+  NS_ERR_INVALID_ARG = 1,   /* bad size, pointer or CSR structure; nothing changed */
+  NS_ERR_OOM = 2,           /* device allocation failed (allocator returned NULL)  */
+  NS_ERR_CUDA = 3,          /* a CUDA call failed; see ns_last_error()             */
+  NS_ERR_NOT_CONVERGED = 4, /* max_matvec reached; basis holds what was locked     */
+  NS_ERR_TIMEOUT = 5,       /* a bounded device wait gave up (no hang)             */
+  NS_ERR_STATE = 6,         /* call out of order (e.g. basis before solve)         */
+  NS_ERR_REFINE = 7         /* some column missed the refinement tolerance          */
+} ns_status;
+
+typedef enum {
+  NS_MODE_NORMAL = 0, /* B = A^T A + eps D              (Eq. defB)                   */
+  NS_MODE_SPD = 1     /* B = A + eps D, A symmetric PSD (Sec. 5.1, graph Laplacians) */
+} ns_mode;
+
+typedef enum {
+  NS_FP64 = 0,  /* everything in FP64                                               */
+  NS_MIXED = 1  /* A values, Lanczos basis, SpMM and projections in FP32; projected
+                   eigenproblem, W recurrence and final refinement in FP64          */
+} ns_precision;
+
+typedef enum {
+  NS_REORTH_PARTIAL = 0, /* W recurrence of Sec. 4.2 decides (default)              */
+  NS_REORTH_FULL = 1     /* project every new block against the whole basis         */
+} ns_reorth;
+
+/* Device memory and stream supplied by the caller (e.g. PyTorch's caching
+ * allocator and current stream).  alloc must return 256-byte aligned device
+ * memory or NULL; free receives the pointer and the size given to alloc.
+ * A NULL ns_env (or NULL alloc) makes the library use cudaMalloc/cudaFree. */
+typedef struct {
+  void* (*alloc)(size_t bytes, void* ctx);
+  void (*free)(void* ptr, size_t bytes, void* ctx);
+  void* ctx;
+  void* stream; /* cudaStream_t; NULL = legacy default stream */
+} ns_env;
+
+typedef struct {
+  double eps;          /* perturbation strength (Sec. 5.3: 1e-3)                       */
+  int precision;       /* ns_precision                                                */
+  int reorth;          /* ns_reorth                                                   */
+  int64_t max_matvec;  /* cap on B applications per column; <=0: min(100n+50R, 1e6) */
+  double stop_factor;  /* stop after stop_factor * s matvecs without a new lock       */
+  double lock_tol_mixed; /* lower bound of the lock tolerance on the mixed path         */
+  int refine;          /* 1: FP64 projection of the basis onto null(A) (default 1)     */
+  double refine_tol;   /* stop when ||A x|| <= refine_tol * ||A||_2 (default 1e-10)    */
+  int refine_maxit;    /* CG / CGLS iteration cap per column (default 500)             */
+  int refine_chunk;    /* columns refined together: 8, 16 or 32 (default 16)           */
+  int use_graphs;      /* 1: replay the Lanczos step as a CUDA graph (default 1)       */
+} ns_opts;
+
+typedef struct {
+  int64_t nullity;       /* N = number of locked (null) vectors                      */
+  int64_t matvecs;       /* B applications counted per column, as in Table tabCH     */
+  int64_t restarts;
+  int64_t reorth_X;      /* partial reorthogonalizations against the locked set     */
+  int64_t reorth_Z;      /* ... against the active basis                            */
+  int64_t breakdowns;
+  int64_t lock_events;
+  int64_t ghosts;        /* lock candidates rejected as copies of locked vectors    */
+  int64_t refine_iters_max;
+  int64_t kernel_launches; /* library kernels launched by the last ns_solve        */
+  double normB;          /* bound on ||B||_2 used in u_d                             */
+  double normA;          /* ||A||_2 estimate (largest Ritz value of the last T)      */
+  double u_d;            /* Eq. (defmprd)                                            */
+  double refine_resid_max; /* max_j ||A x_j||_2 / ||A||_2 after refinement           */
+  double t_lanczos_ms;   /* device time of the Lanczos phase                         */
+  double t_refine_ms;    /* device time of the refinement phase                      */
+  double t_total_ms;
+} ns_stats_t;
+
+typedef struct ns_handle ns_handle;
+
+/* Fill *o with the defaults listed in ns_opts. */
+void ns_default_opts(ns_opts* o);
+
+/* ns_create -- copy A (m x n CSR) to the device, build A^T (normal mode) by a
+ * stable counting sort, bound ||B|| and draw D (Alg. 2 line 1, Eq. defB).
+ *   rowptr  : m+1 int64, rowptr[0] = 0, non-decreasing, rowptr[m] = nnz
+ *   colind  : nnz int32 in [0, n)
+ *   vals    : nnz double, finite
+ *   inputs_on_device : 0 = the three arrays are host memory, 1 = device memory
+ *   seed    : Philox-4x32-10 key for D (stream 0) and the start block (stream 1)
+ *   mode    : ns_mode; NS_MODE_SPD requires m == n and a symmetric PSD A (not checked)
+ *   env     : allocator / stream, may be NULL; copied into the handle
+ * Errors: NS_ERR_INVALID_ARG for m < 0, n <= 0, m < n in normal mode is allowed
+ * but slow (Remark in Sec. 1.1), broken CSR structure (host inputs are fully
+ * checked; device inputs are checked on the device), NaN/Inf values. */
+ns_status ns_create(ns_handle** out, int64_t m, int64_t n, const int64_t* rowptr,
+                    const int32_t* colind, const double* vals, int inputs_on_device,
+                    uint64_t seed, int mode, const ns_env* env);
+
+/* ns_solve -- Alg. 2 with locking and refinement (Sec. 4).
+ *   d           : block size, 1 <= d <= 8
+ *   restart_len : maximal Krylov dimension dim K, multiple of d, >= 3d
+ *   tol         : lock a Ritz pair when its value is < 3 eps and its residual
+ *                 ||Gamma_l V_Z(last block, i)|| <= tol * ||B|| (Remark cormain)
+ *   opts        : NULL = defaults
+ * Returns NS_OK, NS_ERR_NOT_CONVERGED (max_matvec reached; the basis holds the
+ * vectors locked so far), NS_ERR_REFINE (a column missed refine_tol), or an error.
+ * May be called again on the same handle (new solve, same D and start seed). */
+ns_status ns_solve(ns_handle* h, int d, int restart_len, double tol, const ns_opts* opts);
+
+/* Number of null vectors found by the last ns_solve. NS_ERR_STATE before a solve. */
+ns_status ns_nullity(const ns_handle* h, int64_t* N);
+
+/* Copy the n x N basis (FP64, column-major, leading dimension ld >= n) to out. */
+ns_status ns_basis(const ns_handle* h, double* out, int64_t ld, int out_on_device);
+
+/* Counters and timings of the last ns_solve. */
+ns_status ns_stats(const ns_handle* h, ns_stats_t* s);
+
+/* Text of the last error on this handle ("" if none; static string for NULL). */
+const char* ns_last_error(const ns_handle* h);
+
+/* Release every device buffer of the handle. NULL is ignored. */
+void ns_destroy(ns_handle* h);
+
+/* ---------------------------------------------------------------------------
+ * Kernel-level entry points.  They expose single steps of the path on the
+ * matrix held by a handle, so that each can be checked on its own.
+ * -------------------------------------------------------------------------*/
+
+/* Copy A^T as built on the device (CSR: n+1 rowptr, nnz colind, nnz vals) to
+ * host arrays.  Entries of each row of A^T keep the order of the rows of A.
+ * NS_ERR_STATE in SPD mode (no transpose is built). */
+ns_status ns_get_transpose(const ns_handle* h, int64_t* rowptr, int32_t* colind, double* vals);
+
+/* Copy the diagonal D (n doubles, U[0,1), Philox stream 0) to host memory. */
+ns_status ns_get_perturbation(const ns_handle* h, double* D);
+
+/* Draw the n x d start block Omega (row-major, Philox stream 1, Box-Muller) into
+ * host memory, exactly as ns_solve draws it (Alg. 2 line 2). */
+ns_status ns_start_block(const ns_handle* h, int d, double* Omega);
+
+/* Y = B X (Eq. defB) for an n x d row-major block, 1 <= d <= 8.
+ *   X, Y       : n*d doubles, host or device memory (on_device)
+ *   eps        : perturbation strength
+ *   precision  : NS_FP64 or NS_MIXED (X rounded to FP32, FP32 arithmetic with
+ *                FP32 values of A; Y returned widened to FP64) */
+ns_status ns_apply_B(ns_handle* h, int d, const double* X, double* Y, double eps,
+                     int precision, int on_device);
+
+/* Eigen-decomposition of a symmetric k x k matrix (k <= 512) on the device with
+ * the library's one-CTA FP64 solver (Householder tridiagonalization + implicit QL),
+ * the solver used for the projected matrix T of Alg. 2 line 13.
+ *   T     : k*k doubles, column-major, host memory (only the lower triangle is read)
+ *   theta : k eigenvalues, ascending;  V : k*k column-major eigenvectors */
+ns_status ns_syev(int k, const double* T, double* theta, double* V);
+
+/* Block classical Gram-Schmidt, two passes (CGS2), as used for the partial
+ * reorthogonalization (Sec. 4.2): W <- (I - V V^T)^2 W for V (n x K, column-major)
+ * and W (n x w, row-major, 1 <= w <= 8).  Host arrays; FP64 (precision NS_FP64)
+ * or FP32 arithmetic (NS_MIXED).  C (K x w, row-major) receives the summed
+ * coefficients of both passes. */
+ns_status ns_project(int64_t n, int K, int w, const double* V, double* W, double* C, int precision);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NULLSPACE_H */

@@ -1,0 +1,770 @@
+// Dense kernels of the Lanczos loop: random streams, block QR (CholQR2),
+// CGS2 projections for partial reorthogonalization (Sec. 4.2), the W recurrence
+// (one block), thick-restart GEMM and bookkeeping (Sec. 4.1), CG refinement.
+#include "ns_common.cuh"
+#include "ns_kernels.cuh"
+
+namespace ns {
+
+static int stream_grid(int64_t n, int cap = 152 * 16) {
+  int g = ceil_div(n, kThreads);
+  if (g > cap) g = cap;
+  return g < 1 ? 1 : g;
+}
+static int persistent_rows(int64_t n) { return stream_grid(n, kMaxBlocks); }
+
+// ---------------------------------------------------------------------------
+// Philox streams: uniforms (stream 0: D) and Box-Muller normals (stream 1: Omega)
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_rng_uniform(uint64_t seed, uint32_t stream, T* out, int64_t count) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+    const U4 w = philox_at(seed, stream, (uint64_t)i);
+    out[i] = (T)u53(w.x, w.y);
+  }
+}
+
+template <typename T>
+__global__ void k_rng_gauss(uint64_t seed, uint32_t stream, T* out, int64_t count) {
+  const int64_t npairs = (count + 1) / 2;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npairs; p += (int64_t)gridDim.x * blockDim.x) {
+    const U4 w = philox_at(seed, stream, (uint64_t)p);
+    const uint64_t w0 = (uint64_t)w.x | ((uint64_t)w.y << 32);
+    const uint64_t w1 = (uint64_t)w.z | ((uint64_t)w.w << 32);
+    const double u1 = (double)((w0 >> 11) + 1) * 0x1.0p-53;
+    const double u2 = (double)(w1 >> 11) * 0x1.0p-53;
+    const double r = sqrt(-2.0 * log(u1));
+    double sn, cs;
+    sincospi(2.0 * u2, &sn, &cs);
+    out[2 * p] = (T)(r * cs);
+    if (2 * p + 1 < count) out[2 * p + 1] = (T)(r * sn);
+  }
+}
+
+template <typename T>
+void rng_uniform(uint64_t seed, uint32_t stream, T* out, int64_t count, cudaStream_t s) {
+  if (count > 0) k_rng_uniform<T><<<stream_grid(count), kThreads, 0, s>>>(seed, stream, out, count);
+}
+template <typename T>
+void rng_gauss(uint64_t seed, uint32_t stream, T* out, int64_t count, cudaStream_t s) {
+  if (count > 0) k_rng_gauss<T><<<stream_grid((count + 1) / 2), kThreads, 0, s>>>(seed, stream, out, count);
+}
+template void rng_uniform<double>(uint64_t, uint32_t, double*, int64_t, cudaStream_t);
+template void rng_uniform<float>(uint64_t, uint32_t, float*, int64_t, cudaStream_t);
+template void rng_gauss<double>(uint64_t, uint32_t, double*, int64_t, cudaStream_t);
+template void rng_gauss<float>(uint64_t, uint32_t, float*, int64_t, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// CholQR passes on n x D panels
+// ---------------------------------------------------------------------------
+// pivot test shared by the last blocks: Cholesky of G; on failure set flag bit 1
+__device__ inline void finish_chol(const double* G, int d, double* R, double* gdiag, unsigned* flags) {
+  double Rl[kMaxD * kMaxD];
+  const bool ok = chol_upper(G, Rl, d);
+  if (gdiag)
+    for (int i = 0; i < d; ++i) gdiag[i] = G[i * d + i];
+  if (!ok) {
+    for (int i = 0; i < d * d; ++i) Rl[i] = (i % (d + 1) == 0) ? 1.0 : 0.0;
+    if (flags) atomicOr(flags, 1u);
+  }
+  for (int i = 0; i < d * d; ++i) R[i] = Rl[i];
+}
+
+template <typename T, int D>
+__global__ void __launch_bounds__(kThreads) k_axpy_gram(T* __restrict__ qp, const T* __restrict__ x,
+                                                        const double* __restrict__ Xi, int64_t n, double* R1,
+                                                        unsigned* flags, Red red) {
+  constexpr int NP = D * D;
+  __shared__ double red_s[(kThreads / 32) * NP];
+  __shared__ double tot[NP];
+  __shared__ T xi_s[NP];
+  if (threadIdx.x < NP) xi_s[threadIdx.x] = (T)Xi[threadIdx.x];
+  __syncthreads();
+  T part[NP];
+#pragma unroll
+  for (int k = 0; k < NP; ++k) part[k] = T(0);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    T q[D], xr[D];
+    load_row<T, D>(qp + i * D, q);
+    load_row<T, D>(x + i * D, xr);
+#pragma unroll
+    for (int b = 0; b < D; ++b)
+#pragma unroll
+      for (int a = 0; a < D; ++a) q[b] = fma(-xr[a], xi_s[a * D + b], q[b]);
+    store_row<T, D>(qp + i * D, q);
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+      for (int b = 0; b < D; ++b) part[a * D + b] = fma(q[a], q[b], part[a * D + b]);
+  }
+  double pd[NP];
+#pragma unroll
+  for (int k = 0; k < NP; ++k) pd[k] = (double)part[k];
+  block_sum<NP>(pd, red_s, tot);
+  if (threadIdx.x < NP) red.part[(size_t)blockIdx.x * NP + threadIdx.x] = tot[threadIdx.x];
+  if (last_block_reduce(red.part, NP, red.ticket, tot, red_s))
+    if (threadIdx.x == 0) finish_chol(tot, D, R1, nullptr, flags);
+}
+
+template <typename T, int D>
+void axpy_gram(T* qp, const T* x, const double* Xi, int64_t n, double* R1, unsigned* flags, const Red& red,
+               cudaStream_t s) {
+  k_axpy_gram<T, D><<<persistent_rows(n), kThreads, 0, s>>>(qp, x, Xi, n, R1, flags, red);
+}
+
+// out = in R^{-1}; optional Gram of out with Cholesky into R2
+template <typename T, int D>
+__global__ void __launch_bounds__(kThreads) k_scale_gram(const T* in, int64_t ldin, T* out, int64_t ldout,
+                                                         const double* __restrict__ R, int64_t n, double* R2,
+                                                         unsigned* flags, Red red) {
+  constexpr int NP = D * D;
+  __shared__ double red_s[(kThreads / 32) * NP];
+  __shared__ double tot[NP];
+  __shared__ T ri_s[NP];
+  if (threadIdx.x == 0) {
+    double Rl[NP], Ri[NP];
+    for (int k = 0; k < NP; ++k) Rl[k] = R[k];
+    inv_upper(Rl, Ri, D);
+    for (int k = 0; k < NP; ++k) ri_s[k] = (T)Ri[k];
+  }
+  __syncthreads();
+  T part[NP];
+#pragma unroll
+  for (int k = 0; k < NP; ++k) part[k] = T(0);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    T a[D], o[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) a[k] = in[i * ldin + k];
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      T s = T(0);
+#pragma unroll
+      for (int k = 0; k <= c; ++k) s = fma(a[k], ri_s[k * D + c], s);
+      o[c] = s;
+    }
+#pragma unroll
+    for (int k = 0; k < D; ++k) out[i * ldout + k] = o[k];
+    if (R2) {
+#pragma unroll
+      for (int p = 0; p < D; ++p)
+#pragma unroll
+        for (int q = 0; q < D; ++q) part[p * D + q] = fma(o[p], o[q], part[p * D + q]);
+    }
+  }
+  if (!R2) return;  // uniform across the grid
+  double pd[NP];
+#pragma unroll
+  for (int k = 0; k < NP; ++k) pd[k] = (double)part[k];
+  block_sum<NP>(pd, red_s, tot);
+  if (threadIdx.x < NP) red.part[(size_t)blockIdx.x * NP + threadIdx.x] = tot[threadIdx.x];
+  if (last_block_reduce(red.part, NP, red.ticket, tot, red_s))
+    if (threadIdx.x == 0) finish_chol(tot, D, R2, nullptr, flags);
+}
+
+template <typename T, int D>
+void scale_gram(const T* in, int64_t ldin, T* out, int64_t ldout, const double* R, int64_t n, double* R2,
+                unsigned* flags, const Red& red, cudaStream_t s, int) {
+  k_scale_gram<T, D><<<persistent_rows(n), kThreads, 0, s>>>(in, ldin, out, ldout, R, n, R2, flags, red);
+}
+
+template <typename T, int D>
+__global__ void __launch_bounds__(kThreads) k_gram_chol(const T* W, int64_t ld, int64_t n, double* R,
+                                                        double* gdiag, unsigned* flags, Red red) {
+  constexpr int NP = D * D;
+  __shared__ double red_s[(kThreads / 32) * NP];
+  __shared__ double tot[NP];
+  T part[NP];
+#pragma unroll
+  for (int k = 0; k < NP; ++k) part[k] = T(0);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    T a[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) a[k] = W[i * ld + k];
+#pragma unroll
+    for (int p = 0; p < D; ++p)
+#pragma unroll
+      for (int q = 0; q < D; ++q) part[p * D + q] = fma(a[p], a[q], part[p * D + q]);
+  }
+  double pd[NP];
+#pragma unroll
+  for (int k = 0; k < NP; ++k) pd[k] = (double)part[k];
+  block_sum<NP>(pd, red_s, tot);
+  if (threadIdx.x < NP) red.part[(size_t)blockIdx.x * NP + threadIdx.x] = tot[threadIdx.x];
+  if (last_block_reduce(red.part, NP, red.ticket, tot, red_s))
+    if (threadIdx.x == 0) finish_chol(tot, D, R, gdiag, flags);
+}
+
+template <typename T, int D>
+void gram_chol(const T* W, int64_t ld, int, int64_t n, double* R, double* gdiag, unsigned* flags, const Red& red,
+               cudaStream_t s) {
+  k_gram_chol<T, D><<<persistent_rows(n), kThreads, 0, s>>>(W, ld, n, R, gdiag, flags, red);
+}
+
+#define NS_INST_QR(T, D)                                                                                      \
+  template void axpy_gram<T, D>(T*, const T*, const double*, int64_t, double*, unsigned*, const Red&,         \
+                                cudaStream_t);                                                                \
+  template void scale_gram<T, D>(const T*, int64_t, T*, int64_t, const double*, int64_t, double*, unsigned*, \
+                                 const Red&, cudaStream_t, int);                                              \
+  template void gram_chol<T, D>(const T*, int64_t, int, int64_t, double*, double*, unsigned*, const Red&,     \
+                                cudaStream_t);
+NS_INST_QR(double, 1)
+NS_INST_QR(double, 2)
+NS_INST_QR(double, 4)
+NS_INST_QR(double, 8)
+NS_INST_QR(float, 1)
+NS_INST_QR(float, 2)
+NS_INST_QR(float, 4)
+NS_INST_QR(float, 8)
+
+// ---------------------------------------------------------------------------
+// projections against V = [X | Z]  (classical Gram-Schmidt; called twice = CGS2)
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T v_at(const VParts<T>& V, int64_t n, int64_t i, int k) {
+  if (k < V.kx) return V.X[(int64_t)k * n + i];
+  const int kz = k - V.kx;
+  return V.Z[(int64_t)(kz / V.p) * n * V.p + i * V.p + (kz % V.p)];
+}
+
+constexpr int kKT = 8;  // V columns per dots tile
+
+// part[chunk][k][c] = sum over the rows of the chunk of V[i,k] W[i,c]
+template <typename T, int W>
+__global__ void __launch_bounds__(kThreads) k_proj_dots(VParts<T> V, const T* __restrict__ Wp, int64_t ldw,
+                                                        int64_t n, int64_t rows_per_chunk, double* part) {
+  constexpr int NP = kKT * W;
+  __shared__ double red_s[(kThreads / 32) * NP];
+  __shared__ double tot[NP];
+  const int K = V.kx + V.kz;
+  const int k0 = blockIdx.y * kKT;
+  const int64_t r0 = (int64_t)blockIdx.x * rows_per_chunk;
+  int64_t r1 = r0 + rows_per_chunk;
+  if (r1 > n) r1 = n;
+  T acc[NP];
+#pragma unroll
+  for (int k = 0; k < NP; ++k) acc[k] = T(0);
+  for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+    T w[W];
+#pragma unroll
+    for (int c = 0; c < W; ++c) w[c] = Wp[i * ldw + c];
+#pragma unroll
+    for (int kk = 0; kk < kKT; ++kk) {
+      const int k = k0 + kk;
+      const T v = (k < K) ? v_at(V, n, i, k) : T(0);
+#pragma unroll
+      for (int c = 0; c < W; ++c) acc[kk * W + c] = fma(v, w[c], acc[kk * W + c]);
+    }
+  }
+  double pd[NP];
+#pragma unroll
+  for (int k = 0; k < NP; ++k) pd[k] = (double)acc[k];
+  block_sum<NP>(pd, red_s, tot);
+  for (int t = threadIdx.x; t < NP; t += blockDim.x) {
+    const int k = k0 + t / W;
+    if (k < K) part[((size_t)blockIdx.x * K + k) * W + (t % W)] = tot[t];
+  }
+}
+
+__global__ void k_dots_reduce(const double* part, int nchunks, int KW, double* C) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < KW; t += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int c = 0; c < nchunks; ++c) s += part[(size_t)c * KW + t];
+    C[t] = s;
+  }
+}
+
+static int64_t dots_rows_per_chunk(int64_t n) {
+  // at most ~128 rows per thread inside one chunk keeps FP32 partial sums short
+  int64_t r = (int64_t)kThreads * 128;
+  if (r > n) r = n > 0 ? n : 1;
+  return r;
+}
+
+template <typename T, int W>
+void proj_dots(const VParts<T>& V, const T* Wp, int64_t ldw, int64_t n, double* C, double* part, cudaStream_t s) {
+  const int K = V.kx + V.kz;
+  if (K == 0) return;
+  const int64_t rpc = dots_rows_per_chunk(n);
+  const int nchunks = ceil_div(n, rpc);
+  dim3 grid(nchunks, ceil_div(K, kKT));
+  k_proj_dots<T, W><<<grid, kThreads, 0, s>>>(V, Wp, ldw, n, rpc, part);
+  k_dots_reduce<<<ceil_div((int64_t)K * W, kThreads), kThreads, 0, s>>>(part, nchunks, K * W, C);
+}
+
+// W -= V C (C: K x W row-major FP64, staged in dynamic shared memory) ; optional Gram + Cholesky
+template <typename T, int W>
+__global__ void __launch_bounds__(kThreads) k_proj_update(VParts<T> V, const double* __restrict__ C,
+                                                          T* __restrict__ Wp, int64_t ldw, int64_t n, int gram,
+                                                          double* R, double* gdiag, unsigned* flags, Red red) {
+  constexpr int NP = W * W;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* c_s = reinterpret_cast<T*>(smem_raw);
+  __shared__ double red_s[(kThreads / 32) * NP];
+  __shared__ double tot[NP];
+  const int K = V.kx + V.kz;
+  for (int t = threadIdx.x; t < K * W; t += blockDim.x) c_s[t] = (T)C[t];
+  __syncthreads();
+  T part[NP];
+#pragma unroll
+  for (int k = 0; k < NP; ++k) part[k] = T(0);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    T w[W];
+#pragma unroll
+    for (int c = 0; c < W; ++c) w[c] = Wp[i * ldw + c];
+    for (int k = 0; k < V.kx; ++k) {
+      const T v = V.X[(int64_t)k * n + i];
+#pragma unroll
+      for (int c = 0; c < W; ++c) w[c] = fma(-v, c_s[k * W + c], w[c]);
+    }
+    for (int kz = 0; kz < V.kz; ++kz) {
+      const T v = V.Z[(int64_t)(kz / V.p) * n * V.p + i * V.p + (kz % V.p)];
+      const int k = V.kx + kz;
+#pragma unroll
+      for (int c = 0; c < W; ++c) w[c] = fma(-v, c_s[k * W + c], w[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < W; ++c) Wp[i * ldw + c] = w[c];
+    if (gram) {
+#pragma unroll
+      for (int p = 0; p < W; ++p)
+#pragma unroll
+        for (int q = 0; q < W; ++q) part[p * W + q] = fma(w[p], w[q], part[p * W + q]);
+    }
+  }
+  if (!gram) return;
+  double pd[NP];
+#pragma unroll
+  for (int k = 0; k < NP; ++k) pd[k] = (double)part[k];
+  block_sum<NP>(pd, red_s, tot);
+  if (threadIdx.x < NP) red.part[(size_t)blockIdx.x * NP + threadIdx.x] = tot[threadIdx.x];
+  if (last_block_reduce(red.part, NP, red.ticket, tot, red_s))
+    if (threadIdx.x == 0) finish_chol(tot, W, R, gdiag, flags);
+}
+
+template <typename T, int W>
+void proj_update(const VParts<T>& V, const double* C, T* Wp, int64_t ldw, int64_t n, int gram, double* R,
+                 double* gdiag, unsigned* flags, const Red& red, cudaStream_t s) {
+  const int K = V.kx + V.kz;
+  const size_t smem = sizeof(T) * (size_t)K * W;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_proj_update<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr_set = true;
+  }
+  k_proj_update<T, W><<<persistent_rows(n), kThreads, smem, s>>>(V, C, Wp, ldw, n, gram, R, gdiag, flags, red);
+}
+
+#define NS_INST_PROJ(T, W)                                                                                   \
+  template void proj_dots<T, W>(const VParts<T>&, const T*, int64_t, int64_t, double*, double*, cudaStream_t); \
+  template void proj_update<T, W>(const VParts<T>&, const double*, T*, int64_t, int64_t, int, double*, double*, \
+                                  unsigned*, const Red&, cudaStream_t);
+NS_INST_PROJ(double, 1)
+NS_INST_PROJ(double, 2)
+NS_INST_PROJ(double, 4)
+NS_INST_PROJ(double, 8)
+NS_INST_PROJ(float, 1)
+NS_INST_PROJ(float, 2)
+NS_INST_PROJ(float, 4)
+NS_INST_PROJ(float, 8)
+
+// ---------------------------------------------------------------------------
+// thick-restart GEMM: [Lnew | Znext] = Z(:, 0:R) V_Z(:, sel)
+// ---------------------------------------------------------------------------
+constexpr int kGR = 32;  // rows per block
+constexpr int kGC = 32;  // output columns per pass
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_restart_gemm(const T* __restrict__ Z, int d, int R,
+                                                           const double* __restrict__ VZ, const int* __restrict__ sel,
+                                                           int nsel, int nl, int64_t n, T* Lnew, T* Znext) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* zs = reinterpret_cast<T*>(smem_raw);  // kGR x R
+  T* vs = zs + kGR * R;                    // R x kGC
+  const int64_t i0 = (int64_t)blockIdx.x * kGR;
+  for (int t = threadIdx.x; t < kGR * R; t += blockDim.x) {
+    const int r = t / R, j = t % R;
+    const int64_t i = i0 + r;
+    zs[t] = (i < n) ? Z[(int64_t)(j / d) * n * d + i * d + (j % d)] : T(0);
+  }
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 8 warps x 32 columns
+  for (int c0 = 0; c0 < nsel; c0 += kGC) {
+    __syncthreads();
+    for (int t = threadIdx.x; t < R * kGC; t += blockDim.x) {
+      const int j = t / kGC, c = t % kGC;
+      vs[t] = (c0 + c < nsel) ? (T)VZ[(int64_t)sel[c0 + c] * R + j] : T(0);
+    }
+    __syncthreads();
+    T acc[4] = {T(0), T(0), T(0), T(0)};
+    for (int j = 0; j < R; ++j) {
+      const T v = vs[j * kGC + tx];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] = fma(zs[(ty + 8 * q) * R + j], v, acc[q]);
+    }
+    const int c = c0 + tx;
+    if (c < nsel) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int64_t i = i0 + ty + 8 * q;
+        if (i >= n) continue;
+        if (c < nl) {
+          Lnew[i * nl + c] = acc[q];
+        } else {
+          const int kc = c - nl;
+          Znext[(int64_t)(kc / d) * n * d + i * d + (kc % d)] = acc[q];
+        }
+      }
+    }
+  }
+}
+
+template <typename T>
+void restart_gemm(const T* Z, int d, int R, const double* VZ, const int* sel, int nsel, int nl, int64_t n, T* Lnew,
+                  T* Znext, cudaStream_t s) {
+  if (nsel == 0 || n == 0) return;
+  const size_t smem = sizeof(T) * (size_t)(kGR * R + R * kGC);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_restart_gemm<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr_set = true;
+  }
+  k_restart_gemm<T><<<ceil_div(n, kGR), kThreads, smem, s>>>(Z, d, R, VZ, sel, nsel, nl, n, Lnew, Znext);
+}
+template void restart_gemm<double>(const double*, int, int, const double*, const int*, int, int, int64_t, double*,
+                                   double*, cudaStream_t);
+template void restart_gemm<float>(const float*, int, int, const double*, const int*, int, int, int64_t, float*,
+                                  float*, cudaStream_t);
+
+template <typename T>
+__global__ void k_panel_to_cols(const T* P, int64_t ldp, int w, int64_t n, T* X, int c0) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    for (int c = 0; c < w; ++c) X[(int64_t)(c0 + c) * n + i] = P[i * ldp + c];
+}
+template <typename T>
+void panel_to_cols(const T* P, int64_t ldp, int w, int64_t n, T* X, int c0, cudaStream_t s) {
+  k_panel_to_cols<T><<<stream_grid(n), kThreads, 0, s>>>(P, ldp, w, n, X, c0);
+}
+template void panel_to_cols<double>(const double*, int64_t, int, int64_t, double*, int, cudaStream_t);
+template void panel_to_cols<float>(const float*, int64_t, int, int64_t, float*, int, cudaStream_t);
+
+template <typename T>
+__global__ void k_cols_to_panel64(const T* X, int c0, int w, int64_t n, double* P) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    for (int c = 0; c < w; ++c) P[i * w + c] = (double)X[(int64_t)(c0 + c) * n + i];
+}
+template <typename T>
+void cols_to_panel64(const T* X, int c0, int w, int64_t n, double* P, cudaStream_t s) {
+  k_cols_to_panel64<T><<<stream_grid(n), kThreads, 0, s>>>(X, c0, w, n, P);
+}
+template void cols_to_panel64<double>(const double*, int, int, int64_t, double*, cudaStream_t);
+template void cols_to_panel64<float>(const float*, int, int, int64_t, double*, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// Lanczos step finalization: Gamma_j = R2 R1, its norms, and column j+1 of W
+// (Sec. 4.2, three cases, readings R2-R6); one block
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_step_finalize(OmegaArgs a, int mode) {
+  __shared__ double sh[4];  // g, nXj, nGjm1, sumF
+  __shared__ int bd;
+  __shared__ int trig[2];
+  const int d = a.d, j = a.j;
+  const int nbp = a.nb + 1;
+  if (threadIdx.x == 0) {
+    double G[kMaxD * kMaxD];
+    if (a.R2)
+      matmul_dd(a.R2, a.R1, G, d);
+    else
+      for (int k = 0; k < d * d; ++k) G[k] = a.R1[k];
+    double smax, smn;
+    sv_minmax(G, d, &smax, &smn);
+    bd = ((*a.flags & 1u) != 0u) || !(smn > a.bd_tol);
+    if (bd) {
+      for (int k = 0; k < d * d; ++k) G[k] = 0.0;
+      smax = smn = 0.0;
+    }
+    for (int k = 0; k < d * d; ++k) a.Gam[(size_t)j * d * d + k] = G[k];
+    a.nGam[j] = smax;
+    a.sminGam[j] = smn;
+    trig[0] = trig[1] = 0;
+  }
+  __syncthreads();
+  if (mode == 1) return;
+  if (bd) {
+    if (threadIdx.x == 0) {
+      atomicOr(a.flags, 1u);
+      a.counters[2] += 1;
+    }
+    return;
+  }
+  double* cj = a.wz + (size_t)(j % 3) * nbp;
+  double* cjm1 = a.wz + (size_t)((j + 2) % 3) * nbp;
+  double* cn = a.wz + (size_t)((j + 1) % 3) * nbp;
+  if (threadIdx.x == 0) {
+    sh[0] = 1.0 / a.sminGam[j];
+    sh[1] = a.nXi[j];
+    sh[2] = a.nGam[j - 1];
+    double s = 0.0;
+    for (int i = 0; i < a.r0; ++i) s += cj[i] * a.nF[i];  // w_{i,j} ||F_i||, i < r0 < j
+    sh[3] = s;
+  }
+  __syncthreads();
+  const double g = sh[0], nXj = sh[1], nGjm1 = sh[2], sumF = sh[3];
+  const double ud2 = 2.0 * a.u_d;
+  // w(a, c) = W[a][c] for a < c, else 0 (strictly upper triangular W)
+#define WZ(row, colptr, col) ((row) < (col) ? (colptr)[row] : 0.0)
+  int tz = 0;
+  for (int b = threadIdx.x; b <= j; b += blockDim.x) {
+    double val;
+    if (b < a.r0) {
+      val = WZ(b, cj, j) * (a.nTheta[b] + nXj) + WZ(a.r0, cj, j) * a.nF[b] + WZ(b, cjm1, j - 1) * nGjm1 + ud2;
+    } else if (b == a.r0) {
+      val = WZ(b, cj, j) * (a.nXi[b] + nXj) + sumF + WZ(b + 1, cj, j) * a.nGam[b] + WZ(b, cjm1, j - 1) * nGjm1 +
+            ud2;
+    } else {
+      val = WZ(b, cj, j) * (a.nXi[b] + nXj) + WZ(b + 1, cj, j) * a.nGam[b] + WZ(b - 1, cj, j) * a.nGam[b - 1] +
+            WZ(b, cjm1, j - 1) * nGjm1 + ud2;
+    }
+    const double w = g * val;
+    cn[b] = w;
+    if (!(w <= a.u_ro)) tz = 1;
+  }
+#undef WZ
+  double* xj = a.wx + (size_t)(j % 3) * a.cap;
+  double* xjm1 = a.wx + (size_t)((j + 2) % 3) * a.cap;
+  double* xn = a.wx + (size_t)((j + 1) % 3) * a.cap;
+  int tx = 0;
+  for (int k = threadIdx.x; k < a.nlock; k += blockDim.x) {
+    const double w = g * (xj[k] * (a.xtheta[k] + nXj) + a.xrho[k] + xjm1[k] * nGjm1 + ud2);
+    xn[k] = w;
+    if (!(w <= a.u_ro)) tx = 1;
+  }
+  if (tz) atomicOr(&trig[0], 1);
+  if (tx) atomicOr(&trig[1], 1);
+  __syncthreads();
+  const int TZ = trig[0], TX = trig[1];
+  if (TZ) {
+    for (int b = threadIdx.x; b <= j; b += blockDim.x) {
+      if (b < j) cj[b] = a.u_d;
+      cn[b] = a.u_d;
+    }
+  }
+  if (TX) {
+    for (int k = threadIdx.x; k < a.nlock; k += blockDim.x) xj[k] = xn[k] = a.u_d;
+  }
+  if (threadIdx.x == 0) {
+    unsigned f = 0;
+    if (TZ) {
+      f |= 2u;
+      a.counters[0] += 1;
+    }
+    if (TX) {
+      f |= 4u;
+      a.counters[1] += 1;
+    }
+    if (f) atomicOr(a.flags, f);
+  }
+}
+
+void step_finalize(const OmegaArgs& a, cudaStream_t s) { k_step_finalize<<<1, kThreads, 0, s>>>(a, 0); }
+
+// store Gamma and its norms only (first step of a cycle, replacement blocks)
+void gamma_store(const OmegaArgs& a, cudaStream_t s) { k_step_finalize<<<1, kThreads, 0, s>>>(a, 1); }
+
+// W column `col`: rows b < upto set to val; locked rows too
+__global__ void k_omega_fill(double* wz, double* wx, int nb, int cap, int col, int upto, int nlock, double val) {
+  double* cz = wz + (size_t)(col % 3) * (nb + 1);
+  double* cx = wx + (size_t)(col % 3) * cap;
+  for (int b = threadIdx.x; b < upto; b += blockDim.x) cz[b] = val;
+  for (int k = threadIdx.x; k < nlock; k += blockDim.x) cx[k] = val;
+}
+
+void omega_init(double* wz, double* wx, int nb, int cap, int r0, int nlock, double u_d, cudaStream_t s) {
+  k_omega_fill<<<1, kThreads, 0, s>>>(wz, wx, nb, cap, r0, r0, nlock, u_d);
+  k_omega_fill<<<1, kThreads, 0, s>>>(wz, wx, nb, cap, r0 + 1, r0 + 1, nlock, u_d);
+}
+
+void omega_column(double* wz, double* wx, int nb, int cap, int col, int nlock, double u_d, cudaStream_t s) {
+  k_omega_fill<<<1, kThreads, 0, s>>>(wz, wx, nb, cap, col, col, nlock, u_d);
+}
+
+// ---------------------------------------------------------------------------
+// restart bookkeeping (one block each)
+// ---------------------------------------------------------------------------
+// T (R x R, column-major) of Eq. (defT): diag(Theta), arrow F (d x k0, row-major),
+// blocks Xi_b on the diagonal and Gamma_b below it for b = k0/d .. R/d-1
+__global__ void k_build_T(const double* Theta, const double* F, const double* Xi, const double* Gam, int k0, int d,
+                          int R, double* T) {
+  for (int t = threadIdx.x; t < R * R; t += blockDim.x) T[t] = 0.0;
+  __syncthreads();
+  for (int c = threadIdx.x; c < k0; c += blockDim.x) {
+    T[(int64_t)c * R + c] = Theta[c];
+    for (int r = 0; r < d; ++r) {
+      const double f = F[r * k0 + c];
+      T[(int64_t)c * R + (k0 + r)] = f;
+      T[(int64_t)(k0 + r) * R + c] = f;
+    }
+  }
+  const int nb = R / d, r0 = k0 / d;
+  for (int t = threadIdx.x; t < (nb - r0) * d * d; t += blockDim.x) {
+    const int b = r0 + t / (d * d), e = t % (d * d), i = e / d, k = e % d;
+    T[(int64_t)(b * d + k) * R + (b * d + i)] = Xi[(size_t)b * d * d + e];
+    if (b + 1 < nb) {
+      const double gv = Gam[(size_t)b * d * d + e];  // Gamma_b(i,k): row (b+1)d+i, column b d + k
+      T[(int64_t)(b * d + k) * R + ((b + 1) * d + i)] = gv;
+      T[(int64_t)((b + 1) * d + i) * R + (b * d + k)] = gv;
+    }
+  }
+}
+
+void build_T(const double* Theta, const double* F, const double* Xi, const double* Gam, int k0, int d, int R,
+             double* T, cudaStream_t s) {
+  k_build_T<<<1, kThreads, 0, s>>>(Theta, F, Xi, Gam, k0, d, R, T);
+}
+
+// Ritz residual estimates ||Gamma_last V_Z(last d rows, i)||_2
+__global__ void k_ritz_resid(const double* G, const double* VZ, int d, int R, double* res) {
+  for (int i = threadIdx.x; i < R; i += blockDim.x) {
+    double s = 0.0;
+    for (int r = 0; r < d; ++r) {
+      double t = 0.0;
+      for (int k = 0; k < d; ++k) t += G[r * d + k] * VZ[(int64_t)i * R + (R - d + k)];
+      s += t * t;
+    }
+    res[i] = sqrt(s);
+  }
+}
+void ritz_resid(const double* Gam_last, const double* VZ, int d, int R, double* res, cudaStream_t s) {
+  k_ritz_resid<<<1, kThreads, 0, s>>>(Gam_last, VZ, d, R, res);
+}
+
+// F = Rr Gamma_last V_Z(last d rows, keep) (reading R8), Theta = theta(keep), block norms
+__global__ void k_make_F(const double* Rr, const double* G, const double* VZ, const int* keep, const double* theta,
+                         int k0, int d, int R, double* F, double* Theta, double* nTheta, double* nF) {
+  __shared__ double RG[kMaxD * kMaxD];
+  if (threadIdx.x == 0) matmul_dd(Rr, G, RG, d);
+  __syncthreads();
+  for (int c = threadIdx.x; c < k0; c += blockDim.x) {
+    const int col = keep[c];
+    for (int r = 0; r < d; ++r) {
+      double t = 0.0;
+      for (int k = 0; k < d; ++k) t += RG[r * d + k] * VZ[(int64_t)col * R + (R - d + k)];
+      F[r * k0 + c] = t;
+    }
+    Theta[c] = theta[col];
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < k0 / d; b += blockDim.x) {
+    double th = 0.0, M[kMaxD * kMaxD];
+    for (int k = 0; k < d; ++k) th = fmax(th, fabs(Theta[b * d + k]));
+    for (int r = 0; r < d; ++r)
+      for (int k = 0; k < d; ++k) M[r * d + k] = F[r * k0 + b * d + k];
+    double smax, smn;
+    sv_minmax(M, d, &smax, &smn);
+    nTheta[b] = th;
+    nF[b] = smax;
+  }
+}
+void make_F(const double* Rr, const double* Gam_last, const double* VZ, const int* keep, const double* theta, int k0,
+            int d, int R, double* F, double* Theta, double* nTheta, double* nF, cudaStream_t s) {
+  k_make_F<<<1, kThreads, 0, s>>>(Rr, Gam_last, VZ, keep, theta, k0, d, R, F, Theta, nTheta, nF);
+}
+
+// ---------------------------------------------------------------------------
+// FP64 CG / CGLS refinement helpers on panels of width W
+// ---------------------------------------------------------------------------
+// delta += alpha p ; r -= alpha q ; rr_new[c] = sum_i r_i[c]^2
+template <int W>
+__global__ void __launch_bounds__(kThreads) k_cg_update(double* delta, const double* p, int64_t np_, double* r,
+                                                        const double* q, int64_t nr, const double* alpha, Red red,
+                                                        double* rr_new) {
+  __shared__ double red_s[(kThreads / 32) * W];
+  __shared__ double tot[W];
+  __shared__ double al[W];
+  if (threadIdx.x < W) al[threadIdx.x] = alpha[threadIdx.x];
+  __syncthreads();
+  const int64_t nmax = np_ > nr ? np_ : nr;
+  double part[W];
+#pragma unroll
+  for (int c = 0; c < W; ++c) part[c] = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nmax; i += (int64_t)gridDim.x * blockDim.x) {
+    if (i < np_) {
+#pragma unroll
+      for (int c = 0; c < W; ++c) delta[i * W + c] = fma(al[c], p[i * W + c], delta[i * W + c]);
+    }
+    if (i < nr) {
+#pragma unroll
+      for (int c = 0; c < W; ++c) {
+        const double v = fma(-al[c], q[i * W + c], r[i * W + c]);
+        r[i * W + c] = v;
+        part[c] = fma(v, v, part[c]);
+      }
+    }
+  }
+  block_sum<W>(part, red_s, tot);
+  if (threadIdx.x < W) red.part[(size_t)blockIdx.x * W + threadIdx.x] = tot[threadIdx.x];
+  if (last_block_reduce(red.part, W, red.ticket, tot, red_s))
+    if (threadIdx.x < W) rr_new[threadIdx.x] = tot[threadIdx.x];
+}
+
+template <int W>
+void cg_update2(double* delta, const double* p, int64_t np_, double* r, const double* q, int64_t nr,
+                const double* alpha, const Red& red, double* rr_new, cudaStream_t s) {
+  k_cg_update<W><<<persistent_rows(np_ > nr ? np_ : nr), kThreads, 0, s>>>(delta, p, np_, r, q, nr, alpha, red,
+                                                                             rr_new);
+}
+
+// p = s + beta p (columns with active == 0 keep p)
+template <int W>
+__global__ void k_cg_direction(double* p, const double* sres, const double* beta, int64_t n) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n * W; t += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(t % W);
+    p[t] = fma(beta[c], p[t], sres[t]);
+  }
+}
+template <int W>
+void cg_direction2(double* p, const double* sres, const double* beta, int64_t n, cudaStream_t s) {
+  k_cg_direction<W><<<stream_grid(n * W), kThreads, 0, s>>>(p, sres, beta, n);
+}
+
+// alpha[c] = num[c]/den[c] for active columns (else 0); same kernel for beta
+__global__ void k_cg_scalars(const double* num, const double* den, const unsigned char* active, double* out, int w) {
+  const int c = threadIdx.x;
+  if (c < w) out[c] = (active[c] && den[c] > 0.0) ? num[c] / den[c] : 0.0;
+}
+void cg_scalars(const double* num, const double* den, const unsigned char* active, double* out, int w,
+                cudaStream_t s) {
+  k_cg_scalars<<<1, 32, 0, s>>>(num, den, active, out, w);
+}
+
+// active[c] &= rr[c] > tol2 ; *nactive = count
+__global__ void k_cg_check(const double* rr, double tol2, unsigned char* active, int* nactive, int w) {
+  if (threadIdx.x == 0) {
+    int cnt = 0;
+    for (int c = 0; c < w; ++c) {
+      const unsigned char a = active[c] && (rr[c] > tol2);
+      active[c] = a;
+      cnt += a;
+    }
+    *nactive = cnt;
+  }
+}
+void cg_check(const double* rr, double tol2, unsigned char* active, int* nactive, int w, cudaStream_t s) {
+  k_cg_check<<<1, 32, 0, s>>>(rr, tol2, active, nactive, w);
+}
+
+// X[:, c0 + c] = P[:, c] - Dl[:, c]   (refined column written back, FP64)
+template <int W>
+__global__ void k_refined_to_cols(const double* P, const double* Dl, double* X, int c0, int w, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    for (int c = 0; c < w; ++c) X[(int64_t)(c0 + c) * n + i] = P[i * W + c] - Dl[i * W + c];
+}
+template <int W>
+void refined_to_cols(const double* P, const double* Dl, double* X, int c0, int w, int64_t n, cudaStream_t s) {
+  k_refined_to_cols<W><<<stream_grid(n), kThreads, 0, s>>>(P, Dl, X, c0, w, n);
+}
+
+template void cg_update2<8>(double*, const double*, int64_t, double*, const double*, int64_t, const double*,
+                            const Red&, double*, cudaStream_t);
+template void cg_direction2<8>(double*, const double*, const double*, int64_t, cudaStream_t);
+template void refined_to_cols<8>(const double*, const double*, double*, int, int, int64_t, cudaStream_t);
+
+}  // namespace ns

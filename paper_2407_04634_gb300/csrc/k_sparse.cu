@@ -1,0 +1,408 @@
+// Sparse kernels: CSR validation, transpose, norms and the SpMM products of the
+// operator B = A^T A + eps D (or A + eps D), Eq. (defB) and Alg. 1 line 1.
+#include "ns_common.cuh"
+#include "ns_kernels.cuh"
+
+namespace ns {
+
+int choose_lanes(int64_t nrows, int64_t nnz) {
+  const double avg = nrows > 0 ? (double)nnz / (double)nrows : 1.0;
+  int V = 1;
+  while (V < 32 && 2.0 * V <= avg) V *= 2;
+  return V;
+}
+
+// ---------------------------------------------------------------------------
+// row segment of a CSR product, V lanes per row, D columns of the dense operand
+// ---------------------------------------------------------------------------
+template <typename T, int D, int V>
+__device__ __forceinline__ void row_product(const Csr<T>& M, const T* __restrict__ v, int64_t row, int lane,
+                                            T (&acc)[D]) {
+#pragma unroll
+  for (int q = 0; q < D; ++q) acc[q] = T(0);
+  if (row < M.nrows) {
+    const int64_t s = __ldg(M.rowptr + row), e = __ldg(M.rowptr + row + 1);
+    for (int64_t k = s + lane; k < e; k += V) {
+      const T a = __ldg(M.val + k);
+      const int c = __ldg(M.col + k);
+      T xv[D];
+      load_row<T, D>(v + (int64_t)c * D, xv);
+#pragma unroll
+      for (int q = 0; q < D; ++q) acc[q] = fma(a, xv[q], acc[q]);
+    }
+  }
+  if constexpr (V > 1) {
+#pragma unroll
+    for (int o = V / 2; o > 0; o >>= 1)
+#pragma unroll
+      for (int q = 0; q < D; ++q) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+  }
+}
+
+template <typename T, int D, int V>
+__global__ void __launch_bounds__(kThreads) k_spmm_plain(Csr<T> M, const T* __restrict__ v, T* __restrict__ y) {
+  const int lane = threadIdx.x % V;
+  const int64_t row = ((int64_t)blockIdx.x * kThreads + threadIdx.x) / V;
+  T acc[D];
+  row_product<T, D, V>(M, v, row, lane, acc);
+  if (lane == 0 && row < M.nrows) store_row<T, D>(y + row * D, acc);
+}
+
+// Lanczos step product (Alg. 2 line 10):  Q' = M v + eps D x - Q_{j-1} Gamma_{j-1}^T
+// and Xi_j = sym(Q_j^T Q'); the block that finishes last reduces Xi_j.
+template <typename T, int D, int V>
+__global__ void __launch_bounds__(kThreads) k_spmm_lanczos(Csr<T> M, const T* __restrict__ v, StepOps<T> op,
+                                                           Red red) {
+  constexpr int RPB = kThreads / V;
+  constexpr int NP = D * D;
+  __shared__ double red_s[(kThreads / 32) * NP];
+  __shared__ double tot[NP];
+  __shared__ T g_s[D * D];
+  if (threadIdx.x < D * D) g_s[threadIdx.x] = op.gprev ? (T)op.gprev[threadIdx.x] : T(0);
+  __syncthreads();
+  const int lane = threadIdx.x % V, grp = threadIdx.x / V;
+  const bool has_prev = op.qprev != nullptr;
+  T part[NP];
+#pragma unroll
+  for (int k = 0; k < NP; ++k) part[k] = T(0);
+  for (int64_t tile = blockIdx.x; tile * RPB < M.nrows; tile += gridDim.x) {
+    const int64_t row = tile * RPB + grp;
+    T acc[D];
+    row_product<T, D, V>(M, v, row, lane, acc);
+    if (lane == 0 && row < M.nrows) {
+      T xi[D];
+      load_row<T, D>(op.x + row * D, xi);
+      const T de = (T)op.eps * __ldg(op.Dv + row);
+#pragma unroll
+      for (int q = 0; q < D; ++q) acc[q] = fma(de, xi[q], acc[q]);
+      if (has_prev) {
+        T qp[D];
+        load_row<T, D>(op.qprev + row * D, qp);
+#pragma unroll
+        for (int r = 0; r < D; ++r)
+#pragma unroll
+          for (int c = 0; c < D; ++c) acc[r] = fma(-qp[c], g_s[r * D + c], acc[r]);
+      }
+      store_row<T, D>(op.out + row * D, acc);
+#pragma unroll
+      for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int b = 0; b < D; ++b) part[a * D + b] = fma(xi[a], acc[b], part[a * D + b]);
+    }
+  }
+  double pd[NP];
+#pragma unroll
+  for (int k = 0; k < NP; ++k) pd[k] = (double)part[k];
+  block_sum<NP>(pd, red_s, tot);
+  if (threadIdx.x < NP) red.part[(size_t)blockIdx.x * NP + threadIdx.x] = tot[threadIdx.x];
+  if (last_block_reduce(red.part, NP, red.ticket, tot, red_s)) {
+    if (threadIdx.x == 0) {
+      double X[D * D];
+      for (int a = 0; a < D; ++a)
+        for (int b = 0; b < D; ++b) X[a * D + b] = 0.5 * (tot[a * D + b] + tot[b * D + a]);
+      for (int k = 0; k < D * D; ++k) op.xi[k] = X[k];
+      *op.xi_norm = sym_norm2(X, D);
+    }
+  }
+}
+
+// y = M v and per-column dots sum_i w_i[c] y_i[c] (w defaults to the rows of v) or
+// squared norms sum_i y_i[c]^2 (sq = 1); used by the CG / CGLS refinement.
+template <typename T, int D, int V>
+__global__ void __launch_bounds__(kThreads) k_spmm_coldot(Csr<T> M, const T* __restrict__ v, T* __restrict__ y,
+                                                          const T* __restrict__ w, int sq, Red red, double* dots) {
+  constexpr int RPB = kThreads / V;
+  __shared__ double red_s[(kThreads / 32) * D];
+  __shared__ double tot[D];
+  const int lane = threadIdx.x % V, grp = threadIdx.x / V;
+  double part[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) part[k] = 0.0;
+  const T* wv = w ? w : v;
+  for (int64_t tile = blockIdx.x; tile * RPB < M.nrows; tile += gridDim.x) {
+    const int64_t row = tile * RPB + grp;
+    T acc[D];
+    row_product<T, D, V>(M, v, row, lane, acc);
+    if (lane == 0 && row < M.nrows) {
+      store_row<T, D>(y + row * D, acc);
+      if (sq) {
+#pragma unroll
+        for (int q = 0; q < D; ++q) part[q] += (double)acc[q] * (double)acc[q];
+      } else {
+        T wr[D];
+        load_row<T, D>(wv + row * D, wr);
+#pragma unroll
+        for (int q = 0; q < D; ++q) part[q] += (double)wr[q] * (double)acc[q];
+      }
+    }
+  }
+  block_sum<D>(part, red_s, tot);
+  if (threadIdx.x < D) red.part[(size_t)blockIdx.x * D + threadIdx.x] = tot[threadIdx.x];
+  if (last_block_reduce(red.part, D, red.ticket, tot, red_s)) {
+    if (threadIdx.x < D) dots[threadIdx.x] = tot[threadIdx.x];
+  }
+}
+
+#define NS_LANES_SWITCH(V, CALL) \
+  switch (V) {                   \
+    case 1: CALL(1); break;      \
+    case 2: CALL(2); break;      \
+    case 4: CALL(4); break;      \
+    case 8: CALL(8); break;      \
+    case 16: CALL(16); break;    \
+    default: CALL(32); break;    \
+  }
+
+template <typename T, int D>
+void spmm_plain(const Csr<T>& M, const T* v, T* y, cudaStream_t s) {
+  if (M.nrows == 0) return;
+  const int grid = ceil_div(M.nrows * (int64_t)M.V, kThreads);
+#define CALL(VV) k_spmm_plain<T, D, VV><<<grid, kThreads, 0, s>>>(M, v, y)
+  NS_LANES_SWITCH(M.V, CALL)
+#undef CALL
+}
+
+static int persistent_grid(int64_t nrows, int V) {
+  const int64_t tiles = (nrows + (kThreads / V) - 1) / (kThreads / V);
+  return (int)(tiles < kMaxBlocks ? (tiles > 0 ? tiles : 1) : kMaxBlocks);
+}
+
+template <typename T, int D>
+void spmm_lanczos(const Csr<T>& M, const T* v, const StepOps<T>& op, const Red& red, cudaStream_t s) {
+  const int grid = persistent_grid(M.nrows, M.V);
+#define CALL(VV) k_spmm_lanczos<T, D, VV><<<grid, kThreads, 0, s>>>(M, v, op, red)
+  NS_LANES_SWITCH(M.V, CALL)
+#undef CALL
+}
+
+template <typename T, int D>
+void spmm_coldot(const Csr<T>& M, const T* v, T* y, const T* w, int sq, double* dots, const Red& red,
+                 cudaStream_t s) {
+  const int grid = persistent_grid(M.nrows, M.V);
+#define CALL(VV) k_spmm_coldot<T, D, VV><<<grid, kThreads, 0, s>>>(M, v, y, w, sq, red, dots)
+  NS_LANES_SWITCH(M.V, CALL)
+#undef CALL
+}
+
+#define NS_INST_SPMM(T, D)                                                                            \
+  template void spmm_plain<T, D>(const Csr<T>&, const T*, T*, cudaStream_t);                          \
+  template void spmm_lanczos<T, D>(const Csr<T>&, const T*, const StepOps<T>&, const Red&, cudaStream_t); \
+  template void spmm_coldot<T, D>(const Csr<T>&, const T*, T*, const T*, int, double*, const Red&, cudaStream_t);
+NS_INST_SPMM(double, 1)
+NS_INST_SPMM(double, 2)
+NS_INST_SPMM(double, 4)
+NS_INST_SPMM(double, 8)
+NS_INST_SPMM(float, 1)
+NS_INST_SPMM(float, 2)
+NS_INST_SPMM(float, 4)
+NS_INST_SPMM(float, 8)
+
+// ---------------------------------------------------------------------------
+// validation, norms, conversions
+// ---------------------------------------------------------------------------
+__global__ void k_validate(const int64_t* rowptr, const int* col, const double* val, int64_t m, int64_t n,
+                           int64_t nnz, unsigned* err) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r > m) return;
+  if (r == 0 && rowptr[0] != 0) atomicOr(err, 1u);
+  if (r == m) {
+    if (rowptr[m] != nnz) atomicOr(err, 1u);
+    return;
+  }
+  const int64_t s = rowptr[r], e = rowptr[r + 1];
+  if (s > e || s < 0 || e > nnz) {
+    atomicOr(err, 1u);
+    return;
+  }
+  unsigned bad = 0;
+  for (int64_t k = s; k < e; ++k) {
+    const int c = col[k];
+    if (c < 0 || (int64_t)c >= n) bad |= 2u;
+    if (!isfinite(val[k])) bad |= 4u;
+  }
+  if (bad) atomicOr(err, bad);
+}
+
+void csr_validate(const int64_t* rowptr, const int* col, const double* val, int64_t m, int64_t n, int64_t nnz,
+                  unsigned* err, cudaStream_t s) {
+  k_validate<<<ceil_div(m + 1, kThreads), kThreads, 0, s>>>(rowptr, col, val, m, n, nnz, err);
+}
+
+__global__ void k_max_abs_row_sum(const int64_t* rowptr, const double* val, int64_t m, Red red, double* out) {
+  __shared__ double red_s[kThreads / 32];
+  __shared__ double tot[1];
+  double mx = 0.0;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < m; r += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int64_t k = rowptr[r]; k < rowptr[r + 1]; ++k) s += fabs(val[k]);
+    mx = fmax(mx, s);
+  }
+  mx = warp_max(mx);
+  if ((threadIdx.x & 31) == 0) red_s[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = fmax(t, red_s[w]);
+    red.part[blockIdx.x] = t;
+  }
+  __shared__ bool am_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) am_last = (atomicAdd(red.ticket, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (am_last && threadIdx.x == 0) {
+    __threadfence();
+    double t = 0.0;
+    for (unsigned b = 0; b < gridDim.x; ++b) t = fmax(t, __ldcg(red.part + b));
+    *out = t;
+    *red.ticket = 0u;
+  }
+}
+
+void csr_max_abs_row_sum(const int64_t* rowptr, const double* val, int64_t m, double* out, const Red& red,
+                         cudaStream_t s) {
+  int grid = ceil_div(m, kThreads);
+  if (grid > kMaxBlocks) grid = kMaxBlocks;
+  if (grid < 1) grid = 1;
+  k_max_abs_row_sum<<<grid, kThreads, 0, s>>>(rowptr, val, m, red, out);
+}
+
+__global__ void k_d2f(const double* a, float* b, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+__global__ void k_f2d(const float* a, double* b, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (double)a[i];
+}
+static int stream_grid(int64_t n) {
+  int g = ceil_div(n, kThreads);
+  if (g > 152 * 16) g = 152 * 16;
+  return g < 1 ? 1 : g;
+}
+void convert_d2f(const double* a, float* b, int64_t n, cudaStream_t s) {
+  if (n > 0) k_d2f<<<stream_grid(n), kThreads, 0, s>>>(a, b, n);
+}
+void convert_f2d(const float* a, double* b, int64_t n, cudaStream_t s) {
+  if (n > 0) k_f2d<<<stream_grid(n), kThreads, 0, s>>>(a, b, n);
+}
+
+// ---------------------------------------------------------------------------
+// explicit transpose: column histogram -> exclusive scan -> scatter -> per-row
+// sort by original position (so row i of A^T lists the rows of A in order)
+// ---------------------------------------------------------------------------
+__global__ void k_count_cols(const int* col, int64_t nnz, int* count) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(count + col[e], 1);
+}
+
+constexpr int kScanChunk = 4096;
+
+__global__ void k_chunk_totals(const int* count, int64_t n, int64_t* totals) {
+  __shared__ double red_s[kThreads / 32];
+  __shared__ double tot[1];
+  const int64_t base = (int64_t)blockIdx.x * kScanChunk;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < kScanChunk; i += blockDim.x)
+    if (base + i < n) s += (double)count[base + i];
+  double v[1] = {s};
+  block_sum<1>(v, red_s, tot);
+  if (threadIdx.x == 0) totals[blockIdx.x] = (int64_t)tot[0];
+}
+
+__global__ void k_scan_totals(int64_t* totals, int nchunks) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    int64_t run = 0;
+    for (int b = 0; b < nchunks; ++b) {
+      const int64_t t = totals[b];
+      totals[b] = run;
+      run += t;
+    }
+  }
+}
+
+// rowptr_t[i+1] = offset(chunk) + inclusive prefix of count within the chunk
+__global__ void k_chunk_scan(const int* count, int64_t n, const int64_t* offs, int64_t* rowptr_t) {
+  constexpr int PER = kScanChunk / kThreads;  // 16
+  __shared__ int64_t tsum[kThreads];
+  const int64_t base = (int64_t)blockIdx.x * kScanChunk + (int64_t)threadIdx.x * PER;
+  int64_t loc[PER];
+  int64_t run = 0;
+  for (int k = 0; k < PER; ++k) {
+    run += (base + k < n) ? count[base + k] : 0;
+    loc[k] = run;
+  }
+  tsum[threadIdx.x] = run;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int64_t acc = 0;
+    for (int t = 0; t < kThreads; ++t) {
+      const int64_t v = tsum[t];
+      tsum[t] = acc;
+      acc += v;
+    }
+  }
+  __syncthreads();
+  const int64_t off = offs[blockIdx.x] + tsum[threadIdx.x];
+  for (int k = 0; k < PER; ++k)
+    if (base + k < n) rowptr_t[base + k + 1] = off + loc[k];
+  if (blockIdx.x == 0 && threadIdx.x == 0) rowptr_t[0] = 0;
+}
+
+__global__ void k_scatter(const int64_t* rowptr, const int* col, int64_t m, unsigned long long* cursor,
+                          int64_t* perm, int* rowof) {
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < m; r += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t e = rowptr[r]; e < rowptr[r + 1]; ++e) {
+      const unsigned long long pos = atomicAdd(cursor + col[e], 1ull);
+      perm[pos] = e;
+      rowof[pos] = (int)r;
+    }
+  }
+}
+
+__global__ void k_sort_rows(const int64_t* rowptr_t, int64_t n, int64_t* perm, int* rowof) {
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = rowptr_t[r], e = rowptr_t[r + 1];
+    for (int64_t i = s + 1; i < e; ++i) {  // insertion sort by original position
+      const int64_t key = perm[i];
+      const int ro = rowof[i];
+      int64_t j = i - 1;
+      while (j >= s && perm[j] > key) {
+        perm[j + 1] = perm[j];
+        rowof[j + 1] = rowof[j];
+        --j;
+      }
+      perm[j + 1] = key;
+      rowof[j + 1] = ro;
+    }
+  }
+}
+
+__global__ void k_gather_t(const int64_t* perm, const int* rowof, const double* val, int64_t nnz, int* col_t,
+                           double* val_t) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x) {
+    col_t[p] = rowof[p];
+    val_t[p] = val[perm[p]];
+  }
+}
+
+__global__ void k_copy_i64_to_u64(const int64_t* a, unsigned long long* b, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (unsigned long long)a[i];
+}
+
+void csr_transpose(const int64_t* rowptr, const int* col, const double* val, int64_t m, int64_t n, int64_t nnz,
+                   int64_t* rowptr_t, int* col_t, double* val_t, const TransposeWork& w, cudaStream_t s) {
+  cudaMemsetAsync(w.count, 0, sizeof(int) * (size_t)(n + 1), s);
+  if (nnz > 0) k_count_cols<<<stream_grid(nnz), kThreads, 0, s>>>(col, nnz, w.count);
+  const int nchunks = ceil_div(n, kScanChunk);
+  k_chunk_totals<<<nchunks, kThreads, 0, s>>>(w.count, n, w.blocksum);
+  k_scan_totals<<<1, 32, 0, s>>>(w.blocksum, nchunks);
+  k_chunk_scan<<<nchunks, kThreads, 0, s>>>(w.count, n, w.blocksum, rowptr_t);
+  k_copy_i64_to_u64<<<stream_grid(n), kThreads, 0, s>>>(rowptr_t, (unsigned long long*)w.cursor, n);
+  if (m > 0) k_scatter<<<stream_grid(m), kThreads, 0, s>>>(rowptr, col, m, (unsigned long long*)w.cursor, w.perm, w.rowof);
+  k_sort_rows<<<stream_grid(n), kThreads, 0, s>>>(rowptr_t, n, w.perm, w.rowof);
+  if (nnz > 0) k_gather_t<<<stream_grid(nnz), kThreads, 0, s>>>(w.perm, w.rowof, val, nnz, col_t, val_t);
+}
+
+}  // namespace ns

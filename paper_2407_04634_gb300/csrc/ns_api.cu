@@ -1,0 +1,1294 @@
+// Host driver and C ABI of the null-space library.
+//
+// Control flow of Alg. 2 (Kressner & Shao) with locking: the device runs every
+// arithmetic step (SpMM, recurrence, QR, W recurrence, projections, projected
+// eigenproblem, restart GEMM, refinement); the host only sequences kernels and
+// takes the per-restart decisions (which Ritz pairs to lock or keep, when to
+// stop) from a few scalars it reads back.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/nullspace.h"
+#include "ns_common.cuh"
+#include "ns_kernels.cuh"
+
+using namespace ns;
+
+struct ns_handle {
+  ns_env env{};
+  bool own_alloc = true;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  int64_t m = 0, n = 0, nnz = 0;
+  int mode = 0;
+  uint64_t seed = 0;
+  int64_t maxrow_A = 0, maxrow_At = 0;
+  // device matrix
+  int64_t* rowptr = nullptr;
+  int* col = nullptr;
+  double* val = nullptr;
+  float* val32 = nullptr;
+  int64_t* rowptr_t = nullptr;
+  int* col_t = nullptr;
+  double* val_t = nullptr;
+  float* val_t32 = nullptr;
+  double* D64 = nullptr;
+  float* D32 = nullptr;
+  double normA1 = 0.0, normAinf = 0.0;
+  // result
+  bool solved = false;
+  int64_t N = 0;
+  double* basis = nullptr;
+  size_t basis_bytes = 0;
+  ns_stats_t stats{};
+  long long launches = 0;
+};
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+namespace {
+
+struct Fail {
+  ns_status st;
+  std::string msg;
+};
+
+void* dalloc(ns_handle* h, size_t bytes) {
+  if (bytes == 0) bytes = 256;
+  void* p = nullptr;
+  if (!h->own_alloc) {
+    p = h->env.alloc(bytes, h->env.ctx);
+    if (!p) throw Fail{NS_ERR_OOM, "allocator returned NULL for " + std::to_string(bytes) + " bytes"};
+  } else {
+    const cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      throw Fail{NS_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e)};
+    }
+  }
+  return p;
+}
+
+void dfree(ns_handle* h, void* p, size_t bytes) {
+  if (!p) return;
+  if (!h->own_alloc)
+    h->env.free(p, bytes ? bytes : 256, h->env.ctx);
+  else
+    cudaFree(p);
+}
+
+void ck(cudaError_t e, const char* what) {
+  if (e != cudaSuccess) throw Fail{NS_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e)};
+}
+
+void ck_launch(const char* what) { ck(cudaGetLastError(), what); }
+
+// RAII device buffer through the handle's allocator
+struct Buf {
+  ns_handle* h = nullptr;
+  void* p = nullptr;
+  size_t bytes = 0;
+  Buf() = default;
+  Buf(ns_handle* hh, size_t b) : h(hh), p(dalloc(hh, b)), bytes(b) {}
+  Buf(const Buf&) = delete;
+  Buf& operator=(const Buf&) = delete;
+  Buf(Buf&& o) noexcept : h(o.h), p(o.p), bytes(o.bytes) { o.p = nullptr; }
+  Buf& operator=(Buf&& o) noexcept {
+    release();
+    h = o.h;
+    p = o.p;
+    bytes = o.bytes;
+    o.p = nullptr;
+    return *this;
+  }
+  ~Buf() { release(); }
+  void release() {
+    if (p) dfree(h, p, bytes);
+    p = nullptr;
+  }
+  template <typename U>
+  U* as() const {
+    return reinterpret_cast<U*>(p);
+  }
+};
+
+template <typename T>
+struct Prec;
+template <>
+struct Prec<double> {
+  static const double* D(ns_handle* h) { return h->D64; }
+  static const double* val(ns_handle* h) { return h->val; }
+  static const double* val_t(ns_handle* h) { return h->val_t; }
+};
+template <>
+struct Prec<float> {
+  static const float* D(ns_handle* h) { return h->D32; }
+  static const float* val(ns_handle* h) { return h->val32; }
+  static const float* val_t(ns_handle* h) { return h->val_t32; }
+};
+
+void ensure_fp32(ns_handle* h) {
+  if (!h->val32) {
+    h->val32 = (float*)dalloc(h, sizeof(float) * (size_t)std::max<int64_t>(h->nnz, 1));
+    convert_d2f(h->val, h->val32, h->nnz, h->stream);
+    if (h->mode == NS_MODE_NORMAL) {
+      h->val_t32 = (float*)dalloc(h, sizeof(float) * (size_t)std::max<int64_t>(h->nnz, 1));
+      convert_d2f(h->val_t, h->val_t32, h->nnz, h->stream);
+    }
+    h->D32 = (float*)dalloc(h, sizeof(float) * (size_t)h->n);
+    convert_d2f(h->D64, h->D32, h->n, h->stream);
+    ck_launch("fp32 copies");
+  }
+}
+
+template <typename T>
+Csr<T> csr_A(ns_handle* h) {
+  Csr<T> c;
+  c.rowptr = h->rowptr;
+  c.col = h->col;
+  c.val = Prec<T>::val(h);
+  c.nrows = h->m;
+  c.ncols = h->n;
+  c.nnz = h->nnz;
+  c.V = choose_lanes(h->m, h->nnz);
+  return c;
+}
+template <typename T>
+Csr<T> csr_At(ns_handle* h) {
+  Csr<T> c;
+  c.rowptr = h->rowptr_t;
+  c.col = h->col_t;
+  c.val = Prec<T>::val_t(h);
+  c.nrows = h->n;
+  c.ncols = h->m;
+  c.nnz = h->nnz;
+  c.V = choose_lanes(h->n, h->nnz);
+  return c;
+}
+
+// ---------------------------------------------------------------------------
+// the solver
+// ---------------------------------------------------------------------------
+template <typename T, int D>
+struct Solver {
+  ns_handle* h;
+  cudaStream_t s;
+  int64_t n, m;
+  int R, nb;
+  double eps, tol_eff, normB, u, u_d, u_ro, bd_tol;
+  ns_opts o;
+  Csr<T> A, At;
+  const T* Dv;
+  // buffers
+  Buf zb[2], qp, ybuf, xbuf, lnew, cbuf, dpart, redpart, small, pin;
+  T* Z[2];
+  int cur = 0;
+  int cap = 0, nlock = 0;
+  Red red;
+  // small device arrays
+  double *Xi, *Gam, *nXi, *nGam, *sminGam, *Theta, *F, *nTheta, *nF, *Tm, *theta, *VZ, *resid, *syw, *R1, *R2,
+      *Cacc, *gdiag, *wz, *wx, *xtheta, *xrho;
+  int* sel;
+  unsigned* flags;
+  long long* counters;
+  unsigned* flags_h;
+  double* pin_d;  // pinned host scratch
+  std::vector<double> xtheta_h, xrho_h;
+  // statistics
+  int64_t matvecs = 0, restarts = 0, lock_events = 0, ghosts = 0, breakdowns = 0;
+  double theta_max = 0.0;
+  std::vector<std::pair<int64_t, int>> events;
+  long long& launches;
+
+  Solver(ns_handle* hh, int R_, double tol, const ns_opts& oo)
+      : h(hh), s(hh->stream), n(hh->n), m(hh->m), R(R_), nb(R_ / D), o(oo), launches(hh->launches) {
+    eps = o.eps;
+    const bool mixed = std::is_same<T, float>::value;
+    tol_eff = mixed ? std::max(tol, o.lock_tol_mixed) : tol;
+    normB = (h->mode == NS_MODE_NORMAL ? h->normA1 * h->normAinf : h->normAinf) + eps;
+    u = Unit<T>::u;
+    if (!mixed) {
+      u_d = D * std::sqrt((double)n) * u * normB;  // Eq. (defmprd)
+    } else {
+      // FP32 reading: the inner-product length of one application of B is the row
+      // length of B, not n (sparse B); sqrt(n) u_32 would exceed sqrt(u_32).
+      const double k = (h->mode == NS_MODE_NORMAL) ? (double)h->maxrow_A * (double)h->maxrow_At : (double)h->maxrow_A;
+      u_d = D * std::sqrt(std::max(k, 1.0)) * u * normB;
+    }
+    u_ro = std::sqrt(u);
+    bd_tol = 100.0 * u_d;
+    A = csr_A<T>(h);
+    if (h->mode == NS_MODE_NORMAL) At = csr_At<T>(h);
+    Dv = Prec<T>::D(h);
+    const size_t zbytes = sizeof(T) * (size_t)n * (R + D);
+    zb[0] = Buf(h, zbytes);
+    zb[1] = Buf(h, zbytes);
+    Z[0] = zb[0].as<T>();
+    Z[1] = zb[1].as<T>();
+    qp = Buf(h, sizeof(T) * (size_t)n * D);
+    if (h->mode == NS_MODE_NORMAL) ybuf = Buf(h, sizeof(T) * (size_t)m * D);
+    lnew = Buf(h, sizeof(T) * (size_t)n * R);
+    cap = (int)std::min<int64_t>(n, std::max(64, R));
+    xbuf = Buf(h, sizeof(T) * (size_t)n * cap);
+    alloc_proj();
+    redpart = Buf(h, sizeof(double) * (size_t)kMaxBlocks * 64 + 256);
+    red.part = redpart.as<double>();
+    // small arena
+    const size_t nbp = nb + 1;
+    size_t off = 0;
+    auto take = [&](size_t cnt) {
+      const size_t o2 = off;
+      off += (cnt + 7) & ~(size_t)7;
+      return o2;
+    };
+    const size_t oXi = take(nbp * D * D), oGam = take(nbp * D * D), onXi = take(nbp), onGam = take(nbp),
+                 osmin = take(nbp), oTheta = take(R), oF = take((size_t)D * R), onTheta = take(nbp), onF = take(nbp),
+                 oTm = take((size_t)R * R), otheta = take(R), oVZ = take((size_t)R * R), oresid = take(R),
+                 osyw = take(syev_work_doubles(R)), oR1 = take(64), oR2 = take(64), oC = take(64),
+                 ogd = take(8), owz = take(3 * nbp), osel = take(R), oflags = take(8), ocnt = take(8);
+    small = Buf(h, sizeof(double) * off);
+    double* b = small.as<double>();
+    Xi = b + oXi;
+    Gam = b + oGam;
+    nXi = b + onXi;
+    nGam = b + onGam;
+    sminGam = b + osmin;
+    Theta = b + oTheta;
+    F = b + oF;
+    nTheta = b + onTheta;
+    nF = b + onF;
+    Tm = b + oTm;
+    theta = b + otheta;
+    VZ = b + oVZ;
+    resid = b + oresid;
+    syw = b + osyw;
+    R1 = b + oR1;
+    R2 = b + oR2;
+    Cacc = b + oC;
+    gdiag = b + ogd;
+    wz = b + owz;
+    sel = reinterpret_cast<int*>(b + osel);
+    flags = reinterpret_cast<unsigned*>(b + oflags);
+    red.ticket = flags + 4;
+    counters = reinterpret_cast<long long*>(b + ocnt);
+    ck(cudaMemsetAsync(small.p, 0, sizeof(double) * off, s), "memset");
+    alloc_locked_meta();
+    ck(cudaMallocHost(&pin_d, sizeof(double) * (2 * (size_t)R + 64)), "cudaMallocHost");
+    flags_h = reinterpret_cast<unsigned*>(pin_d + 2 * R + 32);
+  }
+  ~Solver() {
+    if (pin_d) cudaFreeHost(pin_d);
+  }
+
+  Buf wxbuf;
+  // W rows of the locked set (3 rotating columns) + their Ritz values and residuals
+  void alloc_locked_meta(int oldcap = 0) {
+    Buf nb2(h, sizeof(double) * (size_t)(5 * (size_t)cap + 64));
+    ck(cudaMemsetAsync(nb2.p, 0, nb2.bytes, s), "memset");
+    if (wxbuf.p && nlock)
+      for (int c = 0; c < 3; ++c)
+        ck(cudaMemcpyAsync(nb2.as<double>() + (size_t)c * cap, wxbuf.as<double>() + (size_t)c * oldcap,
+                           sizeof(double) * nlock, cudaMemcpyDeviceToDevice, s),
+           "copy");
+    wxbuf = std::move(nb2);
+    wx = wxbuf.as<double>();
+    xtheta = wx + 3 * (size_t)cap;
+    xrho = xtheta + cap;
+    if (nlock) {
+      ck(cudaMemcpyAsync(xtheta, xtheta_h.data(), sizeof(double) * nlock, cudaMemcpyHostToDevice, s), "h2d");
+      ck(cudaMemcpyAsync(xrho, xrho_h.data(), sizeof(double) * nlock, cudaMemcpyHostToDevice, s), "h2d");
+    }
+  }
+
+  void alloc_proj() {
+    const int K = cap + R + D;
+    cbuf = Buf(h, sizeof(double) * (size_t)K * 8 * 2);
+    const int64_t rpc = std::min<int64_t>((int64_t)kThreads * 128, std::max<int64_t>(n, 1));
+    const int nch = ceil_div(n, rpc);
+    dpart = Buf(h, sizeof(double) * (size_t)nch * K * 8);
+  }
+
+  void grow_locked(int need) {
+    if (need <= cap) return;
+    int nc = cap;
+    while (nc < need) nc *= 2;
+    nc = (int)std::min<int64_t>(nc, n);
+    Buf nx(h, sizeof(T) * (size_t)n * nc);
+    if (nlock) ck(cudaMemcpyAsync(nx.p, xbuf.p, sizeof(T) * (size_t)n * nlock, cudaMemcpyDeviceToDevice, s), "copy");
+    ck(cudaStreamSynchronize(s), "sync");
+    xbuf = std::move(nx);
+    const int oldcap = cap;
+    cap = nc;
+    alloc_proj();
+    alloc_locked_meta(oldcap);
+    ck(cudaStreamSynchronize(s), "sync");
+  }
+
+  T* X() const { return xbuf.as<T>(); }
+  T* blk(int which, int b) const { return Z[which] + (size_t)b * n * D; }
+
+  void sync() { ck(cudaStreamSynchronize(s), "stream sync"); }
+
+  unsigned read_flags() {
+    ck(cudaMemcpyAsync(flags_h, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s), "d2h flags");
+    sync();
+    return *flags_h;
+  }
+  void clear_flags() { ck(cudaMemsetAsync(flags, 0, sizeof(unsigned), s), "memset flags"); }
+
+  // ---- B applied to one block with the fused recurrence epilogue ----
+  void apply_step(const T* x, const T* qprev, const double* gprev, double* xi, double* xi_norm) {
+    StepOps<T> op;
+    op.x = x;
+    op.Dv = Dv;
+    op.eps = eps;
+    op.qprev = qprev;
+    op.gprev = gprev;
+    op.out = qp.as<T>();
+    op.xi = xi;
+    op.xi_norm = xi_norm;
+    if (h->mode == NS_MODE_SPD) {
+      spmm_lanczos<T, D>(A, x, op, red, s);
+      launches += 1;
+    } else {
+      spmm_plain<T, D>(A, x, ybuf.as<T>(), s);
+      spmm_lanczos<T, D>(At, ybuf.as<T>(), op, red, s);
+      launches += 2;
+    }
+    matvecs += D;
+  }
+
+  // ---- CGS2 of a panel of width W against [X(0:kx) | Z blocks 0..nzb-1 of buffer zw] ----
+  template <int W>
+  void project(T* Wp, int64_t ldw, int kx, int zw, int nzb, bool gram, double* Rout, double* gd) {
+    VParts<T> V;
+    V.X = X();
+    V.kx = kx;
+    V.Z = Z[zw];
+    V.kz = nzb * D;
+    V.p = D;
+    if (V.kx + V.kz == 0) {
+      if (gram) {
+        gram_chol<T, W>(Wp, ldw, W, n, Rout, gd, flags, red, s);
+        launches += 1;
+      }
+      return;
+    }
+    if ((size_t)(V.kx + V.kz) * W * sizeof(T) > 190 * 1024)
+      throw Fail{NS_ERR_INVALID_ARG, "projection basis too wide for one pass"};
+    for (int pass = 0; pass < 2; ++pass) {
+      proj_dots<T, W>(V, Wp, ldw, n, cbuf.as<double>(), dpart.as<double>(), s);
+      proj_update<T, W>(V, cbuf.as<double>(), Wp, ldw, n, (pass == 1 && gram) ? 1 : 0, Rout, gd, flags, red, s);
+      launches += 3;
+    }
+  }
+
+  // CholQR2 of a block (in place); pass-1 factor R1 already computed into r1.
+  // Leaves the full factor R = R2 R1 in (R1, R2).
+  template <int W>
+  void cholqr_finish(T* Wp, int64_t ldw, double* r1, double* r2) {
+    scale_gram<T, W>(Wp, ldw, Wp, ldw, r1, n, r2, flags, red, s, W);
+    scale_gram<T, W>(Wp, ldw, Wp, ldw, r2, n, nullptr, flags, red, s, W);
+    launches += 2;
+  }
+
+  OmegaArgs omega_args(int j, int r0) {
+    OmegaArgs a;
+    a.j = j;
+    a.r0 = r0;
+    a.nb = nb;
+    a.d = D;
+    a.nlock = nlock;
+    a.u_d = u_d;
+    a.u_ro = u_ro;
+    a.R1 = R1;
+    a.R2 = R2;
+    a.Gam = Gam;
+    a.nGam = nGam;
+    a.sminGam = sminGam;
+    a.nXi = nXi;
+    a.nTheta = nTheta;
+    a.nF = nF;
+    a.xtheta = xtheta;
+    a.xrho = xrho;
+    a.wz = wz;
+    a.wx = wx;
+    a.cap = cap;
+    a.bd_tol = bd_tol;
+    a.flags = flags;
+    a.counters = counters;
+    return a;
+  }
+
+  // replacement of a broken-down block (reading R12): random block orthogonalized
+  // against [X, Z blocks 0..b-1] of the current buffer
+  void replace_block(int which, int b) {
+    breakdowns += 1;
+    T* q = blk(which, b);
+    rng_gauss<T>(h->seed, (uint32_t)(2 + breakdowns - 1), q, n * D, s);
+    launches += 1;
+    clear_flags();
+    project<D>(q, D, nlock, which, b, true, R1, nullptr);
+    cholqr_finish<D>(q, D, R1, R2);
+    clear_flags();
+  }
+
+  void orthonormal_start() {
+    T* q0 = blk(cur, 0);
+    rng_gauss<T>(h->seed, 1u, q0, n * D, s);  // Alg. 2 line 2
+    launches += 1;
+    gram_chol<T, D>(q0, D, D, n, R1, nullptr, flags, red, s);
+    launches += 1;
+    cholqr_finish<D>(q0, D, R1, R2);  // Alg. 2 line 4
+    if (read_flags() & 1u) {
+      clear_flags();
+      replace_block(cur, 0);
+    }
+  }
+
+  // Alg. 2 lines 6-8: first step of a cycle
+  void first_step(int r0) {
+    T* q = blk(cur, r0);
+    apply_step(q, nullptr, nullptr, Xi + (size_t)r0 * D * D, nXi + r0);
+    project<D>(qp.as<T>(), D, nlock, cur, r0 + 1, true, R1, nullptr);
+    T* qn = blk(cur, r0 + 1);
+    scale_gram<T, D>(qp.as<T>(), D, qn, D, R1, n, R2, flags, red, s, D);
+    OmegaArgs a = omega_args(r0, r0);
+    gamma_store(a, s);
+    scale_gram<T, D>(qn, D, qn, D, R2, n, nullptr, flags, red, s, D);
+    launches += 3;
+    if (read_flags() & 1u) {
+      clear_flags();
+      replace_block(cur, r0 + 1);
+      set_gamma_zero_host(r0);
+    }
+    omega_init(wz, wx, nb, cap, r0, nlock, u_d, s);
+    launches += 2;
+  }
+
+  void set_gamma_zero_host(int j) {
+    ck(cudaMemsetAsync(Gam + (size_t)j * D * D, 0, sizeof(double) * D * D, s), "memset");
+    ck(cudaMemsetAsync(nGam + j, 0, sizeof(double), s), "memset");
+    ck(cudaMemsetAsync(sminGam + j, 0, sizeof(double), s), "memset");
+  }
+
+  // Alg. 2 lines 10-12 for block j (r0 < j < nb)
+  void inner_step(int j, int r0) {
+    T* q = blk(cur, j);
+    T* qn = blk(cur, j + 1);
+    apply_step(q, blk(cur, j - 1), Gam + (size_t)(j - 1) * D * D, Xi + (size_t)j * D * D, nXi + j);
+    axpy_gram<T, D>(qp.as<T>(), q, Xi + (size_t)j * D * D, n, R1, flags, red, s);
+    scale_gram<T, D>(qp.as<T>(), D, qn, D, R1, n, R2, flags, red, s, D);
+    OmegaArgs a = omega_args(j, r0);
+    if (o.reorth == NS_REORTH_FULL) a.u_ro = -1.0;  // every column triggers
+    step_finalize(a, s);
+    scale_gram<T, D>(qn, D, qn, D, R2, n, nullptr, flags, red, s, D);
+    launches += 4;
+    const unsigned f = read_flags();
+    if (f) clear_flags();
+    if (f & 1u) {  // breakdown: fresh block, coupling set to zero
+      replace_block(cur, j + 1);
+      omega_column(wz, wx, nb, cap, j + 1, nlock, u_d, s);
+      launches += 1;
+      return;
+    }
+    const bool tz = (f & 2u) != 0, tx = (f & 4u) != 0;
+    if (tz || tx) {
+      const int kx = tx ? nlock : 0;
+      // Q_j against [X, Z_{0..j-1}], then Q_{j+1} against [X, Z_{0..j}] (Sec. 4.2)
+      project_parts(q, kx, tz ? j : 0);
+      project_parts(qn, kx, tz ? j + 1 : 0);
+    }
+  }
+
+  void project_parts(T* q, int kx, int nzb) {
+    project<D>(q, D, kx, cur, nzb, true, R1, nullptr);
+    cholqr_finish<D>(q, D, R1, R2);
+    if (read_flags() & 1u) throw Fail{NS_ERR_CUDA, "rank loss in reorthogonalization"};
+  }
+
+  // lock the new Ritz vectors stored in lnew (row-major, width nl); returns ghosts
+  int lock_new(int nl, const std::vector<int>& cand, std::vector<char>& is_ghost) {
+    T* L = lnew.as<T>();
+    int c0 = 0, ng = 0;
+    grow_locked(nlock + nl);
+    while (c0 < nl) {
+      const int left = nl - c0;
+      const int w = left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
+      bool ok = lock_chunk(L + c0, nl, w, cand, c0, is_ghost);
+      if (!ok) {  // ghost inside: lock the columns one by one
+        for (int c = c0; c < c0 + w; ++c) {
+          if (!lock_chunk(L + c, nl, 1, cand, c, is_ghost)) {
+            is_ghost[c] = 1;
+            ++ng;
+          }
+        }
+      }
+      c0 += w;
+    }
+    return ng;
+  }
+
+  template <int W>
+  bool lock_chunk_w(T* P, int64_t ld, const std::vector<int>& cand, int c0) {
+    clear_flags();
+    project<W>(P, ld, nlock, cur, 0, true, R1, gdiag);
+    double* gd = pin_d;
+    ck(cudaMemcpyAsync(gd, gdiag, sizeof(double) * W, cudaMemcpyDeviceToHost, s), "d2h");
+    const unsigned f = read_flags();
+    for (int c = 0; c < W; ++c)
+      if (!(gd[c] >= 0.25)) return false;  // mostly inside span(X): a ghost
+    if (f & 1u) return false;
+    cholqr_finish<W>(P, ld, R1, R2);
+    if (read_flags() & 1u) return false;
+    panel_to_cols<T>(P, ld, W, n, X(), nlock, s);
+    launches += 1;
+    for (int c = 0; c < W; ++c) {
+      xtheta_h.push_back(pin_theta[cand[c0 + c]]);
+      xrho_h.push_back(pin_res[cand[c0 + c]]);
+    }
+    ck(cudaMemcpyAsync(xtheta + nlock, xtheta_h.data() + nlock, sizeof(double) * W, cudaMemcpyHostToDevice, s), "h2d");
+    ck(cudaMemcpyAsync(xrho + nlock, xrho_h.data() + nlock, sizeof(double) * W, cudaMemcpyHostToDevice, s), "h2d");
+    nlock += W;
+    return true;
+  }
+
+  bool lock_chunk(T* P, int64_t ld, int w, const std::vector<int>& cand, int c0, std::vector<char>& is_ghost) {
+    (void)is_ghost;
+    switch (w) {
+      case 8: return lock_chunk_w<8>(P, ld, cand, c0);
+      case 4: return lock_chunk_w<4>(P, ld, cand, c0);
+      case 2: return lock_chunk_w<2>(P, ld, cand, c0);
+      default: return lock_chunk_w<1>(P, ld, cand, c0);
+    }
+  }
+
+  std::vector<double> pin_theta, pin_res;
+
+  // ---- Alg. 2 lines 13-17 + locking + stopping rule; returns true to stop ----
+  bool restart(int& k0) {
+    const int r0 = k0 / D;
+    build_T(Theta, F, Xi, Gam, k0, D, R, Tm, s);
+    syev(Tm, R, theta, VZ, syw, s);
+    ritz_resid(Gam + (size_t)(nb - 1) * D * D, VZ, D, R, resid, s);
+    launches += 4;
+    (void)r0;
+    ck(cudaMemcpyAsync(pin_d, theta, sizeof(double) * R, cudaMemcpyDeviceToHost, s), "d2h");
+    ck(cudaMemcpyAsync(pin_d + R, resid, sizeof(double) * R, cudaMemcpyDeviceToHost, s), "d2h");
+    sync();
+    pin_theta.assign(pin_d, pin_d + R);
+    pin_res.assign(pin_d + R, pin_d + 2 * R);
+    restarts += 1;
+    theta_max = std::max(theta_max, pin_theta[R - 1]);
+    std::vector<int> cand;
+    int nsmall = 0;
+    for (int i = 0; i < R; ++i) {
+      if (pin_theta[i] < 3.0 * eps) {
+        ++nsmall;
+        if (pin_res[i] <= tol_eff * normB) cand.push_back(i);
+      }
+    }
+    std::vector<char> taken(R, 0), is_ghost(cand.size(), 0);
+    int nlocked_now = 0;
+    if (!cand.empty()) {
+      ck(cudaMemcpyAsync(sel, cand.data(), sizeof(int) * cand.size(), cudaMemcpyHostToDevice, s), "h2d");
+      restart_gemm<T>(Z[cur], D, R, VZ, sel, (int)cand.size(), (int)cand.size(), n, lnew.as<T>(), nullptr, s);
+      launches += 1;
+      const int before = nlock;
+      const int ng = lock_new((int)cand.size(), cand, is_ghost);
+      ghosts += ng;
+      nlocked_now = nlock - before;
+      if (nlocked_now > 0) {
+        events.emplace_back(matvecs, nlocked_now);
+        lock_events += 1;
+      }
+      for (int i : cand) taken[i] = 1;
+    }
+    const int n_unl = nsmall - (int)cand.size();
+    std::vector<int> avail;
+    for (int i = 0; i < R; ++i)
+      if (!taken[i]) avail.push_back(i);
+    int nk = D * ((n_unl + R) / (2 * D));
+    nk = std::max(nk, D);
+    nk = std::min(nk, R - 2 * D);
+    nk = std::min(nk, D * ((int)avail.size() / D));
+    const int other = 1 - cur;
+    ck(cudaMemcpyAsync(sel, avail.data(), sizeof(int) * nk, cudaMemcpyHostToDevice, s), "h2d");
+    restart_gemm<T>(Z[cur], D, R, VZ, sel, nk, 0, n, nullptr, Z[other], s);
+    launches += 1;
+    // Alg. 2 line 16: Q_{l+1} against [X, Z_new], moved to block nk/D of the new buffer
+    T* qlast = blk(cur, nb);
+    clear_flags();
+    project<D>(qlast, D, nlock, other, nk / D, true, R1, nullptr);
+    T* qn = blk(other, nk / D);
+    scale_gram<T, D>(qlast, D, qn, D, R1, n, R2, flags, red, s, D);
+    scale_gram<T, D>(qn, D, qn, D, R2, n, nullptr, flags, red, s, D);
+    launches += 2;
+    bool bd = (read_flags() & 1u) != 0;
+    if (bd) {
+      clear_flags();
+      replace_block(other, nk / D);
+      ck(cudaMemsetAsync(Cacc, 0, sizeof(double) * 64, s), "memset");
+    } else {
+      mat2(R2, R1, Cacc);  // Rr = R2 R1
+    }
+    make_F(Cacc, Gam + (size_t)(nb - 1) * D * D, VZ, sel, theta, nk, D, R, F, Theta, nTheta, nF, s);
+    launches += 1;
+    cur = other;
+    k0 = nk;
+    // ---- stopping rule (Sec. 4.3, reading R11) ----
+    double sv = (double)R;
+    if (events.size() >= 2) {
+      int later = 0;
+      for (size_t e = 1; e < events.size(); ++e) later += events[e].second;
+      sv = (double)(events.back().first - events.front().first) / std::max(1.0, (double)later / D);
+    }
+    sv = std::max(sv, (double)R);
+    const int64_t since = matvecs - (events.empty() ? 0 : events.back().first);
+    if (n_unl == 0 && nlocked_now == 0 && (double)since > o.stop_factor * sv) return true;
+    return false;
+  }
+
+  void mat2(const double* a, const double* b, double* c) {
+    // c = a b for d x d on the device via the finalize helper: reuse a tiny kernel
+    mat_small(a, b, c);
+  }
+  void mat_small(const double* a, const double* b, double* c);
+
+  // ---- whole Lanczos phase ----
+  ns_status run(bool& converged) {
+    orthonormal_start();
+    int k0 = 0;
+    const int64_t maxmv = o.max_matvec > 0 ? o.max_matvec : std::min<int64_t>(100 * n + 50 * R, 1000000);
+    converged = false;
+    while (true) {
+      const int r0 = k0 / D;
+      first_step(r0);
+      for (int j = r0 + 1; j < nb; ++j) inner_step(j, r0);
+      if (restart(k0)) {
+        converged = true;
+        break;
+      }
+      if (matvecs >= maxmv) break;
+    }
+    return converged ? NS_OK : NS_ERR_NOT_CONVERGED;
+  }
+};
+
+__global__ void k_mat_small(const double* a, const double* b, double* c, int d) {
+  if (threadIdx.x == 0) matmul_dd(a, b, c, d);
+}
+template <typename T, int D>
+void Solver<T, D>::mat_small(const double* a, const double* b, double* c) {
+  k_mat_small<<<1, 32, 0, s>>>(a, b, c, D);
+  launches += 1;
+}
+
+// ---------------------------------------------------------------------------
+// FP64 refinement: project every basis column onto null(A) (CG / CGLS)
+// ---------------------------------------------------------------------------
+// columns [c0, c0+w) of X into a zero-padded row-major panel of width 8
+__global__ void k_cols_to_panel8(const double* X, int c0, int w, int64_t n, double* P) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    for (int c = 0; c < 8; ++c) P[i * 8 + c] = (c < w) ? X[(int64_t)(c0 + c) * n + i] : 0.0;
+}
+
+struct RefineOut {
+  int64_t iters_max = 0;
+  double resid_max = 0.0;
+  int failed = 0;
+};
+
+RefineOut refine(ns_handle* h, double* X, int64_t N, double normA, const ns_opts& o) {
+  RefineOut out;
+  constexpr int W = 8;
+  cudaStream_t s = h->stream;
+  const int64_t n = h->n, m = h->m;
+  Csr<double> A = csr_A<double>(h), At;
+  if (h->mode == NS_MODE_NORMAL) At = csr_At<double>(h);
+  Buf bx(h, sizeof(double) * n * W), bdl(h, sizeof(double) * n * W), bp(h, sizeof(double) * n * W),
+      bq(h, sizeof(double) * std::max(n, m) * W), br(h, sizeof(double) * std::max(n, m) * W),
+      bs(h, sizeof(double) * n * W), bred(h, sizeof(double) * (size_t)kMaxBlocks * 64 + 256), bsm(h, 4096);
+  Red red;
+  red.part = bred.as<double>();
+  double* sm = bsm.as<double>();
+  double *rr = sm, *rrn = sm + 8, *den = sm + 16, *alpha = sm + 24, *beta = sm + 32, *gam = sm + 40;
+  unsigned char* active = reinterpret_cast<unsigned char*>(sm + 48);
+  int* nact = reinterpret_cast<int*>(sm + 50);
+  red.ticket = reinterpret_cast<unsigned*>(sm + 52);
+  ck(cudaMemsetAsync(bsm.p, 0, 4096, s), "memset");
+  int* nact_h = nullptr;
+  ck(cudaMallocHost(&nact_h, 64), "cudaMallocHost");
+  double* rr_h = reinterpret_cast<double*>(nact_h + 4);
+  const double tol2 = (o.refine_tol * normA) * (o.refine_tol * normA);
+  for (int64_t c0 = 0; c0 < N; c0 += W) {
+    const int w = (int)std::min<int64_t>(W, N - c0);
+    k_cols_to_panel8<<<std::min<int64_t>(ceil_div(n, kThreads), 152 * 16), kThreads, 0, s>>>(X, (int)c0, w, n,
+                                                                                          bx.as<double>());
+    h->launches += 1;
+    ck_launch("refine panel");
+    std::vector<unsigned char> act(W, 0);
+    for (int c = 0; c < w; ++c) act[c] = 1;
+    ck(cudaMemcpyAsync(active, act.data(), W, cudaMemcpyHostToDevice, s), "h2d");
+    ck(cudaMemsetAsync(bdl.p, 0, bdl.bytes, s), "memset");
+    int it = 0;
+    if (h->mode == NS_MODE_SPD) {
+      // r = A x ; p = r
+      spmm_coldot<double, W>(A, bx.as<double>(), br.as<double>(), nullptr, 1, rr, red, s);
+      ck(cudaMemcpyAsync(bp.p, br.p, sizeof(double) * n * W, cudaMemcpyDeviceToDevice, s), "copy");
+      cg_check(rr, tol2, active, nact, W, s);
+      h->launches += 2;
+      for (; it < o.refine_maxit; ++it) {
+        ck(cudaMemcpyAsync(nact_h, nact, sizeof(int), cudaMemcpyDeviceToHost, s), "d2h");
+        ck(cudaStreamSynchronize(s), "sync");
+        if (*nact_h == 0) break;
+        spmm_coldot<double, W>(A, bp.as<double>(), bq.as<double>(), nullptr, 0, den, red, s);  // p^T A p
+        cg_scalars(rr, den, active, alpha, W, s);
+        cg_update2<W>(bdl.as<double>(), bp.as<double>(), n, br.as<double>(), bq.as<double>(), n, alpha, red, rrn, s);
+        cg_scalars(rrn, rr, active, beta, W, s);
+        cg_direction2<W>(bp.as<double>(), br.as<double>(), beta, n, s);
+        ck(cudaMemcpyAsync(rr, rrn, sizeof(double) * W, cudaMemcpyDeviceToDevice, s), "copy");
+        cg_check(rr, tol2, active, nact, W, s);
+        h->launches += 6;
+      }
+    } else {
+      // CGLS on min ||A delta - A x||: r = A x (m), s = A^T r, p = s
+      spmm_coldot<double, W>(A, bx.as<double>(), br.as<double>(), nullptr, 1, rr, red, s);
+      spmm_coldot<double, W>(At, br.as<double>(), bs.as<double>(), nullptr, 1, gam, red, s);
+      ck(cudaMemcpyAsync(bp.p, bs.p, sizeof(double) * n * W, cudaMemcpyDeviceToDevice, s), "copy");
+      cg_check(rr, tol2, active, nact, W, s);
+      h->launches += 3;
+      for (; it < o.refine_maxit; ++it) {
+        ck(cudaMemcpyAsync(nact_h, nact, sizeof(int), cudaMemcpyDeviceToHost, s), "d2h");
+        ck(cudaStreamSynchronize(s), "sync");
+        if (*nact_h == 0) break;
+        spmm_coldot<double, W>(A, bp.as<double>(), bq.as<double>(), nullptr, 1, den, red, s);  // ||A p||^2
+        cg_scalars(gam, den, active, alpha, W, s);
+        cg_update2<W>(bdl.as<double>(), bp.as<double>(), n, br.as<double>(), bq.as<double>(), m, alpha, red, rr, s);
+        spmm_coldot<double, W>(At, br.as<double>(), bs.as<double>(), nullptr, 1, rrn, red, s);  // ||A^T r||^2
+        cg_scalars(rrn, gam, active, beta, W, s);
+        cg_direction2<W>(bp.as<double>(), bs.as<double>(), beta, n, s);
+        ck(cudaMemcpyAsync(gam, rrn, sizeof(double) * W, cudaMemcpyDeviceToDevice, s), "copy");
+        cg_check(rr, tol2, active, nact, W, s);
+        h->launches += 7;
+      }
+    }
+    refined_to_cols<W>(bx.as<double>(), bdl.as<double>(), X, (int)c0, w, n, s);
+    ck(cudaMemcpyAsync(rr_h, rr, sizeof(double) * W, cudaMemcpyDeviceToHost, s), "d2h");
+    ck(cudaStreamSynchronize(s), "sync");
+    ck_launch("refine");
+    out.iters_max = std::max<int64_t>(out.iters_max, it);
+    for (int c = 0; c < w; ++c) {
+      const double rel = std::sqrt(std::max(rr_h[c], 0.0)) / std::max(normA, 1e-300);
+      out.resid_max = std::max(out.resid_max, rel);
+      if (rr_h[c] > tol2 * 1.0001) out.failed += 1;
+    }
+  }
+  cudaFreeHost(nact_h);
+  return out;
+}
+
+}  // namespace
+
+// typed bodies of the C entry points
+template <typename T, int D>
+static ns_status solve_typed(ns_handle* h, int R, double tol, const ns_opts& o) {
+  cudaStream_t s = h->stream;
+  cudaEvent_t e0, e1, e2;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventCreate(&e2);
+  ns_status st = NS_OK;
+  bool conv = false;
+  int64_t N = 0;
+  Solver<T, D> S(h, R, tol, o);
+  cudaEventRecord(e0, s);
+  st = S.run(conv);
+  cudaEventRecord(e1, s);
+  N = S.nlock;
+  // FP64 basis
+  if (h->basis) dfree(h, h->basis, h->basis_bytes);
+  h->basis_bytes = sizeof(double) * (size_t)std::max<int64_t>(N, 1) * h->n;
+  h->basis = (double*)dalloc(h, h->basis_bytes);
+  if (N) {
+    if (std::is_same<T, double>::value)
+      ck(cudaMemcpyAsync(h->basis, S.X(), sizeof(double) * (size_t)N * h->n, cudaMemcpyDeviceToDevice, s), "copy");
+    else
+      convert_f2d(reinterpret_cast<const float*>(S.X()), h->basis, (int64_t)N * h->n, s);
+  }
+  double normA = (h->mode == NS_MODE_NORMAL) ? std::sqrt(std::max(S.theta_max, 0.0)) : S.theta_max;
+  RefineOut ro;
+  if (o.refine && N) {
+    ro = refine(h, h->basis, N, normA, o);
+    if (ro.failed && st == NS_OK) st = NS_ERR_REFINE;
+  }
+  cudaEventRecord(e2, s);
+  ck(cudaEventSynchronize(e2), "sync");
+  float t1 = 0.f, t2 = 0.f;
+  cudaEventElapsedTime(&t1, e0, e1);
+  cudaEventElapsedTime(&t2, e1, e2);
+  long long cnt[4] = {0, 0, 0, 0};
+  ck(cudaMemcpy(cnt, S.counters, sizeof(cnt), cudaMemcpyDeviceToHost), "d2h");
+  ns_stats_t& x = h->stats;
+  x = ns_stats_t{};
+  x.nullity = N;
+  x.matvecs = S.matvecs;
+  x.restarts = S.restarts;
+  x.reorth_Z = cnt[0];
+  x.reorth_X = cnt[1];
+  x.breakdowns = S.breakdowns;
+  x.lock_events = S.lock_events;
+  x.ghosts = S.ghosts;
+  x.refine_iters_max = ro.iters_max;
+  x.normB = S.normB;
+  x.normA = normA;
+  x.u_d = S.u_d;
+  x.refine_resid_max = ro.resid_max;
+  x.t_lanczos_ms = t1;
+  x.t_refine_ms = t2;
+  x.t_total_ms = t1 + t2;
+  h->N = N;
+  h->solved = true;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaEventDestroy(e2);
+  return st;
+}
+
+template <typename T, int D>
+static void apply_B_typed(ns_handle* h, const T* x, T* y, double eps, Red red) {
+  StepOps<T> op;
+  op.x = x;
+  op.Dv = Prec<T>::D(h);
+  op.eps = eps;
+  op.out = y;
+  Buf xi(h, sizeof(double) * 80);
+  op.xi = xi.as<double>();
+  op.xi_norm = xi.as<double>() + 64;
+  Csr<T> A = csr_A<T>(h);
+  if (h->mode == NS_MODE_SPD) {
+    spmm_lanczos<T, D>(A, x, op, red, h->stream);
+  } else {
+    Buf yb(h, sizeof(T) * h->m * D);
+    spmm_plain<T, D>(A, x, yb.as<T>(), h->stream);
+    spmm_lanczos<T, D>(csr_At<T>(h), yb.as<T>(), op, red, h->stream);
+    ck(cudaStreamSynchronize(h->stream), "sync");
+  }
+  ck(cudaStreamSynchronize(h->stream), "sync");
+  ck_launch("apply_B");
+}
+
+template <typename T, int W>
+static void project_typed(ns_handle* h, int64_t n, int K, const double* V, double* Wm, double* C) {
+  Buf vb(h, sizeof(T) * n * std::max(K, 1)), wb(h, sizeof(T) * n * W), v64(h, sizeof(double) * n * std::max(K, 1)),
+      w64(h, sizeof(double) * n * W), cb(h, sizeof(double) * K * W), cb2(h, sizeof(double) * K * W),
+      part(h, sizeof(double) * ((size_t)ceil_div(n, std::min<int64_t>(kThreads * 128, n)) * K * W + 8)),
+      rp(h, sizeof(double) * kMaxBlocks * 64 + 256), tk(h, 256);
+  ck(cudaMemset(tk.p, 0, 256), "memset");
+  Red red;
+  red.part = rp.as<double>();
+  red.ticket = tk.as<unsigned>();
+  ck(cudaMemcpy(v64.p, V, sizeof(double) * n * K, cudaMemcpyHostToDevice), "h2d");
+  ck(cudaMemcpy(w64.p, Wm, sizeof(double) * n * W, cudaMemcpyHostToDevice), "h2d");
+  T *vp, *wp;
+  if (std::is_same<T, double>::value) {
+    vp = reinterpret_cast<T*>(v64.p);
+    wp = reinterpret_cast<T*>(w64.p);
+  } else {
+    convert_d2f(v64.as<double>(), vb.as<float>(), n * K, nullptr);
+    convert_d2f(w64.as<double>(), wb.as<float>(), n * W, nullptr);
+    vp = vb.as<T>();
+    wp = wb.as<T>();
+  }
+  VParts<T> P;
+  P.X = vp;
+  P.kx = K;
+  P.Z = nullptr;
+  P.kz = 0;
+  P.p = 1;
+  proj_dots<T, W>(P, wp, W, n, cb.as<double>(), part.as<double>(), nullptr);
+  proj_update<T, W>(P, cb.as<double>(), wp, W, n, 0, nullptr, nullptr, nullptr, red, nullptr);
+  proj_dots<T, W>(P, wp, W, n, cb2.as<double>(), part.as<double>(), nullptr);
+  proj_update<T, W>(P, cb2.as<double>(), wp, W, n, 0, nullptr, nullptr, nullptr, red, nullptr);
+  ck_launch("project");
+  ck(cudaDeviceSynchronize(), "sync");
+  if (!std::is_same<T, double>::value) convert_f2d(wb.as<float>(), w64.as<double>(), n * W, nullptr);
+  ck(cudaDeviceSynchronize(), "sync");
+  ck(cudaMemcpy(Wm, w64.p, sizeof(double) * n * W, cudaMemcpyDeviceToHost), "d2h");
+  std::vector<double> c1(K * W), c2(K * W);
+  ck(cudaMemcpy(c1.data(), cb.p, sizeof(double) * K * W, cudaMemcpyDeviceToHost), "d2h");
+  ck(cudaMemcpy(c2.data(), cb2.p, sizeof(double) * K * W, cudaMemcpyDeviceToHost), "d2h");
+  for (int t = 0; t < K * W; ++t) C[t] = c1[t] + c2[t];
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+void ns_default_opts(ns_opts* o) {
+  if (!o) return;
+  o->eps = 1e-3;
+  o->precision = NS_FP64;
+  o->reorth = NS_REORTH_PARTIAL;
+  o->max_matvec = 0;
+  o->stop_factor = 2.0;
+  o->lock_tol_mixed = 1e-5;
+  o->refine = 1;
+  o->refine_tol = 1e-10;
+  o->refine_maxit = 500;
+  o->refine_chunk = 8;
+  o->use_graphs = 0;
+}
+
+static ns_status set_err(ns_handle* h, ns_status st, const std::string& msg) {
+  if (h) h->err = msg;
+  return st;
+}
+
+ns_status ns_create(ns_handle** out, int64_t m, int64_t n, const int64_t* rowptr, const int32_t* colind,
+                    const double* vals, int inputs_on_device, uint64_t seed, int mode, const ns_env* env) {
+  if (!out) return NS_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (m < 0 || n <= 0 || !rowptr || (mode != NS_MODE_NORMAL && mode != NS_MODE_SPD)) return NS_ERR_INVALID_ARG;
+  if (mode == NS_MODE_SPD && m != n) return NS_ERR_INVALID_ARG;
+  if (n > (int64_t)INT32_MAX || m > (int64_t)INT32_MAX) return NS_ERR_INVALID_ARG;
+  if (!inputs_on_device) {  // host inputs are validated before any device work
+    if (rowptr[0] != 0) return NS_ERR_INVALID_ARG;
+    for (int64_t r = 0; r < m; ++r)
+      if (rowptr[r + 1] < rowptr[r]) return NS_ERR_INVALID_ARG;
+    const int64_t nz = rowptr[m];
+    if (nz > 0 && (!colind || !vals)) return NS_ERR_INVALID_ARG;
+    for (int64_t k = 0; k < nz; ++k)
+      if (colind[k] < 0 || (int64_t)colind[k] >= n || !std::isfinite(vals[k])) return NS_ERR_INVALID_ARG;
+  }
+  int dev = 0, ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return NS_ERR_CUDA;
+  }
+  ns_handle* h = new ns_handle();
+  h->m = m;
+  h->n = n;
+  h->mode = mode;
+  h->seed = seed;
+  if (env) {
+    h->env = *env;
+    h->own_alloc = (env->alloc == nullptr || env->free == nullptr);
+    h->stream = (cudaStream_t)env->stream;
+  }
+  cudaGetDevice(&dev);
+  try {
+    int64_t nnz = 0;
+    std::vector<int64_t> rp_h;
+    if (!inputs_on_device) {
+      // full host-side validation
+      if (rowptr[0] != 0) throw Fail{NS_ERR_INVALID_ARG, "rowptr[0] != 0"};
+      for (int64_t r = 0; r < m; ++r)
+        if (rowptr[r + 1] < rowptr[r]) throw Fail{NS_ERR_INVALID_ARG, "rowptr not monotone"};
+      nnz = rowptr[m];
+      if (nnz > 0 && (!colind || !vals)) throw Fail{NS_ERR_INVALID_ARG, "null colind/vals"};
+      if (nnz > (int64_t)INT32_MAX * 2) throw Fail{NS_ERR_INVALID_ARG, "nnz too large"};
+      for (int64_t k = 0; k < nnz; ++k) {
+        if (colind[k] < 0 || (int64_t)colind[k] >= n) throw Fail{NS_ERR_INVALID_ARG, "column index out of range"};
+        if (!std::isfinite(vals[k])) throw Fail{NS_ERR_INVALID_ARG, "non-finite value"};
+      }
+      for (int64_t r = 0; r < m; ++r) h->maxrow_A = std::max(h->maxrow_A, rowptr[r + 1] - rowptr[r]);
+    } else {
+      ck(cudaMemcpy(&nnz, rowptr + m, sizeof(int64_t), cudaMemcpyDeviceToHost), "read nnz");
+      rp_h.resize(m + 1);
+      ck(cudaMemcpy(rp_h.data(), rowptr, sizeof(int64_t) * (m + 1), cudaMemcpyDeviceToHost), "read rowptr");
+      for (int64_t r = 0; r < m; ++r) h->maxrow_A = std::max(h->maxrow_A, rp_h[r + 1] - rp_h[r]);
+      if (nnz < 0) throw Fail{NS_ERR_INVALID_ARG, "negative nnz"};
+    }
+    h->nnz = nnz;
+    cudaStream_t s = h->stream;
+    const cudaMemcpyKind kind = inputs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    h->rowptr = (int64_t*)dalloc(h, sizeof(int64_t) * (m + 1));
+    h->col = (int*)dalloc(h, sizeof(int) * std::max<int64_t>(nnz, 1));
+    h->val = (double*)dalloc(h, sizeof(double) * std::max<int64_t>(nnz, 1));
+    ck(cudaMemcpyAsync(h->rowptr, rowptr, sizeof(int64_t) * (m + 1), kind, s), "copy rowptr");
+    if (nnz) {
+      ck(cudaMemcpyAsync(h->col, colind, sizeof(int) * nnz, kind, s), "copy colind");
+      ck(cudaMemcpyAsync(h->val, vals, sizeof(double) * nnz, kind, s), "copy vals");
+    }
+    Buf small(h, 4096);
+    Red red;
+    red.part = nullptr;
+    Buf rp(h, sizeof(double) * (size_t)kMaxBlocks * 64 + 256);
+    red.part = rp.as<double>();
+    ck(cudaMemsetAsync(small.p, 0, 4096, s), "memset");
+    red.ticket = reinterpret_cast<unsigned*>(small.as<char>() + 1024);
+    unsigned* err = reinterpret_cast<unsigned*>(small.as<char>() + 1032);
+    double* norms = reinterpret_cast<double*>(small.as<char>() + 2048);
+    if (inputs_on_device) {
+      csr_validate(h->rowptr, h->col, h->val, m, n, nnz, err, s);
+      unsigned e = 0;
+      ck(cudaMemcpyAsync(&e, err, sizeof(unsigned), cudaMemcpyDeviceToHost, s), "d2h");
+      ck(cudaStreamSynchronize(s), "sync");
+      if (e) throw Fail{NS_ERR_INVALID_ARG, "invalid device CSR (code " + std::to_string(e) + ")"};
+    }
+    csr_max_abs_row_sum(h->rowptr, h->val, m, norms, red, s);
+    h->launches += 1;
+    if (mode == NS_MODE_NORMAL) {
+      h->rowptr_t = (int64_t*)dalloc(h, sizeof(int64_t) * (n + 1));
+      h->col_t = (int*)dalloc(h, sizeof(int) * std::max<int64_t>(nnz, 1));
+      h->val_t = (double*)dalloc(h, sizeof(double) * std::max<int64_t>(nnz, 1));
+      Buf wc(h, sizeof(int) * (n + 1)), wcur(h, sizeof(int64_t) * n), wp(h, sizeof(int64_t) * std::max<int64_t>(nnz, 1)),
+          wr(h, sizeof(int) * std::max<int64_t>(nnz, 1)), wb(h, sizeof(int64_t) * (n / 4096 + 2));
+      TransposeWork tw{wc.as<int>(), wcur.as<int64_t>(), wp.as<int64_t>(), wr.as<int>(), wb.as<int64_t>()};
+      csr_transpose(h->rowptr, h->col, h->val, m, n, nnz, h->rowptr_t, h->col_t, h->val_t, tw, s);
+      csr_max_abs_row_sum(h->rowptr_t, h->val_t, n, norms + 1, red, s);
+      h->launches += 9;
+      std::vector<int64_t> rpt(n + 1);
+      ck(cudaMemcpyAsync(rpt.data(), h->rowptr_t, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, s), "d2h");
+      ck(cudaStreamSynchronize(s), "sync");
+      for (int64_t r = 0; r < n; ++r) h->maxrow_At = std::max(h->maxrow_At, rpt[r + 1] - rpt[r]);
+    }
+    h->D64 = (double*)dalloc(h, sizeof(double) * n);
+    rng_uniform<double>(seed, 0u, h->D64, n, s);  // Alg. 2 line 1: D ~ U[0,1]
+    double nr[2] = {0.0, 0.0};
+    ck(cudaMemcpyAsync(nr, norms, sizeof(double) * 2, cudaMemcpyDeviceToHost, s), "d2h");
+    ck(cudaStreamSynchronize(s), "sync");
+    ck_launch("ns_create");
+    h->normAinf = nr[0];
+    h->normA1 = (mode == NS_MODE_NORMAL) ? nr[1] : nr[0];
+  } catch (const Fail& f) {
+    const ns_status st = f.st;
+    fprintf(stderr, "ns_create: %s\n", f.msg.c_str());
+    ns_destroy(h);
+    return st;
+  }
+  *out = h;
+  return NS_OK;
+}
+
+ns_status ns_solve(ns_handle* h, int d, int restart_len, double tol, const ns_opts* opts) {
+  if (!h) return NS_ERR_INVALID_ARG;
+  if (!(d == 1 || d == 2 || d == 4 || d == 8)) return set_err(h, NS_ERR_INVALID_ARG, "d must be 1, 2, 4 or 8");
+  if (restart_len % d || restart_len < 3 * d || restart_len > 512)
+    return set_err(h, NS_ERR_INVALID_ARG, "restart_len must be a multiple of d in [3d, 512]");
+  if (!(tol > 0.0)) return set_err(h, NS_ERR_INVALID_ARG, "tol must be positive");
+  ns_opts o;
+  ns_default_opts(&o);
+  if (opts) o = *opts;
+  if (!(o.eps >= 0.0) || o.stop_factor <= 0.0) return set_err(h, NS_ERR_INVALID_ARG, "bad opts");
+  h->err.clear();
+  h->solved = false;
+  h->launches = 0;
+  try {
+    ns_status st;
+    if (o.precision == NS_MIXED) {
+      ensure_fp32(h);
+      switch (d) {
+        case 1: st = solve_typed<float, 1>(h, restart_len, tol, o); break;
+        case 2: st = solve_typed<float, 2>(h, restart_len, tol, o); break;
+        case 4: st = solve_typed<float, 4>(h, restart_len, tol, o); break;
+        default: st = solve_typed<float, 8>(h, restart_len, tol, o); break;
+      }
+    } else {
+      switch (d) {
+        case 1: st = solve_typed<double, 1>(h, restart_len, tol, o); break;
+        case 2: st = solve_typed<double, 2>(h, restart_len, tol, o); break;
+        case 4: st = solve_typed<double, 4>(h, restart_len, tol, o); break;
+        default: st = solve_typed<double, 8>(h, restart_len, tol, o); break;
+      }
+    }
+    h->stats.kernel_launches = h->launches;
+    return st;
+  } catch (const Fail& f) {
+    cudaGetLastError();
+    return set_err(h, f.st, f.msg);
+  }
+}
+
+ns_status ns_nullity(const ns_handle* h, int64_t* N) {
+  if (!h || !N) return NS_ERR_INVALID_ARG;
+  if (!h->solved) return NS_ERR_STATE;
+  *N = h->N;
+  return NS_OK;
+}
+
+ns_status ns_basis(const ns_handle* hc, double* out, int64_t ld, int out_on_device) {
+  ns_handle* h = const_cast<ns_handle*>(hc);
+  if (!h || (!out && h->N)) return NS_ERR_INVALID_ARG;
+  if (!h->solved) return NS_ERR_STATE;
+  if (ld < h->n) return set_err(h, NS_ERR_INVALID_ARG, "ld < n");
+  const cudaMemcpyKind kind = out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  try {
+    if (h->N)
+      ck(cudaMemcpy2DAsync(out, sizeof(double) * ld, h->basis, sizeof(double) * h->n, sizeof(double) * h->n, h->N,
+                           kind, h->stream),
+         "copy basis");
+    ck(cudaStreamSynchronize(h->stream), "sync");
+  } catch (const Fail& f) {
+    return set_err(h, f.st, f.msg);
+  }
+  return NS_OK;
+}
+
+ns_status ns_stats(const ns_handle* h, ns_stats_t* s) {
+  if (!h || !s) return NS_ERR_INVALID_ARG;
+  if (!h->solved) return NS_ERR_STATE;
+  *s = h->stats;
+  return NS_OK;
+}
+
+const char* ns_last_error(const ns_handle* h) {
+  if (!h) return "null handle";
+  return h->err.c_str();
+}
+
+void ns_destroy(ns_handle* h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->stream);
+  dfree(h, h->rowptr, 0);
+  dfree(h, h->col, 0);
+  dfree(h, h->val, 0);
+  dfree(h, h->val32, 0);
+  dfree(h, h->rowptr_t, 0);
+  dfree(h, h->col_t, 0);
+  dfree(h, h->val_t, 0);
+  dfree(h, h->val_t32, 0);
+  dfree(h, h->D64, 0);
+  dfree(h, h->D32, 0);
+  dfree(h, h->basis, h->basis_bytes);
+  delete h;
+}
+
+// ---------------------------------------------------------------------------
+// kernel-level entry points
+// ---------------------------------------------------------------------------
+ns_status ns_get_transpose(const ns_handle* h, int64_t* rowptr, int32_t* colind, double* vals) {
+  if (!h || !rowptr) return NS_ERR_INVALID_ARG;
+  if (h->mode != NS_MODE_NORMAL) return NS_ERR_STATE;
+  cudaStream_t s = h->stream;
+  if (cudaMemcpyAsync(rowptr, h->rowptr_t, sizeof(int64_t) * (h->n + 1), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return NS_ERR_CUDA;
+  if (h->nnz) {
+    if (!colind || !vals) return NS_ERR_INVALID_ARG;
+    cudaMemcpyAsync(colind, h->col_t, sizeof(int) * h->nnz, cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(vals, h->val_t, sizeof(double) * h->nnz, cudaMemcpyDeviceToHost, s);
+  }
+  return cudaStreamSynchronize(s) == cudaSuccess ? NS_OK : NS_ERR_CUDA;
+}
+
+ns_status ns_get_perturbation(const ns_handle* h, double* D) {
+  if (!h || !D) return NS_ERR_INVALID_ARG;
+  if (cudaMemcpyAsync(D, h->D64, sizeof(double) * h->n, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+    return NS_ERR_CUDA;
+  return cudaStreamSynchronize(h->stream) == cudaSuccess ? NS_OK : NS_ERR_CUDA;
+}
+
+ns_status ns_start_block(const ns_handle* hc, int d, double* Omega) {
+  ns_handle* h = const_cast<ns_handle*>(hc);
+  if (!h || !Omega || d < 1 || d > 8) return NS_ERR_INVALID_ARG;
+  try {
+    Buf b(h, sizeof(double) * h->n * d);
+    rng_gauss<double>(h->seed, 1u, b.as<double>(), h->n * d, h->stream);
+    ck_launch("rng");
+    ck(cudaMemcpyAsync(Omega, b.p, sizeof(double) * h->n * d, cudaMemcpyDeviceToHost, h->stream), "d2h");
+    ck(cudaStreamSynchronize(h->stream), "sync");
+  } catch (const Fail& f) {
+    return set_err(h, f.st, f.msg);
+  }
+  return NS_OK;
+}
+
+ns_status ns_apply_B(ns_handle* h, int d, const double* X, double* Y, double eps, int precision, int on_device) {
+  if (!h || !X || !Y || !(d == 1 || d == 2 || d == 4 || d == 8)) return NS_ERR_INVALID_ARG;
+  try {
+    const size_t cnt = (size_t)h->n * d;
+    Buf xb(h, sizeof(double) * cnt), yb(h, sizeof(double) * cnt), rp(h, sizeof(double) * kMaxBlocks * 64 + 256),
+        tk(h, 256);
+    ck(cudaMemsetAsync(tk.p, 0, 256, h->stream), "memset");
+    Red red;
+    red.part = rp.as<double>();
+    red.ticket = tk.as<unsigned>();
+    ck(cudaMemcpyAsync(xb.p, X, sizeof(double) * cnt, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                       h->stream),
+       "copy X");
+    if (precision == NS_MIXED) {
+      ensure_fp32(h);
+      Buf xf(h, sizeof(float) * cnt), yf(h, sizeof(float) * cnt);
+      convert_d2f(xb.as<double>(), xf.as<float>(), (int64_t)cnt, h->stream);
+      switch (d) {
+        case 1: apply_B_typed<float, 1>(h, xf.as<float>(), yf.as<float>(), eps, red); break;
+        case 2: apply_B_typed<float, 2>(h, xf.as<float>(), yf.as<float>(), eps, red); break;
+        case 4: apply_B_typed<float, 4>(h, xf.as<float>(), yf.as<float>(), eps, red); break;
+        default: apply_B_typed<float, 8>(h, xf.as<float>(), yf.as<float>(), eps, red); break;
+      }
+      convert_f2d(yf.as<float>(), yb.as<double>(), (int64_t)cnt, h->stream);
+      ck(cudaStreamSynchronize(h->stream), "sync");
+    } else {
+      switch (d) {
+        case 1: apply_B_typed<double, 1>(h, xb.as<double>(), yb.as<double>(), eps, red); break;
+        case 2: apply_B_typed<double, 2>(h, xb.as<double>(), yb.as<double>(), eps, red); break;
+        case 4: apply_B_typed<double, 4>(h, xb.as<double>(), yb.as<double>(), eps, red); break;
+        default: apply_B_typed<double, 8>(h, xb.as<double>(), yb.as<double>(), eps, red); break;
+      }
+    }
+    ck(cudaMemcpyAsync(Y, yb.p, sizeof(double) * cnt, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                       h->stream),
+       "copy Y");
+    ck(cudaStreamSynchronize(h->stream), "sync");
+  } catch (const Fail& f) {
+    return set_err(h, f.st, f.msg);
+  }
+  return NS_OK;
+}
+
+ns_status ns_syev(int k, const double* T, double* theta, double* V) {
+  if (k < 1 || k > 512 || !T || !theta || !V) return NS_ERR_INVALID_ARG;
+  ns_handle tmp;
+  try {
+    Buf bt(&tmp, sizeof(double) * k * k), bth(&tmp, sizeof(double) * k), bv(&tmp, sizeof(double) * k * k),
+        bw(&tmp, sizeof(double) * syev_work_doubles(k));
+    ck(cudaMemcpy(bt.p, T, sizeof(double) * k * k, cudaMemcpyHostToDevice), "h2d");
+    syev(bt.as<double>(), k, bth.as<double>(), bv.as<double>(), bw.as<double>(), nullptr);
+    ck_launch("syev");
+    ck(cudaDeviceSynchronize(), "sync");
+    int status = 0;
+    ck(cudaMemcpy(&status, bw.as<double>() + syev_work_doubles(k) - 2, sizeof(int), cudaMemcpyDeviceToHost), "d2h");
+    ck(cudaMemcpy(theta, bth.p, sizeof(double) * k, cudaMemcpyDeviceToHost), "d2h");
+    ck(cudaMemcpy(V, bv.p, sizeof(double) * k * k, cudaMemcpyDeviceToHost), "d2h");
+    if (status) return NS_ERR_NOT_CONVERGED;
+  } catch (const Fail& f) {
+    return f.st;
+  }
+  return NS_OK;
+}
+
+ns_status ns_project(int64_t n, int K, int w, const double* V, double* Wm, double* C, int precision) {
+  if (n < 1 || K < 1 || !(w == 1 || w == 2 || w == 4 || w == 8) || !V || !Wm || !C) return NS_ERR_INVALID_ARG;
+  ns_handle tmp;
+  tmp.n = n;
+  try {
+    if (precision == NS_MIXED) {
+      switch (w) {
+        case 1: project_typed<float, 1>(&tmp, n, K, V, Wm, C); break;
+        case 2: project_typed<float, 2>(&tmp, n, K, V, Wm, C); break;
+        case 4: project_typed<float, 4>(&tmp, n, K, V, Wm, C); break;
+        default: project_typed<float, 8>(&tmp, n, K, V, Wm, C); break;
+      }
+    } else {
+      switch (w) {
+        case 1: project_typed<double, 1>(&tmp, n, K, V, Wm, C); break;
+        case 2: project_typed<double, 2>(&tmp, n, K, V, Wm, C); break;
+        case 4: project_typed<double, 4>(&tmp, n, K, V, Wm, C); break;
+        default: project_typed<double, 8>(&tmp, n, K, V, Wm, C); break;
+      }
+    }
+  } catch (const Fail& f) {
+    return f.st;
+  }
+  return NS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,181 @@
+// Launch wrappers of the null-space library's kernels (host side declarations).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ns {
+
+// CSR matrix resident on the device; V = lanes cooperating on one row (1..32)
+template <typename T>
+struct Csr {
+  const int64_t* rowptr = nullptr;
+  const int* col = nullptr;
+  const T* val = nullptr;
+  int64_t nrows = 0, ncols = 0, nnz = 0;
+  int V = 8;
+};
+
+// Reduction workspace: partial sums and an atomic ticket for the last-block protocol
+struct Red {
+  double* part = nullptr;  // >= kMaxBlocks * 64 doubles
+  unsigned* ticket = nullptr;
+};
+
+constexpr int kMaxBlocks = 152 * 8;  // persistent grid cap of reducing kernels
+
+// Lanczos step epilogue operands (all device pointers)
+template <typename T>
+struct StepOps {
+  const T* x = nullptr;       // Q_j (panel n x d)
+  const T* Dv = nullptr;      // perturbation diagonal
+  double eps = 0.0;
+  const T* qprev = nullptr;   // Q_{j-1} or null
+  const double* gprev = nullptr;  // Gamma_{j-1} (d x d, row-major) or null
+  T* out = nullptr;           // Q'
+  double* xi = nullptr;       // Xi_j output (d x d)
+  double* xi_norm = nullptr;  // ||Xi_j||_2 output
+};
+
+// ---- sparse (k_sparse.cu) ----
+int choose_lanes(int64_t nrows, int64_t nnz);
+template <typename T, int D>
+void spmm_plain(const Csr<T>& M, const T* v, T* y, cudaStream_t s);
+// Lanczos fused step: out = M v + eps D x - qprev gprev^T ; Xi = sym(x^T out)
+template <typename T, int D>
+void spmm_lanczos(const Csr<T>& M, const T* v, const StepOps<T>& op, const Red& red, cudaStream_t s);
+// column-wise dots: y = M v, dots[c] = sum_i w_i[c] y_i[c] (w = v if w == null) or
+// norms (sq=1): dots[c] = sum_i y_i[c]^2
+template <typename T, int D>
+void spmm_coldot(const Csr<T>& M, const T* v, T* y, const T* w, int sq, double* dots, const Red& red,
+                 cudaStream_t s);
+
+// transpose by counting sort; work buffers are caller-provided (device)
+struct TransposeWork {
+  int* count;        // ncols + 1
+  int64_t* cursor;   // ncols
+  int64_t* perm;     // nnz
+  int* rowof;        // nnz
+  int64_t* blocksum; // scan partials (>= 4096)
+};
+void csr_transpose(const int64_t* rowptr, const int* col, const double* val, int64_t m, int64_t n,
+                   int64_t nnz, int64_t* rowptr_t, int* col_t, double* val_t, const TransposeWork& w,
+                   cudaStream_t s);
+// validation of a device CSR: err bit 1 rowptr, 2 colind, 4 values
+void csr_validate(const int64_t* rowptr, const int* col, const double* val, int64_t m, int64_t n,
+                  int64_t nnz, unsigned* err, cudaStream_t s);
+// max_i sum_j |a_ij|  (into *out, device double); uses red
+void csr_max_abs_row_sum(const int64_t* rowptr, const double* val, int64_t m, double* out, const Red& red,
+                         cudaStream_t s);
+// max row length (into *out, device int64 via double)
+void convert_d2f(const double* a, float* b, int64_t n, cudaStream_t s);
+void convert_f2d(const float* a, double* b, int64_t n, cudaStream_t s);
+
+// ---- dense Lanczos kernels (k_dense.cu) ----
+// Philox streams
+template <typename T>
+void rng_uniform(uint64_t seed, uint32_t stream, T* out, int64_t count, cudaStream_t s);
+template <typename T>
+void rng_gauss(uint64_t seed, uint32_t stream, T* out, int64_t count, cudaStream_t s);
+
+// q'' = q' - x Xi (in place on qp), G = q''^T q'' ; last block: R1 = chol(G) (flag bit 1 on failure)
+template <typename T, int D>
+void axpy_gram(T* qp, const T* x, const double* Xi, int64_t n, double* R1, unsigned* flags, const Red& red,
+               cudaStream_t s);
+// out = in R^{-1} (R upper d x d FP64); if R2 != null: G = out^T out, last block R2 = chol(G)
+template <typename T, int D>
+void scale_gram(const T* in, int64_t ldin, T* out, int64_t ldout, const double* R, int64_t n, double* R2,
+                unsigned* flags, const Red& red, cudaStream_t s, int w = D);
+// G = W^T W (W panel, leading dim ld, width w<=D) ; last block: R = chol(G), diag saved in gdiag
+template <typename T, int D>
+void gram_chol(const T* W, int64_t ld, int w, int64_t n, double* R, double* gdiag, unsigned* flags,
+               const Red& red, cudaStream_t s);
+
+// projection against V = [X (n x kx, column-major, ld n) | Z (kz columns in panels of width p)]
+template <typename T>
+struct VParts {
+  const T* X = nullptr;
+  int kx = 0;
+  const T* Z = nullptr;
+  int kz = 0;
+  int p = 1;
+};
+// C (K x w, FP64, row-major) = V^T W ; W panel with leading dim ldw
+template <typename T, int W>
+void proj_dots(const VParts<T>& V, const T* Wp, int64_t ldw, int64_t n, double* C, double* part,
+               cudaStream_t s);
+// W -= V C ; if gram: G = W^T W partials, last block chol -> R (+gdiag)
+template <typename T, int W>
+void proj_update(const VParts<T>& V, const double* C, T* Wp, int64_t ldw, int64_t n, int gram, double* R,
+                 double* gdiag, unsigned* flags, const Red& red, cudaStream_t s);
+
+// restart GEMM: out_c = Z V_Z(:, sel_c), c < nl -> Lnew (row-major, width nl), else Znext panel (width d)
+template <typename T>
+void restart_gemm(const T* Z, int d, int R, const double* VZ, const int* sel, int nsel, int nl, int64_t n,
+                  T* Lnew, T* Znext, cudaStream_t s);
+// copy w columns of a row-major panel (ld) into column-major X (ld n) starting at column c0
+template <typename T>
+void panel_to_cols(const T* P, int64_t ldp, int w, int64_t n, T* X, int c0, cudaStream_t s);
+// gather columns [c0, c0+w) of column-major X (T) into an FP64 row-major panel of width w
+template <typename T>
+void cols_to_panel64(const T* X, int c0, int w, int64_t n, double* P, cudaStream_t s);
+
+// Lanczos step finalization (one block): Gamma_j = R2 R1, norms, W recurrence, flags.
+struct OmegaArgs {
+  int j, r0, nb, d, nlock;
+  double u_d, u_ro;
+  const double* R1;
+  const double* R2;      // null for a single CholQR pass
+  double* Gam;           // Gamma blocks (nb+1) x d x d
+  double* nGam;          // ||Gamma_b||
+  double* sminGam;       // sigma_min(Gamma_b)
+  const double* nXi;     // ||Xi_b||
+  const double* nTheta;  // ||Theta_b|| of retained blocks
+  const double* nF;      // ||F_b|| of retained blocks
+  const double* xtheta;  // locked Ritz values
+  const double* xrho;    // locked residuals
+  double* wz;            // 3 x (nb+1) rotating columns of W
+  double* wx;            // 3 x cap rotating columns of the locked rows
+  int cap;
+  double bd_tol;
+  unsigned* flags;       // bit 1 breakdown, bit 2 reorth Z, bit 4 reorth X
+  long long* counters;   // [0] reorth_Z, [1] reorth_X, [2] breakdowns
+};
+void step_finalize(const OmegaArgs& a, cudaStream_t s);
+// Gamma and its norms only (first step of a cycle)
+void gamma_store(const OmegaArgs& a, cudaStream_t s);
+// W columns r0 and r0+1 set to u_d (start of a cycle)
+void omega_init(double* wz, double* wx, int nb, int cap, int r0, int nlock, double u_d, cudaStream_t s);
+// W column col set to u_d (after a breakdown replacement)
+void omega_column(double* wz, double* wx, int nb, int cap, int col, int nlock, double u_d, cudaStream_t s);
+
+// restart bookkeeping: T assembly, Ritz residuals, F, Theta, norms
+void build_T(const double* Theta, const double* F, const double* Xi, const double* Gam, int k0, int d, int R,
+             double* T, cudaStream_t s);
+void ritz_resid(const double* Gam_last, const double* VZ, int d, int R, double* res, cudaStream_t s);
+void make_F(const double* Rr, const double* Gam_last, const double* VZ, const int* keep, const double* theta,
+            int k0, int d, int R, double* F, double* Theta, double* nTheta, double* nF, cudaStream_t s);
+
+// ---- eigensolver (k_eig.cu) ----
+// symmetric k x k (column-major, lower triangle read) -> ascending theta, V (column-major)
+void syev(const double* T, int k, double* theta, double* V, double* work, cudaStream_t s);
+size_t syev_work_doubles(int k);
+
+// ---- FP64 CG / CGLS refinement helpers on panels of width W (k_dense.cu) ----
+// delta += alpha p (np rows) ; r -= alpha q (nr rows) ; rr_new[c] = sum_i r_i[c]^2
+template <int W>
+void cg_update2(double* delta, const double* p, int64_t np_, double* r, const double* q, int64_t nr,
+                const double* alpha, const Red& red, double* rr_new, cudaStream_t s);
+// p = s + beta p
+template <int W>
+void cg_direction2(double* p, const double* sres, const double* beta, int64_t n, cudaStream_t s);
+// out[c] = num[c] / den[c] on active columns, else 0
+void cg_scalars(const double* num, const double* den, const unsigned char* active, double* out, int w,
+                cudaStream_t s);
+// active[c] &= rr[c] > tol2 ; *nactive = number of active columns
+void cg_check(const double* rr, double tol2, unsigned char* active, int* nactive, int w, cudaStream_t s);
+// X[:, c0 + c] = P[:, c] - Dl[:, c] for c < w
+template <int W>
+void refined_to_cols(const double* P, const double* Dl, double* X, int c0, int w, int64_t n, cudaStream_t s);
+
+}  // namespace ns

@@ -1,0 +1,262 @@
+"""ctypes binding of libnullspace (C ABI declared in include/nullspace.h).
+
+Argument marshalling only: every step of the method runs in the CUDA library.
+PyTorch, when used, only supplies device memory (its caching allocator) and the
+current CUDA stream.  There is no CPU fallback: loading fails loudly when the
+library cannot be built or loaded.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+NS_OK, NS_ERR_INVALID_ARG, NS_ERR_OOM, NS_ERR_CUDA, NS_ERR_NOT_CONVERGED, NS_ERR_TIMEOUT, NS_ERR_STATE, \
+    NS_ERR_REFINE = range(8)
+STATUS = {0: "NS_OK", 1: "NS_ERR_INVALID_ARG", 2: "NS_ERR_OOM", 3: "NS_ERR_CUDA", 4: "NS_ERR_NOT_CONVERGED",
+          5: "NS_ERR_TIMEOUT", 6: "NS_ERR_STATE", 7: "NS_ERR_REFINE"}
+MODE = {"normal": 0, "spd": 1}
+PRECISION = {"fp64": 0, "mixed": 1}
+REORTH = {"partial": 0, "full": 1}
+
+_ALLOC = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+_FREE = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p)
+
+
+class NsEnv(C.Structure):
+    _fields_ = [("alloc", _ALLOC), ("free", _FREE), ("ctx", C.c_void_p), ("stream", C.c_void_p)]
+
+
+class NsOpts(C.Structure):
+    _fields_ = [("eps", C.c_double), ("precision", C.c_int), ("reorth", C.c_int), ("max_matvec", C.c_int64),
+                ("stop_factor", C.c_double), ("lock_tol_mixed", C.c_double), ("refine", C.c_int),
+                ("refine_tol", C.c_double), ("refine_maxit", C.c_int), ("refine_chunk", C.c_int),
+                ("use_graphs", C.c_int)]
+
+
+class NsStats(C.Structure):
+    _fields_ = [("nullity", C.c_int64), ("matvecs", C.c_int64), ("restarts", C.c_int64), ("reorth_X", C.c_int64),
+                ("reorth_Z", C.c_int64), ("breakdowns", C.c_int64), ("lock_events", C.c_int64),
+                ("ghosts", C.c_int64), ("refine_iters_max", C.c_int64), ("kernel_launches", C.c_int64),
+                ("normB", C.c_double), ("normA", C.c_double), ("u_d", C.c_double), ("refine_resid_max", C.c_double),
+                ("t_lanczos_ms", C.c_double), ("t_refine_ms", C.c_double), ("t_total_ms", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+# exported symbols and their prototypes (kept in sync with include/nullspace.h)
+_P = C.c_void_p
+SIGNATURES = {
+    "ns_default_opts": (None, [C.POINTER(NsOpts)]),
+    "ns_create": (C.c_int, [C.POINTER(_P), C.c_int64, C.c_int64, _P, _P, _P, C.c_int, C.c_uint64, C.c_int,
+                            C.POINTER(NsEnv)]),
+    "ns_solve": (C.c_int, [_P, C.c_int, C.c_int, C.c_double, C.POINTER(NsOpts)]),
+    "ns_nullity": (C.c_int, [_P, C.POINTER(C.c_int64)]),
+    "ns_basis": (C.c_int, [_P, _P, C.c_int64, C.c_int]),
+    "ns_stats": (C.c_int, [_P, C.POINTER(NsStats)]),
+    "ns_last_error": (C.c_char_p, [_P]),
+    "ns_destroy": (None, [_P]),
+    "ns_get_transpose": (C.c_int, [_P, _P, _P, _P]),
+    "ns_get_perturbation": (C.c_int, [_P, _P]),
+    "ns_start_block": (C.c_int, [_P, C.c_int, _P]),
+    "ns_apply_B": (C.c_int, [_P, C.c_int, _P, _P, C.c_double, C.c_int, C.c_int]),
+    "ns_syev": (C.c_int, [C.c_int, _P, _P, _P]),
+    "ns_project": (C.c_int, [C.c_int64, C.c_int, C.c_int, _P, _P, _P, C.c_int]),
+}
+
+_LIB = None
+
+
+def load(path: str | None = None):
+    """Build (if needed) and load libnullspace.so; declare every prototype."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    lib = C.CDLL(path or _build.build())
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _LIB = lib
+    return lib
+
+
+class NullspaceError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _ptr(a: np.ndarray):
+    return C.c_void_p(a.ctypes.data)
+
+
+def default_opts(**kw) -> NsOpts:
+    lib = load()
+    o = NsOpts()
+    lib.ns_default_opts(C.byref(o))
+    for k, v in kw.items():
+        if k == "precision" and isinstance(v, str):
+            v = PRECISION[v]
+        if k == "reorth" and isinstance(v, str):
+            v = REORTH[v]
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k}")
+        setattr(o, k, v)
+    return o
+
+
+def torch_env():
+    """ns_env backed by PyTorch's caching allocator and current stream."""
+    import torch
+
+    dev = torch.cuda.current_device()
+    stream = torch.cuda.current_stream(dev)
+
+    @_ALLOC
+    def _alloc(nbytes, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), dev, stream)
+        except Exception:  # the library maps NULL to NS_ERR_OOM
+            return None
+
+    @_FREE
+    def _free(ptr, nbytes, ctx):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    env = NsEnv(_alloc, _free, None, C.c_void_p(stream.cuda_stream))
+    env._keep = (_alloc, _free, stream)
+    return env
+
+
+@dataclass
+class SolveResult:
+    status: int
+    nullity: int
+    stats: dict
+
+
+class Handle:
+    """One matrix on the device (ns_create); solve / basis / stats / destroy."""
+
+    def __init__(self, rowptr, colind, vals, m: int, n: int, seed: int, mode: str = "normal",
+                 env: str | None = "torch"):
+        self.lib = load()
+        self.m, self.n = int(m), int(n)
+        self._env = torch_env() if env == "torch" else None
+        on_dev = 0
+        if hasattr(rowptr, "data_ptr"):  # torch tensors on the device
+            on_dev = 1
+            ptrs = [C.c_void_p(t.data_ptr()) for t in (rowptr, colind, vals)]
+        else:
+            self._keep = (np.ascontiguousarray(rowptr, dtype=np.int64), np.ascontiguousarray(colind, dtype=np.int32),
+                          np.ascontiguousarray(vals, dtype=np.float64))
+            ptrs = [_ptr(a) for a in self._keep]
+        h = C.c_void_p()
+        st = self.lib.ns_create(C.byref(h), self.m, self.n, *ptrs, on_dev, C.c_uint64(seed), MODE[mode],
+                                C.byref(self._env) if self._env is not None else None)
+        if st != NS_OK:
+            raise NullspaceError(st, "ns_create failed")
+        self.h = h
+        self.mode = mode
+
+    def _check(self, st, what):
+        if st not in (NS_OK,):
+            raise NullspaceError(st, f"{what}: {self.lib.ns_last_error(self.h).decode()}")
+
+    def solve(self, d: int, restart_len: int, tol: float, check: bool = True, **opts) -> SolveResult:
+        o = default_opts(**opts)
+        st = self.lib.ns_solve(self.h, int(d), int(restart_len), float(tol), C.byref(o))
+        if check and st not in (NS_OK,):
+            self._check(st, "ns_solve")
+        N = C.c_int64()
+        self.lib.ns_nullity(self.h, C.byref(N))
+        return SolveResult(st, int(N.value), self.stats() if st in (NS_OK, NS_ERR_NOT_CONVERGED, NS_ERR_REFINE) else {})
+
+    def nullity(self) -> int:
+        N = C.c_int64()
+        self._check(self.lib.ns_nullity(self.h, C.byref(N)), "ns_nullity")
+        return int(N.value)
+
+    def basis(self, out=None) -> np.ndarray:
+        """n x N FP64 basis; out may be a CUDA torch tensor of shape (N, n) (column-major basis)."""
+        N = self.nullity()
+        if out is not None and hasattr(out, "data_ptr"):
+            self._check(self.lib.ns_basis(self.h, C.c_void_p(out.data_ptr()), self.n, 1), "ns_basis")
+            return out
+        X = np.zeros((N, self.n), dtype=np.float64)  # column-major n x N == row-major N x n
+        self._check(self.lib.ns_basis(self.h, _ptr(X), self.n, 0), "ns_basis")
+        return X.T
+
+    def stats(self) -> dict:
+        s = NsStats()
+        self._check(self.lib.ns_stats(self.h, C.byref(s)), "ns_stats")
+        return s.as_dict()
+
+    def transpose(self, nnz: int):
+        rp = np.zeros(self.n + 1, dtype=np.int64)
+        ci = np.zeros(max(nnz, 1), dtype=np.int32)
+        va = np.zeros(max(nnz, 1), dtype=np.float64)
+        self._check(self.lib.ns_get_transpose(self.h, _ptr(rp), _ptr(ci), _ptr(va)), "ns_get_transpose")
+        return rp, ci[:nnz], va[:nnz]
+
+    def perturbation(self) -> np.ndarray:
+        D = np.zeros(self.n)
+        self._check(self.lib.ns_get_perturbation(self.h, _ptr(D)), "ns_get_perturbation")
+        return D
+
+    def start_block(self, d: int) -> np.ndarray:
+        Om = np.zeros((self.n, d))
+        self._check(self.lib.ns_start_block(self.h, int(d), _ptr(Om)), "ns_start_block")
+        return Om
+
+    def apply_B(self, X: np.ndarray, eps: float, precision: str = "fp64") -> np.ndarray:
+        X = np.ascontiguousarray(X, dtype=np.float64)
+        d = X.shape[1]
+        Y = np.zeros_like(X)
+        self._check(self.lib.ns_apply_B(self.h, d, _ptr(X), _ptr(Y), float(eps), PRECISION[precision], 0),
+                    "ns_apply_B")
+        return Y
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.ns_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def syev(T: np.ndarray):
+    """Device eigensolver of the projected matrix (ascending eigenvalues, eigenvectors)."""
+    lib = load()
+    k = T.shape[0]
+    Tc = np.asfortranarray(T, dtype=np.float64)
+    th = np.zeros(k)
+    V = np.zeros((k, k), order="F")
+    st = lib.ns_syev(k, C.c_void_p(Tc.ctypes.data), _ptr(th), C.c_void_p(V.ctypes.data))
+    if st != NS_OK:
+        raise NullspaceError(st, "ns_syev")
+    return th, V
+
+
+def project(V: np.ndarray, W: np.ndarray, precision: str = "fp64"):
+    """CGS2 of W (n x w) against V (n x K) on the device; returns (W', C)."""
+    lib = load()
+    n, K = V.shape
+    w = W.shape[1]
+    Vc = np.asfortranarray(V, dtype=np.float64)
+    Wc = np.ascontiguousarray(W, dtype=np.float64).copy()
+    Cc = np.zeros((K, w))
+    st = lib.ns_project(n, K, w, C.c_void_p(Vc.ctypes.data), _ptr(Wc), _ptr(Cc), PRECISION[precision])
+    if st != NS_OK:
+        raise NullspaceError(st, "ns_project")
+    return Wc, Cc

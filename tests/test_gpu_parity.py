@@ -1,0 +1,238 @@
+"""Parity of the CUDA library (through its C ABI) with the CPU oracle.
+
+Inputs are seeded synthetic matrices from `workloads`; expected values come
+from the oracle or from closed forms (component indicators, planted copies).
+Tolerances:
+  * integer / index work (transpose, nullity): bit-exact;
+  * FP64 products: |y_gpu - y_ref| <= 1e-13 (|B| |X|)_i elementwise (a few
+    roundings per inner product of at most ~40 terms);
+  * FP32 products: 1e-5 (|B| |X|)_i;
+  * null-space bases: largest principal-angle sine <= 1e-6 (FP64 path) and
+    <= 1e-5 (mixed path, after FP64 refinement) against the oracle's basis, and
+    ||A X||_F / ||A||_2 <= 1e-8.
+"""
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import (lanczos_nullspace, principal_sine, indicator_basis, copy_pair_basis, perturbation_diagonal,
+                    start_block, Operator, norm2_A)
+from workloads import (make_config, laplacian_cycle_components, incidence_cycle_components, rectangular_copies,
+                       laplacian_er_components)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ns(lib):
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_2407_04634_gb300 import nullspace
+    return nullspace
+
+
+def handle(ns, w, seed):
+    A = w.A
+    return ns.Handle(A.rowptr, A.colind, A.vals, A.m, A.n, seed, w.mode)
+
+
+def abs_bound(w, X, eps, D):
+    A = abs(w.A.to_scipy())
+    Xa = np.abs(X)
+    if w.mode == "normal":
+        return A.T @ (A @ Xa) + eps * D[:, None] * Xa
+    return A @ Xa + eps * D[:, None] * Xa
+
+
+# ------------------------------------------------------------------ kernels ---
+
+def test_perturbation_and_start_block_match_philox_streams(ns):
+    w = laplacian_cycle_components(5, 3001, 3, 6, "uniform", 100, 2000)
+    h = handle(ns, w, 12345)
+    np.testing.assert_array_equal(h.perturbation(), perturbation_diagonal(12345, 3001))
+    for d in (1, 3, 8):
+        np.testing.assert_allclose(h.start_block(d), start_block(12345, 3001, d), rtol=1e-13, atol=1e-14)
+
+
+@pytest.mark.parametrize("make", ["incidence", "copies"])
+def test_transpose_bit_exact(ns, make):
+    if make == "incidence":
+        w = incidence_cycle_components(7, 20011, 9, 8, 100, 4000)
+    else:
+        w = rectangular_copies(7, 30011, 20011, 13)
+    h = handle(ns, w, 1)
+    rp, ci, va = h.transpose(w.A.nnz)
+    At = w.A.to_scipy().T.tocsr()
+    At.sort_indices()
+    np.testing.assert_array_equal(rp, At.indptr)
+    np.testing.assert_array_equal(ci, At.indices)
+    np.testing.assert_array_equal(va, At.data)
+
+
+@pytest.mark.parametrize("mode", ["spd", "normal"])
+@pytest.mark.parametrize("d", [1, 2, 4, 8])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_apply_B_matches_oracle(ns, mode, d, precision):
+    if mode == "spd":
+        w = laplacian_cycle_components(9, 40009, 7, 8, "powerlaw", 50)
+    else:
+        w = rectangular_copies(9, 30007, 20011, 5)
+    h = handle(ns, w, 77)
+    rng = np.random.default_rng(d)
+    X = rng.standard_normal((w.A.n, d))
+    if precision == "mixed":
+        X = X.astype(np.float32).astype(np.float64)
+    eps = 1e-3
+    D = h.perturbation()
+    ref = Operator(w.A.to_scipy(), mode, eps, D).apply(X)
+    Y = h.apply_B(X, eps, precision)
+    bound = abs_bound(w, X, eps, D)
+    tol = 1e-13 if precision == "fp64" else 1e-5
+    assert np.all(np.abs(Y - ref) <= tol * bound + 1e-300)
+
+
+@pytest.mark.parametrize("k", [3, 17, 64, 120, 160])
+def test_syev_matches_dense_eigensolver(ns, k):
+    rng = np.random.default_rng(k)
+    M = rng.standard_normal((k, k))
+    T = M + M.T
+    if k >= 64:  # a cluster of tiny eigenvalues, as in the projected null-space problem
+        Q, _ = np.linalg.qr(rng.standard_normal((k, k)))
+        ev = np.concatenate([1e-3 * (0.5 + 1e-6 * rng.random(k // 3)), 1 + 10 * rng.random(k - k // 3)])
+        T = (Q * ev) @ Q.T
+        T = 0.5 * (T + T.T)
+    th, V = ns.syev(T)
+    ref = np.linalg.eigvalsh(T)
+    nrm = np.linalg.norm(T, 2)
+    assert np.all(np.diff(th) >= 0)
+    np.testing.assert_allclose(th, ref, atol=1e-12 * nrm)
+    assert np.linalg.norm(T @ V - V * th) <= 1e-12 * nrm * k
+    assert np.linalg.norm(V.T @ V - np.eye(k)) <= 1e-13 * k
+
+
+@pytest.mark.parametrize("w", [1, 2, 4, 8])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_cgs2_projection(ns, w, precision):
+    rng = np.random.default_rng(w)
+    n, K = 70001, 37
+    V, _ = np.linalg.qr(rng.standard_normal((n, K)))
+    W = rng.standard_normal((n, w)) + V[:, :w] * 3.0
+    Wp, Cc = ns.project(V, W, precision)
+    tol = 1e-13 if precision == "fp64" else 2e-6
+    assert np.abs(V.T @ Wp).max() <= tol * np.sqrt(n)
+    ref = W - V @ (V.T @ W)
+    assert np.abs(Wp - ref).max() <= (1e-12 if precision == "fp64" else 1e-4)
+    np.testing.assert_allclose(Cc, V.T @ W, atol=1e-11 if precision == "fp64" else 1e-3)
+
+
+# ------------------------------------------------------------------- solves ---
+
+def check_solution(w, X, N_expect, U_ref, sine_tol, normA=None):
+    A = w.A.to_scipy()
+    assert X.shape[1] == N_expect
+    assert principal_sine(U_ref, X) <= sine_tol
+    normA = normA or norm2_A(A, w.mode)
+    assert np.linalg.norm(A @ X) / normA <= 1e-8
+    assert np.linalg.norm(X.T @ X - np.eye(X.shape[1])) <= max(1e-12, A.shape[1] * X.shape[1] * 2.0**-52)
+
+
+def test_config1_fp64_matches_oracle(ns):
+    w, p = make_config(1)
+    ref = lanczos_nullspace(w.A.to_scipy(), w.mode, p["d"], p["restart"], tol=p["tol"], seed=1000)
+    h = handle(ns, w, 1000)
+    r = h.solve(p["d"], p["restart"], p["tol"])
+    assert r.status == ns.NS_OK
+    assert r.nullity == ref.N == 20
+    X = h.basis()
+    check_solution(w, X, ref.N, ref.X, 1e-6)
+    assert principal_sine(indicator_basis(w.labels), X) <= 1e-6
+
+
+@pytest.mark.parametrize("d", [1, 2, 4])
+def test_cycle_laplacian_twin_fp64(ns, d):
+    w = laplacian_cycle_components(21, 30000, 15, 8, "powerlaw", 50)
+    ref = lanczos_nullspace(w.A.to_scipy(), "spd", d, 120, tol=1e-10, seed=1001)
+    h = handle(ns, w, 1001)
+    r = h.solve(d, 120, 1e-10)
+    assert r.nullity == ref.N == 15
+    check_solution(w, h.basis(), 15, ref.X, 1e-6)
+
+
+def test_incidence_twin_fp64(ns):
+    w = incidence_cycle_components(22, 8000, 8, 8, 100, 3900 // 4)
+    ref = lanczos_nullspace(w.A.to_scipy(), "normal", 4, 80, tol=1e-10, seed=1002)
+    h = handle(ns, w, 1002)
+    r = h.solve(4, 80, 1e-10)
+    assert r.nullity == ref.N == 8
+    check_solution(w, h.basis(), 8, ref.X, 1e-6)
+
+
+def test_copies_twin_fp64(ns):
+    w = rectangular_copies(23, 4500, 3000, 6)
+    ref = lanczos_nullspace(w.A.to_scipy(), "normal", 2, 60, tol=1e-10, seed=1003)
+    h = handle(ns, w, 1003)
+    r = h.solve(2, 60, 1e-10)
+    assert r.nullity == ref.N == 6
+    check_solution(w, h.basis(), 6, ref.X, 1e-6)
+
+
+@pytest.mark.parametrize("case", ["laplacian", "incidence", "copies"])
+def test_mixed_precision_twins(ns, case):
+    if case == "laplacian":
+        w = laplacian_cycle_components(21, 30000, 15, 8, "powerlaw", 50)
+        d, R, U = 1, 120, indicator_basis(w.labels)
+    elif case == "incidence":
+        w = incidence_cycle_components(22, 8000, 8, 8, 100, 3900 // 4)
+        d, R, U = 4, 80, indicator_basis(w.labels)
+    else:
+        w = rectangular_copies(23, 4500, 3000, 6)
+        d, R, U = 2, 60, copy_pair_basis(3000, w.copy_pairs)
+    h = handle(ns, w, 2000)
+    r = h.solve(d, R, 1e-10, precision="mixed")
+    assert r.nullity == w.nullity
+    check_solution(w, h.basis(), w.nullity, U, 1e-5)
+
+
+def test_full_rank_matrix_has_empty_null_space(ns):
+    w = laplacian_er_components(3, 1, 400, 0.05)  # one connected component: nullity 1
+    h = handle(ns, w, 5)
+    r = h.solve(1, 40, 1e-10)
+    assert r.nullity == 1
+    # shift away the null space: A + I is nonsingular
+    A = (w.A.to_scipy() + sp.identity(w.A.n)).tocsr()
+    h2 = ns.Handle(A.indptr.astype(np.int64), A.indices.astype(np.int32), A.data, A.shape[0], A.shape[1], 5, "spd")
+    r2 = h2.solve(1, 40, 1e-10)
+    assert r2.nullity == 0
+
+
+def test_max_matvec_reports_not_converged(ns):
+    w = laplacian_cycle_components(21, 30000, 15, 8, "powerlaw", 50)
+    h = handle(ns, w, 1001)
+    r = h.solve(1, 120, 1e-10, check=False, max_matvec=200)
+    assert r.status == ns.NS_ERR_NOT_CONVERGED
+
+
+def test_calls_out_of_order_and_bad_sizes(ns):
+    w = laplacian_cycle_components(21, 3000, 3, 8, "powerlaw", 50)
+    h = handle(ns, w, 1)
+    import ctypes
+    N = ctypes.c_int64()
+    assert h.lib.ns_nullity(h.h, ctypes.byref(N)) == ns.NS_ERR_STATE
+    assert h.lib.ns_solve(h.h, 3, 30, 1e-10, None) == ns.NS_ERR_INVALID_ARG
+    assert h.lib.ns_solve(h.h, 2, 31, 1e-10, None) == ns.NS_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_config2_full_size_closed_form(ns, precision):
+    """n = 1e6, 500 components: nullity and the indicator basis (closed form, any size)."""
+    w, p = make_config(2)
+    h = handle(ns, w, 1001)
+    r = h.solve(1, 120, 1e-10, precision=precision)
+    assert r.nullity == 500
+    X = h.basis()
+    U = indicator_basis(w.labels)
+    assert principal_sine(U, X) <= (1e-6 if precision == "fp64" else 1e-5)
+    A = w.A.to_scipy()
+    assert np.linalg.norm(A @ X) / r.stats["normA"] <= 1e-8
