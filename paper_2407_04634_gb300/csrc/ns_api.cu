@@ -9,6 +9,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -83,11 +84,14 @@ void dfree(ns_handle* h, void* p, size_t bytes) {
     cudaFree(p);
 }
 
-void ck(cudaError_t e, const char* what) {
-  if (e != cudaSuccess) throw Fail{NS_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e)};
+void ck_at(cudaError_t e, const char* what, int line) {
+  if (e != cudaSuccess)
+    throw Fail{NS_ERR_CUDA, std::string(what) + " (ns_api.cu:" + std::to_string(line) + "): " + cudaGetErrorString(e)};
 }
+#define ck(e, what) ck_at((e), (what), __LINE__)
 
-void ck_launch(const char* what) { ck(cudaGetLastError(), what); }
+void ck_launch_at(const char* what, int line) { ck_at(cudaGetLastError(), what, line); }
+#define ck_launch(what) ck_launch_at((what), __LINE__)
 
 // RAII device buffer through the handle's allocator
 struct Buf {
@@ -570,6 +574,7 @@ struct Solver {
   }
 
   std::vector<double> pin_theta, pin_res;
+  bool debug = getenv("NS_DEBUG") != nullptr;
 
   // ---- Alg. 2 lines 13-17 + locking + stopping rule; returns true to stop ----
   bool restart(int& k0) {
@@ -651,6 +656,9 @@ struct Solver {
     }
     sv = std::max(sv, (double)R);
     const int64_t since = matvecs - (events.empty() ? 0 : events.back().first);
+    if (debug)
+      fprintf(stderr, "[ns] restart %lld matvecs %lld locked %d small %d unlocked %d k0 %d theta0 %.3e res0 %.3e\n",
+              (long long)restarts, (long long)matvecs, nlock, nsmall, n_unl, nk, pin_theta[0], pin_res[0]);
     if (n_unl == 0 && nlocked_now == 0 && (double)since > o.stop_factor * sv) return true;
     return false;
   }
@@ -724,7 +732,7 @@ RefineOut refine(ns_handle* h, double* X, int64_t N, double normA, const ns_opts
   red.ticket = reinterpret_cast<unsigned*>(sm + 52);
   ck(cudaMemsetAsync(bsm.p, 0, 4096, s), "memset");
   int* nact_h = nullptr;
-  ck(cudaMallocHost(&nact_h, 64), "cudaMallocHost");
+  ck(cudaMallocHost(&nact_h, 256), "cudaMallocHost");
   double* rr_h = reinterpret_cast<double*>(nact_h + 4);
   const double tol2 = (o.refine_tol * normA) * (o.refine_tol * normA);
   for (int64_t c0 = 0; c0 < N; c0 += W) {
