@@ -80,7 +80,9 @@ typedef struct {
   double refine_tol;   /* stop when ||A x|| <= refine_tol * ||A||_2 (default 1e-10)    */
   int refine_maxit;    /* CG / CGLS iteration cap per column (default 500)             */
   int refine_chunk;    /* columns refined together: 8, 16 or 32 (default 16)           */
-  int use_graphs;      /* 1: replay the Lanczos step as a CUDA graph (default 1)       */
+  int use_graphs;      /* reserved, must be 0                                          */
+  int profile;         /* > 0: time every profile-th launch of each kernel class with
+                          CUDA events on the library stream (ns_profile); 0 = off   */
 } ns_opts;
 
 typedef struct {
@@ -98,6 +100,8 @@ typedef struct {
   double normA;          /* ||A||_2 estimate (largest Ritz value of the last T)      */
   double u_d;            /* Eq. (defmprd)                                            */
   double refine_resid_max; /* max_j ||A x_j||_2 / ||A||_2 after refinement           */
+  double orth_before;    /* max |X^T X - I| after refinement, before re-orthonormalizing */
+  double orth_after;     /* same after the symmetric correction (predicted remainder)  */
   double t_lanczos_ms;   /* device time of the Lanczos phase                         */
   double t_refine_ms;    /* device time of the refinement phase                      */
   double t_total_ms;
@@ -143,6 +147,25 @@ ns_status ns_basis(const ns_handle* h, double* out, int64_t ld, int out_on_devic
 
 /* Counters and timings of the last ns_solve. */
 ns_status ns_stats(const ns_handle* h, ns_stats_t* s);
+
+/* Per-kernel-class measurements of the last ns_solve run with opts.profile > 0.
+ * Classes: 0 B-apply (SpMM + recurrence epilogue), 1 recurrence / block QR,
+ * 2 CGS2 projections, 3 restart GEMM, 4 projected eigenproblem, 5 locking,
+ * 6 refinement, 7 re-orthonormalization.  Bytes and flops are algorithmic
+ * (each operand counted once), per launch, averaged over all launches of the
+ * class; ms_per_launch is the mean CUDA-event duration of the sampled launches. */
+typedef struct {
+  char name[24];
+  int64_t launches;
+  int64_t sampled;
+  double ms_per_launch;
+  double bytes_per_launch;
+  double flops_per_launch;
+  double ms_total_est; /* ms_per_launch * launches */
+} ns_kernel_prof;
+
+/* Copies min(max, 8) class records to out; returns the number written in *count. */
+ns_status ns_profile(const ns_handle* h, ns_kernel_prof* out, int max, int* count);
 
 /* Text of the last error on this handle ("" if none; static string for NULL). */
 const char* ns_last_error(const ns_handle* h);

@@ -4,6 +4,9 @@
 #include "ns_common.cuh"
 #include "ns_kernels.cuh"
 
+#include <algorithm>
+#include <vector>
+
 namespace ns {
 
 static int stream_grid(int64_t n, int cap = 152 * 16) {
@@ -766,5 +769,151 @@ template void cg_update2<8>(double*, const double*, int64_t, double*, const doub
                             const Red&, double*, cudaStream_t);
 template void cg_direction2<8>(double*, const double*, const double*, int64_t, cudaStream_t);
 template void refined_to_cols<8>(const double*, const double*, double*, int, int, int64_t, cudaStream_t);
+
+}  // namespace ns
+
+namespace ns {
+
+// ---------------------------------------------------------------------------
+// Gram matrix G = X^T X of an FP64 column-major n x N basis (upper-triangular
+// 32 x 32 tiles, split over row chunks; partials reduced in chunk order)
+// ---------------------------------------------------------------------------
+constexpr int kGT = 32;
+
+__global__ void __launch_bounds__(kThreads) k_gram_tiles(const double* __restrict__ X, int64_t n, int N,
+                                                         int64_t rows_per_chunk, const int2* __restrict__ pairs,
+                                                         double* part) {
+  __shared__ double xa[kGT][kGT + 1];
+  __shared__ double xb[kGT][kGT + 1];
+  const int2 pr = pairs[blockIdx.x];
+  const int ca = pr.x * kGT, cb = pr.y * kGT;
+  const int64_t r0 = (int64_t)blockIdx.y * rows_per_chunk;
+  int64_t r1 = r0 + rows_per_chunk;
+  if (r1 > n) r1 = n;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int64_t base = r0; base < r1; base += kGT) {
+    __syncthreads();
+    for (int t = threadIdx.x; t < kGT * kGT; t += blockDim.x) {
+      const int r = t & 31, c = t >> 5;  // 32 consecutive rows of one column per warp
+      const int64_t i = base + r;
+      xa[r][c] = (i < r1 && ca + c < N) ? X[(int64_t)(ca + c) * n + i] : 0.0;
+      xb[r][c] = (i < r1 && cb + c < N) ? X[(int64_t)(cb + c) * n + i] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int r = 0; r < kGT; ++r) {
+      const double b = xb[r][tx];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] = fma(xa[r][ty + 8 * q], b, acc[q]);
+    }
+  }
+  double* out = part + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * (kGT * kGT);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) out[(ty + 8 * q) * kGT + tx] = acc[q];
+}
+
+__global__ void k_gram_reduce(const double* part, const int2* pairs, int npairs, int nchunks, int N, double* G) {
+  const int64_t total = (int64_t)npairs * kGT * kGT;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int p = (int)(t / (kGT * kGT)), e = (int)(t % (kGT * kGT));
+    double s = 0.0;
+    for (int c = 0; c < nchunks; ++c) s += part[((size_t)c * npairs + p) * (kGT * kGT) + e];
+    const int i = pairs[p].x * kGT + e / kGT, j = pairs[p].y * kGT + e % kGT;
+    if (i < N && j < N) {
+      G[(int64_t)j * N + i] = s;
+      G[(int64_t)i * N + j] = s;
+    }
+  }
+}
+
+size_t gram_part_doubles(int64_t n, int N) {
+  const int nt = (N + kGT - 1) / kGT;
+  const int npairs = nt * (nt + 1) / 2;
+  int nchunks = (int)((152 * 4 + npairs - 1) / npairs);
+  if (nchunks < 1) nchunks = 1;
+  if ((int64_t)nchunks * kGT > n) nchunks = (int)std::max<int64_t>(1, n / kGT);
+  return (size_t)nchunks * npairs * kGT * kGT + 2 * (size_t)npairs;
+}
+
+void gram64(const double* X, int64_t n, int N, double* G, double* part, cudaStream_t s) {
+  const int nt = (N + kGT - 1) / kGT;
+  const int npairs = nt * (nt + 1) / 2;
+  int nchunks = (int)((152 * 4 + npairs - 1) / npairs);
+  if (nchunks < 1) nchunks = 1;
+  if ((int64_t)nchunks * kGT > n) nchunks = (int)std::max<int64_t>(1, n / kGT);
+  int64_t rpc = (n + nchunks - 1) / nchunks;
+  rpc = (rpc + kGT - 1) / kGT * kGT;
+  int2* pairs = reinterpret_cast<int2*>(part + (size_t)nchunks * npairs * kGT * kGT);
+  std::vector<int2> hp;
+  for (int a = 0; a < nt; ++a)
+    for (int b = a; b < nt; ++b) hp.push_back(make_int2(a, b));
+  cudaMemcpyAsync(pairs, hp.data(), sizeof(int2) * hp.size(), cudaMemcpyHostToDevice, s);
+  k_gram_tiles<<<dim3(npairs, nchunks), kThreads, 0, s>>>(X, n, N, rpc, pairs, part);
+  k_gram_reduce<<<stream_grid((int64_t)npairs * kGT * kGT), kThreads, 0, s>>>(part, pairs, npairs, nchunks, N, G);
+}
+
+// ---------------------------------------------------------------------------
+// first-order symmetric (Loewdin) re-orthonormalization:
+//   Xout = X - 0.5 X E,  E = X^T X - I  (|E| small, so the product runs in FP32)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_lowdin(const double* __restrict__ X, int64_t n, int N,
+                                                     const double* __restrict__ G, double* __restrict__ Xout) {
+  __shared__ float xs[kGT][kGT + 1];
+  __shared__ float es[kGT][kGT + 1];
+  const int64_t i0 = (int64_t)blockIdx.x * kGT;
+  const int c0 = blockIdx.y * kGT;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int k0 = 0; k0 < N; k0 += kGT) {
+    __syncthreads();
+    for (int t = threadIdx.x; t < kGT * kGT; t += blockDim.x) {
+      const int r = t & 31, c = t >> 5;
+      const int64_t i = i0 + r;
+      xs[r][c] = (i < n && k0 + c < N) ? (float)X[(int64_t)(k0 + c) * n + i] : 0.f;
+      const int kk = k0 + r, j = c0 + c;  // es[r][c] = E(k0 + r, c0 + c)
+      es[r][c] = (kk < N && j < N) ? (float)(G[(int64_t)j * N + kk] - (kk == j ? 1.0 : 0.0)) : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int k = 0; k < kGT; ++k) {
+      const float e = es[k][tx];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] = fmaf(xs[ty + 8 * q][k], e, acc[q]);
+    }
+  }
+  const int j = c0 + tx;
+  if (j < N) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int64_t i = i0 + ty + 8 * q;
+      if (i < n) Xout[(int64_t)j * n + i] = X[(int64_t)j * n + i] - 0.5 * (double)acc[q];
+    }
+  }
+}
+
+void lowdin_update(const double* X, int64_t n, int N, const double* G, double* Xout, cudaStream_t s) {
+  dim3 grid(ceil_div(n, kGT), ceil_div(N, kGT));
+  k_lowdin<<<grid, kThreads, 0, s>>>(X, n, N, G, Xout);
+}
+
+// max_ij |G_ij - delta_ij| (one block)
+__global__ void k_max_offdiag(const double* G, int N, double* out) {
+  __shared__ double red_s[kThreads / 32];
+  double m = 0.0;
+  for (int64_t t = threadIdx.x; t < (int64_t)N * N; t += blockDim.x) {
+    const int i = (int)(t % N), j = (int)(t / N);
+    m = fmax(m, fabs(G[t] - (i == j ? 1.0 : 0.0)));
+  }
+  m = warp_max(m);
+  if ((threadIdx.x & 31) == 0) red_s[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = fmax(t, red_s[w]);
+    *out = t;
+  }
+}
+void max_offdiag(const double* G, int N, double* out, cudaStream_t s) { k_max_offdiag<<<1, kThreads, 0, s>>>(G, N, out); }
 
 }  // namespace ns

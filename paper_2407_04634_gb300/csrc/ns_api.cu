@@ -20,6 +20,78 @@
 
 using namespace ns;
 
+// Sampling profiler: every `every`-th launch of each kernel class is bracketed
+// by CUDA events on the library stream; algorithmic bytes / flops of every
+// launch are accumulated from the operand sizes.
+struct Prof {
+  static constexpr int NC = 8;
+  int every = 0;
+  cudaStream_t s = nullptr;
+  long long units[NC] = {}, sampled[NC] = {}, counter[NC] = {};
+  double ms[NC] = {}, bytes[NC] = {}, flops[NC] = {};
+  struct Pend {
+    int c;
+    cudaEvent_t a, b;
+  };
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  std::vector<Pend> pend;
+  void reset(int e, cudaStream_t st) {
+    every = e;
+    s = st;
+    for (int c = 0; c < NC; ++c) units[c] = sampled[c] = counter[c] = 0, ms[c] = bytes[c] = flops[c] = 0.0;
+    pend.clear();
+    used = 0;
+  }
+  cudaEvent_t ev() {
+    if (used == pool.size()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      pool.push_back(e);
+    }
+    return pool[used++];
+  }
+  int begin(int c, double by, double fl) {
+    units[c] += 1;
+    bytes[c] += by;
+    flops[c] += fl;
+    if (every <= 0 || (counter[c]++ % every) != 0) return -1;
+    Pend p{c, ev(), ev()};
+    cudaEventRecord(p.a, s);
+    pend.push_back(p);
+    return (int)pend.size() - 1;
+  }
+  void end(int tok) {
+    if (tok >= 0) cudaEventRecord(pend[tok].b, s);
+  }
+  void flush() {  // call after the stream was synchronized
+    for (auto& p : pend) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, p.a, p.b) == cudaSuccess) {
+        ms[p.c] += t;
+        sampled[p.c] += 1;
+      }
+    }
+    cudaGetLastError();
+    pend.clear();
+    used = 0;
+  }
+  ~Prof() {
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+
+struct PScope {
+  Prof* p;
+  int tok;
+  PScope(Prof* pp, int c, double by, double fl) : p(pp), tok(pp->begin(c, by, fl)) {}
+  ~PScope() { p->end(tok); }
+};
+
+enum { P_APPLY = 0, P_REC = 1, P_PROJ = 2, P_GEMM = 3, P_EIG = 4, P_LOCK = 5, P_REFINE = 6, P_ORTH = 7 };
+static const char* kProfNames[Prof::NC] = {"b_apply", "recurrence_qr", "cgs2_project", "restart_gemm",
+                                           "projected_eig", "locking", "refine", "reorthonormalize"};
+
 struct ns_handle {
   ns_env env{};
   bool own_alloc = true;
@@ -48,6 +120,7 @@ struct ns_handle {
   size_t basis_bytes = 0;
   ns_stats_t stats{};
   long long launches = 0;
+  Prof prof;
 };
 
 // ---------------------------------------------------------------------------
@@ -337,7 +410,10 @@ struct Solver {
   T* X() const { return xbuf.as<T>(); }
   T* blk(int which, int b) const { return Z[which] + (size_t)b * n * D; }
 
-  void sync() { ck(cudaStreamSynchronize(s), "stream sync"); }
+  void sync() {
+    ck(cudaStreamSynchronize(s), "stream sync");
+    h->prof.flush();
+  }
 
   unsigned read_flags() {
     ck(cudaMemcpyAsync(flags_h, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s), "d2h flags");
@@ -357,6 +433,14 @@ struct Solver {
     op.out = qp.as<T>();
     op.xi = xi;
     op.xi_norm = xi_norm;
+    const double sv = sizeof(T);
+    double by = (double)h->nnz * (4 + sv) + (n + 1) * 8.0 + n * (3.0 * D + 1.0) * sv + (qprev ? n * D * sv : 0.0);
+    double fl = 2.0 * h->nnz * D + 2.0 * n * D + 2.0 * n * D * D * (qprev ? 2 : 1);
+    if (h->mode == NS_MODE_NORMAL) {
+      by += (double)h->nnz * (4 + sv) + (m + 1) * 8.0 + 2.0 * m * D * sv;
+      fl += 2.0 * h->nnz * D;
+    }
+    PScope ps(&h->prof, P_APPLY, by, fl);
     if (h->mode == NS_MODE_SPD) {
       spmm_lanczos<T, D>(A, x, op, red, s);
       launches += 1;
@@ -386,6 +470,8 @@ struct Solver {
     }
     if ((size_t)(V.kx + V.kz) * W * sizeof(T) > 190 * 1024)
       throw Fail{NS_ERR_INVALID_ARG, "projection basis too wide for one pass"};
+    const double K = V.kx + V.kz, sv = sizeof(T);
+    PScope ps(&h->prof, P_PROJ, 2.0 * (2.0 * K * n * sv + 3.0 * n * W * sv), 8.0 * K * n * W);
     for (int pass = 0; pass < 2; ++pass) {
       proj_dots<T, W>(V, Wp, ldw, n, cbuf.as<double>(), dpart.as<double>(), s);
       proj_update<T, W>(V, cbuf.as<double>(), Wp, ldw, n, (pass == 1 && gram) ? 1 : 0, Rout, gd, flags, red, s);
@@ -487,12 +573,15 @@ struct Solver {
     T* q = blk(cur, j);
     T* qn = blk(cur, j + 1);
     apply_step(q, blk(cur, j - 1), Gam + (size_t)(j - 1) * D * D, Xi + (size_t)j * D * D, nXi + j);
-    axpy_gram<T, D>(qp.as<T>(), q, Xi + (size_t)j * D * D, n, R1, flags, red, s);
-    scale_gram<T, D>(qp.as<T>(), D, qn, D, R1, n, R2, flags, red, s, D);
-    OmegaArgs a = omega_args(j, r0);
-    if (o.reorth == NS_REORTH_FULL) a.u_ro = -1.0;  // every column triggers
-    step_finalize(a, s);
-    scale_gram<T, D>(qn, D, qn, D, R2, n, nullptr, flags, red, s, D);
+    {
+      PScope ps(&h->prof, P_REC, 7.0 * n * D * sizeof(T), 8.0 * n * D * D);
+      axpy_gram<T, D>(qp.as<T>(), q, Xi + (size_t)j * D * D, n, R1, flags, red, s);
+      scale_gram<T, D>(qp.as<T>(), D, qn, D, R1, n, R2, flags, red, s, D);
+      OmegaArgs a = omega_args(j, r0);
+      if (o.reorth == NS_REORTH_FULL) a.u_ro = -1.0;  // every column triggers
+      step_finalize(a, s);
+      scale_gram<T, D>(qn, D, qn, D, R2, n, nullptr, flags, red, s, D);
+    }
     launches += 4;
     const unsigned f = read_flags();
     if (f) clear_flags();
@@ -579,9 +668,12 @@ struct Solver {
   // ---- Alg. 2 lines 13-17 + locking + stopping rule; returns true to stop ----
   bool restart(int& k0) {
     const int r0 = k0 / D;
-    build_T(Theta, F, Xi, Gam, k0, D, R, Tm, s);
-    syev(Tm, R, theta, VZ, syw, s);
-    ritz_resid(Gam + (size_t)(nb - 1) * D * D, VZ, D, R, resid, s);
+    {
+      PScope ps(&h->prof, P_EIG, 8.0 * 4 * R * R, 9.0 * R * R * R);
+      build_T(Theta, F, Xi, Gam, k0, D, R, Tm, s);
+      syev(Tm, R, theta, VZ, syw, s);
+      ritz_resid(Gam + (size_t)(nb - 1) * D * D, VZ, D, R, resid, s);
+    }
     launches += 4;
     (void)r0;
     ck(cudaMemcpyAsync(pin_d, theta, sizeof(double) * R, cudaMemcpyDeviceToHost, s), "d2h");
@@ -603,10 +695,20 @@ struct Solver {
     int nlocked_now = 0;
     if (!cand.empty()) {
       ck(cudaMemcpyAsync(sel, cand.data(), sizeof(int) * cand.size(), cudaMemcpyHostToDevice, s), "h2d");
-      restart_gemm<T>(Z[cur], D, R, VZ, sel, (int)cand.size(), (int)cand.size(), n, lnew.as<T>(), nullptr, s);
+      {
+        const double nc = (double)cand.size();
+        PScope ps(&h->prof, P_GEMM, (double)n * (R + nc) * sizeof(T), 2.0 * n * R * nc);
+        restart_gemm<T>(Z[cur], D, R, VZ, sel, (int)cand.size(), (int)cand.size(), n, lnew.as<T>(), nullptr, s);
+      }
       launches += 1;
       const int before = nlock;
-      const int ng = lock_new((int)cand.size(), cand, is_ghost);
+      int ng = 0;
+      {
+        const double nc = (double)cand.size();
+        PScope ps(&h->prof, P_LOCK, 4.0 * nlock * n * sizeof(T) * ((nc + 7) / 8) + 6.0 * n * nc * sizeof(T),
+                  8.0 * nlock * n * nc + 8.0 * n * nc * 8);
+        ng = lock_new((int)cand.size(), cand, is_ghost);
+      }
       ghosts += ng;
       nlocked_now = nlock - before;
       if (nlocked_now > 0) {
@@ -625,7 +727,10 @@ struct Solver {
     nk = std::min(nk, D * ((int)avail.size() / D));
     const int other = 1 - cur;
     ck(cudaMemcpyAsync(sel, avail.data(), sizeof(int) * nk, cudaMemcpyHostToDevice, s), "h2d");
-    restart_gemm<T>(Z[cur], D, R, VZ, sel, nk, 0, n, nullptr, Z[other], s);
+    {
+      PScope ps(&h->prof, P_GEMM, (double)n * (R + nk) * sizeof(T), 2.0 * n * R * nk);
+      restart_gemm<T>(Z[cur], D, R, VZ, sel, nk, 0, n, nullptr, Z[other], s);
+    }
     launches += 1;
     // Alg. 2 line 16: Q_{l+1} against [X, Z_new], moved to block nk/D of the new buffer
     T* qlast = blk(cur, nb);
@@ -815,6 +920,7 @@ static ns_status solve_typed(ns_handle* h, int R, double tol, const ns_opts& o) 
   ns_status st = NS_OK;
   bool conv = false;
   int64_t N = 0;
+  h->prof.reset(o.profile, s);
   Solver<T, D> S(h, R, tol, o);
   cudaEventRecord(e0, s);
   st = S.run(conv);
@@ -833,11 +939,54 @@ static ns_status solve_typed(ns_handle* h, int R, double tol, const ns_opts& o) 
   double normA = (h->mode == NS_MODE_NORMAL) ? std::sqrt(std::max(S.theta_max, 0.0)) : S.theta_max;
   RefineOut ro;
   if (o.refine && N) {
-    ro = refine(h, h->basis, N, normA, o);
+    {
+      PScope ps(&h->prof, P_REFINE, 0.0, 0.0);
+      ro = refine(h, h->basis, N, normA, o);
+    }
+    ck(cudaStreamSynchronize(s), "sync");
+    h->prof.flush();
     if (ro.failed && st == NS_OK) st = NS_ERR_REFINE;
+  }
+  // Projecting B-eigenvectors onto null(A) removes an O(eps/sigma) component from
+  // each, so the refined basis is orthonormal only to O(eps^2/sigma^2); a
+  // symmetric (Loewdin) correction X <- X (I - E/2), E = X^T X - I, restores it.
+  double orth0 = 0.0, orth1 = 0.0;
+  if (N) {
+    Buf G(h, sizeof(double) * (size_t)N * N), part(h, sizeof(double) * gram_part_doubles(h->n, (int)N)),
+        mx(h, 256);
+    double* X2 = (double*)dalloc(h, h->basis_bytes);
+    double* mx_h = nullptr;
+    ck(cudaMallocHost(&mx_h, 64), "cudaMallocHost");
+    for (int it = 0; it < 4; ++it) {
+      {
+        PScope ps(&h->prof, P_ORTH, 8.0 * N * h->n, 1.0 * N * N * h->n);
+        gram64(h->basis, h->n, (int)N, G.as<double>(), part.as<double>(), s);
+        max_offdiag(G.as<double>(), (int)N, mx.as<double>(), s);
+      }
+      h->launches += 3;
+      ck(cudaMemcpyAsync(mx_h, mx.p, sizeof(double), cudaMemcpyDeviceToHost, s), "d2h orth");
+      ck(cudaStreamSynchronize(s), "sync");
+      h->prof.flush();
+      if (it == 0) orth0 = *mx_h;
+      orth1 = *mx_h;
+      if (*mx_h <= 1e-14) break;
+      {
+        PScope ps(&h->prof, P_ORTH, 16.0 * N * h->n, 2.0 * N * N * h->n);
+        lowdin_update(h->basis, h->n, (int)N, G.as<double>(), X2, s);
+      }
+      h->launches += 1;
+      std::swap(h->basis, X2);
+      orth1 = 0.375 * (*mx_h) * (*mx_h) * N;  // predicted second-order remainder
+      if (*mx_h <= 1e-6) break;
+    }
+    ck(cudaStreamSynchronize(s), "sync");
+    ck_launch("reorthonormalize");
+    cudaFreeHost(mx_h);
+    dfree(h, X2, h->basis_bytes);
   }
   cudaEventRecord(e2, s);
   ck(cudaEventSynchronize(e2), "sync");
+  h->prof.flush();
   float t1 = 0.f, t2 = 0.f;
   cudaEventElapsedTime(&t1, e0, e1);
   cudaEventElapsedTime(&t2, e1, e2);
@@ -858,6 +1007,8 @@ static ns_status solve_typed(ns_handle* h, int R, double tol, const ns_opts& o) 
   x.normA = normA;
   x.u_d = S.u_d;
   x.refine_resid_max = ro.resid_max;
+  x.orth_before = orth0;
+  x.orth_after = orth1;
   x.t_lanczos_ms = t1;
   x.t_refine_ms = t2;
   x.t_total_ms = t1 + t2;
@@ -953,6 +1104,7 @@ void ns_default_opts(ns_opts* o) {
   o->refine_maxit = 500;
   o->refine_chunk = 8;
   o->use_graphs = 0;
+  o->profile = 0;
 }
 
 static ns_status set_err(ns_handle* h, ns_status st, const std::string& msg) {
@@ -1145,6 +1297,26 @@ ns_status ns_stats(const ns_handle* h, ns_stats_t* s) {
   if (!h || !s) return NS_ERR_INVALID_ARG;
   if (!h->solved) return NS_ERR_STATE;
   *s = h->stats;
+  return NS_OK;
+}
+
+ns_status ns_profile(const ns_handle* h, ns_kernel_prof* out, int max, int* count) {
+  if (!h || !out || !count) return NS_ERR_INVALID_ARG;
+  if (!h->solved) return NS_ERR_STATE;
+  const Prof& p = h->prof;
+  int k = 0;
+  for (int c = 0; c < Prof::NC && k < max; ++c, ++k) {
+    ns_kernel_prof& r = out[k];
+    std::memset(&r, 0, sizeof(r));
+    std::snprintf(r.name, sizeof(r.name), "%s", kProfNames[c]);
+    r.launches = p.units[c];
+    r.sampled = p.sampled[c];
+    r.ms_per_launch = p.sampled[c] ? p.ms[c] / (double)p.sampled[c] : 0.0;
+    r.bytes_per_launch = p.units[c] ? p.bytes[c] / (double)p.units[c] : 0.0;
+    r.flops_per_launch = p.units[c] ? p.flops[c] / (double)p.units[c] : 0.0;
+    r.ms_total_est = r.ms_per_launch * (double)p.units[c];
+  }
+  *count = k;
   return NS_OK;
 }
 

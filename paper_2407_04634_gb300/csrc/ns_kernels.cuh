@@ -179,3 +179,14 @@ template <int W>
 void refined_to_cols(const double* P, const double* Dl, double* X, int c0, int w, int64_t n, cudaStream_t s);
 
 }  // namespace ns
+
+namespace ns {
+// ---- re-orthonormalization of the refined FP64 basis (k_dense.cu) ----
+size_t gram_part_doubles(int64_t n, int N);
+// G = X^T X (X column-major n x N FP64); part needs gram_part_doubles(n, N) doubles
+void gram64(const double* X, int64_t n, int N, double* G, double* part, cudaStream_t s);
+// Xout = X - 0.5 X (G - I)
+void lowdin_update(const double* X, int64_t n, int N, const double* G, double* Xout, cudaStream_t s);
+// *out = max |G - I|
+void max_offdiag(const double* G, int N, double* out, cudaStream_t s);
+}  // namespace ns

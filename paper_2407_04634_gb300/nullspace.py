@@ -35,14 +35,14 @@ class NsOpts(C.Structure):
     _fields_ = [("eps", C.c_double), ("precision", C.c_int), ("reorth", C.c_int), ("max_matvec", C.c_int64),
                 ("stop_factor", C.c_double), ("lock_tol_mixed", C.c_double), ("refine", C.c_int),
                 ("refine_tol", C.c_double), ("refine_maxit", C.c_int), ("refine_chunk", C.c_int),
-                ("use_graphs", C.c_int)]
+                ("use_graphs", C.c_int), ("profile", C.c_int)]
 
 
 class NsStats(C.Structure):
     _fields_ = [("nullity", C.c_int64), ("matvecs", C.c_int64), ("restarts", C.c_int64), ("reorth_X", C.c_int64),
                 ("reorth_Z", C.c_int64), ("breakdowns", C.c_int64), ("lock_events", C.c_int64),
                 ("ghosts", C.c_int64), ("refine_iters_max", C.c_int64), ("kernel_launches", C.c_int64),
-                ("normB", C.c_double), ("normA", C.c_double), ("u_d", C.c_double), ("refine_resid_max", C.c_double),
+                ("normB", C.c_double), ("normA", C.c_double), ("u_d", C.c_double), ("refine_resid_max", C.c_double), ("orth_before", C.c_double), ("orth_after", C.c_double),
                 ("t_lanczos_ms", C.c_double), ("t_refine_ms", C.c_double), ("t_total_ms", C.c_double)]
 
     def as_dict(self):
@@ -50,6 +50,12 @@ class NsStats(C.Structure):
 
 
 # exported symbols and their prototypes (kept in sync with include/nullspace.h)
+class NsKernelProf(C.Structure):
+    _fields_ = [("name", C.c_char * 24), ("launches", C.c_int64), ("sampled", C.c_int64),
+                ("ms_per_launch", C.c_double), ("bytes_per_launch", C.c_double), ("flops_per_launch", C.c_double),
+                ("ms_total_est", C.c_double)]
+
+
 _P = C.c_void_p
 SIGNATURES = {
     "ns_default_opts": (None, [C.POINTER(NsOpts)]),
@@ -59,6 +65,7 @@ SIGNATURES = {
     "ns_nullity": (C.c_int, [_P, C.POINTER(C.c_int64)]),
     "ns_basis": (C.c_int, [_P, _P, C.c_int64, C.c_int]),
     "ns_stats": (C.c_int, [_P, C.POINTER(NsStats)]),
+    "ns_profile": (C.c_int, [_P, C.POINTER(NsKernelProf), C.c_int, C.POINTER(C.c_int)]),
     "ns_last_error": (C.c_char_p, [_P]),
     "ns_destroy": (None, [_P]),
     "ns_get_transpose": (C.c_int, [_P, _P, _P, _P]),
@@ -197,6 +204,18 @@ class Handle:
         s = NsStats()
         self._check(self.lib.ns_stats(self.h, C.byref(s)), "ns_stats")
         return s.as_dict()
+
+    def profile(self) -> list[dict]:
+        """Per-kernel-class CUDA-event measurements of the last solve (opts profile > 0)."""
+        arr = (NsKernelProf * 8)()
+        cnt = C.c_int()
+        self._check(self.lib.ns_profile(self.h, arr, 8, C.byref(cnt)), "ns_profile")
+        out = []
+        for r in arr[:cnt.value]:
+            out.append(dict(name=r.name.decode(), launches=r.launches, sampled=r.sampled,
+                            ms_per_launch=r.ms_per_launch, bytes_per_launch=r.bytes_per_launch,
+                            flops_per_launch=r.flops_per_launch, ms_total_est=r.ms_total_est))
+        return out
 
     def transpose(self, nnz: int):
         rp = np.zeros(self.n + 1, dtype=np.int64)
