@@ -664,6 +664,7 @@ struct Solver {
 
   std::vector<double> pin_theta, pin_res;
   bool debug = getenv("NS_DEBUG") != nullptr;
+  std::chrono::steady_clock::time_point t_start = std::chrono::steady_clock::now();
 
   // ---- Alg. 2 lines 13-17 + locking + stopping rule; returns true to stop ----
   bool restart(int& k0) {
@@ -761,9 +762,16 @@ struct Solver {
     }
     sv = std::max(sv, (double)R);
     const int64_t since = matvecs - (events.empty() ? 0 : events.back().first);
-    if (debug)
-      fprintf(stderr, "[ns] restart %lld matvecs %lld locked %d small %d unlocked %d k0 %d theta0 %.3e res0 %.3e\n",
-              (long long)restarts, (long long)matvecs, nlock, nsmall, n_unl, nk, pin_theta[0], pin_res[0]);
+    if (debug) {
+      long long cnt[4] = {0, 0, 0, 0};
+      cudaMemcpy(cnt, counters, sizeof(cnt), cudaMemcpyDeviceToHost);
+      const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+      fprintf(stderr,
+              "[ns] %.3fs restart %lld matvecs %lld locked %d small %d unlocked %d k0 %d theta0 %.3e res0 %.3e "
+              "reorthZ %lld reorthX %lld\n",
+              el, (long long)restarts, (long long)matvecs, nlock, nsmall, n_unl, nk, pin_theta[0], pin_res[0], cnt[0],
+              cnt[1]);
+    }
     if (n_unl == 0 && nlocked_now == 0 && (double)since > o.stop_factor * sv) return true;
     return false;
   }
