@@ -43,6 +43,11 @@ Readings of points the paper leaves open (each is also listed in the design doc):
       the rows that were reorthogonalized are reset to u_d;
   R7  retained count l0 d = d * floor((N_unlocked + dimK) / (2d)) clamped to
       [d, dimK - 2d] (Alg. 2 line 14 counted in vectors);
+  R7b when the nullity exceeds dimK the unconverged near-null Ritz pairs fill the
+      basis and that rule leaves almost no room for new vectors; the retained
+      count is therefore capped at dimK/2, and among the Ritz values below 3 eps
+      the pairs with the smallest residuals are kept first (keep_rule="capped",
+      default; "paper" keeps the l0 d smallest as printed);
   R8  after restart F = R Gamma_l V_Z(last block, kept) where R is the factor of the
       re-orthogonalization QR of Q_{l+1} (Alg. 2 line 17, printed index garbled);
   R9  ||B|| in u_d is the bound ||A||_1 ||A||_inf + eps (normal) or ||A||_inf + eps (spd);
@@ -153,7 +158,7 @@ def lanczos_nullspace(A, mode: str, d: int, restart_len: int, tol: float = 1e-10
                       refine_maxit: int = 500, final_rr: bool = True,
                       u: float = U_FP64, D: np.ndarray | None = None,
                       Omega: np.ndarray | None = None, record: bool = False,
-                      probe=None) -> Result:
+                      probe=None, keep_rule: str = "capped") -> Result:
     """Null space of A by Alg. 2 (restarted, partially reorthogonalized small-block Lanczos).
 
     reorth: "partial" (Sec. 4.2), "full" (every new block projected against the whole
@@ -345,6 +350,11 @@ def lanczos_nullspace(A, mode: str, d: int, restart_len: int, tol: float = 1e-10
         avail = np.nonzero(~taken)[0]
         k0 = d * ((n_unl + R) // (2 * d))
         k0 = min(max(k0, d), R - 2 * d, d * (avail.size // d))
+        if keep_rule == "capped":  # reading R7b: room for >= dimK/2 new vectors per cycle
+            k0 = min(k0, max(d, d * (R // (2 * d))))
+            sm = avail[small[avail]]
+            sm = sm[np.argsort(resid[sm], kind="stable")]  # most converged small pairs first
+            avail = np.concatenate([sm, avail[~small[avail]]])
         keep = avail[:k0]
         Znew = Z[:, :R] @ VZ[:, keep]
         q = project(Z[:, R:R + d], [X, Znew])

@@ -726,6 +726,17 @@ struct Solver {
     nk = std::max(nk, D);
     nk = std::min(nk, R - 2 * D);
     nk = std::min(nk, D * ((int)avail.size() / D));
+    // at most dimK/2 retained pairs, so every cycle adds >= dimK/2 new vectors; the
+    // most converged small pairs are kept first (any subset of Ritz pairs keeps the
+    // Krylov-Schur decomposition exact)
+    nk = std::min(nk, std::max(D, D * (R / (2 * D))));
+    {
+      std::vector<int> sm, rest;
+      for (int i : avail) (pin_theta[i] < 3.0 * eps ? sm : rest).push_back(i);
+      std::stable_sort(sm.begin(), sm.end(), [&](int a, int b) { return pin_res[a] < pin_res[b]; });
+      avail = sm;
+      avail.insert(avail.end(), rest.begin(), rest.end());
+    }
     const int other = 1 - cur;
     ck(cudaMemcpyAsync(sel, avail.data(), sizeof(int) * nk, cudaMemcpyHostToDevice, s), "h2d");
     {
