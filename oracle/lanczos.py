@@ -289,10 +289,10 @@ def lanczos_nullspace(A, mode: str, d: int, restart_len: int, tol: float = 1e-10
             trig_Z = bool(np.any(newcol[:j + 1] > u_ro))
             trig_X = bool(np.any(newX > u_ro))
             if trig_Z or trig_X:
+                # Sec. 4.2: Q_l and Q_{l+1} versus Z_{l-1} (and the locked vectors)
                 partsj = ([X] if trig_X else []) + ([Z[:, :j * d]] if trig_Z else [])
                 Z[:, j * d:(j + 1) * d], _ = qr_pos(project(blk(j), partsj))
-                partsj1 = ([X] if trig_X else []) + ([Z[:, :(j + 1) * d]] if trig_Z else [])
-                Z[:, (j + 1) * d:(j + 2) * d], _ = qr_pos(project(blk(j + 1), partsj1))
+                Z[:, (j + 1) * d:(j + 2) * d], _ = qr_pos(project(blk(j + 1), partsj))
                 if trig_Z:
                     st["reorth_Z"] += 1
                     W[:j, j] = u_d

@@ -220,40 +220,80 @@ NS_INST_QR(float, 4)
 NS_INST_QR(float, 8)
 
 // ---------------------------------------------------------------------------
-// projections against V = [X | Z]  (classical Gram-Schmidt; called twice = CGS2)
+// projections against V = [X | Z] (classical Gram-Schmidt; CGS2 = two calls)
+// W is a row-major panel of width W (leading dimension ldw); when Wp2 is given,
+// columns [W/2, W) come from the second panel (two adjacent Lanczos blocks).
+// Z holds panels of width P, so the column -> address map needs no division.
 // ---------------------------------------------------------------------------
-template <typename T>
-__device__ __forceinline__ T v_at(const VParts<T>& V, int64_t n, int64_t i, int k) {
-  if (k < V.kx) return V.X[(int64_t)k * n + i];
-  const int kz = k - V.kx;
-  return V.Z[(int64_t)(kz / V.p) * n * V.p + i * V.p + (kz % V.p)];
+constexpr int kKT = 8;  // V columns per dots tile (a multiple of every P)
+
+template <typename T, int W>
+__device__ __forceinline__ void load_w(const T* Wp, const T* Wp2, int64_t ldw, int64_t i, T (&w)[W]) {
+  if (Wp2 == nullptr) {
+#pragma unroll
+    for (int c = 0; c < W; ++c) w[c] = Wp[i * ldw + c];
+  } else {
+#pragma unroll
+    for (int c = 0; c < W / 2; ++c) {
+      w[c] = Wp[i * ldw + c];
+      w[W / 2 + c] = Wp2[i * ldw + c];
+    }
+  }
 }
 
-constexpr int kKT = 8;  // V columns per dots tile
+template <typename T, int W>
+__device__ __forceinline__ void store_w(T* Wp, T* Wp2, int64_t ldw, int64_t i, const T (&w)[W]) {
+  if (Wp2 == nullptr) {
+#pragma unroll
+    for (int c = 0; c < W; ++c) Wp[i * ldw + c] = w[c];
+  } else {
+#pragma unroll
+    for (int c = 0; c < W / 2; ++c) {
+      Wp[i * ldw + c] = w[c];
+      Wp2[i * ldw + c] = w[W / 2 + c];
+    }
+  }
+}
 
 // part[chunk][k][c] = sum over the rows of the chunk of V[i,k] W[i,c]
-template <typename T, int W>
-__global__ void __launch_bounds__(kThreads) k_proj_dots(VParts<T> V, const T* __restrict__ Wp, int64_t ldw,
-                                                        int64_t n, int64_t rows_per_chunk, double* part) {
+template <typename T, int W, int P>
+__global__ void __launch_bounds__(kThreads) k_proj_dots(VParts<T> V, const T* __restrict__ Wp,
+                                                        const T* __restrict__ Wp2, int64_t ldw, int64_t n,
+                                                        int64_t rows_per_chunk, double* part) {
   constexpr int NP = kKT * W;
   __shared__ double red_s[(kThreads / 32) * NP];
   __shared__ double tot[NP];
   const int K = V.kx + V.kz;
-  const int k0 = blockIdx.y * kKT;
+  const int tilesX = (V.kx + kKT - 1) / kKT;
+  const bool isX = (int)blockIdx.y < tilesX;
+  const int k0 = isX ? blockIdx.y * kKT : V.kx + (blockIdx.y - tilesX) * kKT;  // first global column
+  const int kend = isX ? V.kx : K;
   const int64_t r0 = (int64_t)blockIdx.x * rows_per_chunk;
   int64_t r1 = r0 + rows_per_chunk;
   if (r1 > n) r1 = n;
   T acc[NP];
 #pragma unroll
   for (int k = 0; k < NP; ++k) acc[k] = T(0);
+  // column base pointers of this tile (element i of column kk at base[kk] + i * stride)
+  const T* base[kKT];
+  int64_t stride = 1;
+#pragma unroll
+  for (int kk = 0; kk < kKT; ++kk) {
+    const int k = k0 + kk;
+    if (isX) {
+      base[kk] = V.X + (int64_t)(k < kend ? k : 0) * n;
+    } else {
+      const int kz = (k < kend ? k : V.kx) - V.kx;
+      base[kk] = V.Z + (int64_t)(kz / P) * n * P + (kz % P);
+    }
+  }
+  if (!isX) stride = P;
   for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
     T w[W];
-#pragma unroll
-    for (int c = 0; c < W; ++c) w[c] = Wp[i * ldw + c];
+    load_w<T, W>(Wp, Wp2, ldw, i, w);
 #pragma unroll
     for (int kk = 0; kk < kKT; ++kk) {
-      const int k = k0 + kk;
-      const T v = (k < K) ? v_at(V, n, i, k) : T(0);
+      const T v = (k0 + kk < kend) ? base[kk][i * stride] : T(0);
 #pragma unroll
       for (int c = 0; c < W; ++c) acc[kk * W + c] = fma(v, w[c], acc[kk * W + c]);
     }
@@ -264,7 +304,7 @@ __global__ void __launch_bounds__(kThreads) k_proj_dots(VParts<T> V, const T* __
   block_sum<NP>(pd, red_s, tot);
   for (int t = threadIdx.x; t < NP; t += blockDim.x) {
     const int k = k0 + t / W;
-    if (k < K) part[((size_t)blockIdx.x * K + k) * W + (t % W)] = tot[t];
+    if (k < kend) part[((size_t)blockIdx.x * K + k) * W + (t % W)] = tot[t];
   }
 }
 
@@ -283,22 +323,34 @@ static int64_t dots_rows_per_chunk(int64_t n) {
   return r;
 }
 
+#define NS_P_SWITCH(P, CALL) \
+  switch (P) {               \
+    case 1: CALL(1); break;  \
+    case 2: CALL(2); break;  \
+    case 4: CALL(4); break;  \
+    default: CALL(8); break; \
+  }
+
 template <typename T, int W>
-void proj_dots(const VParts<T>& V, const T* Wp, int64_t ldw, int64_t n, double* C, double* part, cudaStream_t s) {
+void proj_dots(const VParts<T>& V, const T* Wp, const T* Wp2, int64_t ldw, int64_t n, double* C, double* part,
+               cudaStream_t s) {
   const int K = V.kx + V.kz;
   if (K == 0) return;
   const int64_t rpc = dots_rows_per_chunk(n);
   const int nchunks = ceil_div(n, rpc);
-  dim3 grid(nchunks, ceil_div(K, kKT));
-  k_proj_dots<T, W><<<grid, kThreads, 0, s>>>(V, Wp, ldw, n, rpc, part);
+  dim3 grid(nchunks, ceil_div(V.kx, kKT) + ceil_div(V.kz, kKT));
+#define CALL(PP) k_proj_dots<T, W, PP><<<grid, kThreads, 0, s>>>(V, Wp, Wp2, ldw, n, rpc, part)
+  NS_P_SWITCH(V.p, CALL)
+#undef CALL
   k_dots_reduce<<<ceil_div((int64_t)K * W, kThreads), kThreads, 0, s>>>(part, nchunks, K * W, C);
 }
 
 // W -= V C (C: K x W row-major FP64, staged in dynamic shared memory) ; optional Gram + Cholesky
-template <typename T, int W>
+template <typename T, int W, int P>
 __global__ void __launch_bounds__(kThreads) k_proj_update(VParts<T> V, const double* __restrict__ C,
-                                                          T* __restrict__ Wp, int64_t ldw, int64_t n, int gram,
-                                                          double* R, double* gdiag, unsigned* flags, Red red) {
+                                                          T* __restrict__ Wp, T* __restrict__ Wp2, int64_t ldw,
+                                                          int64_t n, int gram, double* R, double* gdiag,
+                                                          unsigned* flags, Red red) {
   constexpr int NP = W * W;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* c_s = reinterpret_cast<T*>(smem_raw);
@@ -310,23 +362,26 @@ __global__ void __launch_bounds__(kThreads) k_proj_update(VParts<T> V, const dou
   T part[NP];
 #pragma unroll
   for (int k = 0; k < NP; ++k) part[k] = T(0);
+  const int nzp = V.kz / P;  // whole panels of Z
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     T w[W];
-#pragma unroll
-    for (int c = 0; c < W; ++c) w[c] = Wp[i * ldw + c];
+    load_w<T, W>(Wp, Wp2, ldw, i, w);
     for (int k = 0; k < V.kx; ++k) {
       const T v = V.X[(int64_t)k * n + i];
 #pragma unroll
       for (int c = 0; c < W; ++c) w[c] = fma(-v, c_s[k * W + c], w[c]);
     }
-    for (int kz = 0; kz < V.kz; ++kz) {
-      const T v = V.Z[(int64_t)(kz / V.p) * n * V.p + i * V.p + (kz % V.p)];
-      const int k = V.kx + kz;
+    for (int b = 0; b < nzp; ++b) {
+      T zr[P];
+      load_row<T, P>(V.Z + (int64_t)b * n * P + i * P, zr);
 #pragma unroll
-      for (int c = 0; c < W; ++c) w[c] = fma(-v, c_s[k * W + c], w[c]);
+      for (int q = 0; q < P; ++q) {
+        const int k = V.kx + b * P + q;
+#pragma unroll
+        for (int c = 0; c < W; ++c) w[c] = fma(-zr[q], c_s[k * W + c], w[c]);
+      }
     }
-#pragma unroll
-    for (int c = 0; c < W; ++c) Wp[i * ldw + c] = w[c];
+    store_w<T, W>(Wp, Wp2, ldw, i, w);
     if (gram) {
 #pragma unroll
       for (int p = 0; p < W; ++p)
@@ -345,30 +400,39 @@ __global__ void __launch_bounds__(kThreads) k_proj_update(VParts<T> V, const dou
 }
 
 template <typename T, int W>
-void proj_update(const VParts<T>& V, const double* C, T* Wp, int64_t ldw, int64_t n, int gram, double* R,
+void proj_update(const VParts<T>& V, const double* C, T* Wp, T* Wp2, int64_t ldw, int64_t n, int gram, double* R,
                  double* gdiag, unsigned* flags, const Red& red, cudaStream_t s) {
   const int K = V.kx + V.kz;
   const size_t smem = sizeof(T) * (size_t)K * W;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_proj_update<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr_set = true;
-  }
-  k_proj_update<T, W><<<persistent_rows(n), kThreads, smem, s>>>(V, C, Wp, ldw, n, gram, R, gdiag, flags, red);
+#define CALL(PP)                                                                                         \
+  do {                                                                                                   \
+    static bool attr_set = false;                                                                        \
+    if (!attr_set) {                                                                                     \
+      cudaFuncSetAttribute(k_proj_update<T, W, PP>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); \
+      attr_set = true;                                                                                   \
+    }                                                                                                    \
+    k_proj_update<T, W, PP><<<persistent_rows(n), kThreads, smem, s>>>(V, C, Wp, Wp2, ldw, n, gram, R, gdiag, \
+                                                                        flags, red);                     \
+  } while (0)
+  NS_P_SWITCH(V.p, CALL)
+#undef CALL
 }
 
-#define NS_INST_PROJ(T, W)                                                                                   \
-  template void proj_dots<T, W>(const VParts<T>&, const T*, int64_t, int64_t, double*, double*, cudaStream_t); \
-  template void proj_update<T, W>(const VParts<T>&, const double*, T*, int64_t, int64_t, int, double*, double*, \
-                                  unsigned*, const Red&, cudaStream_t);
+#define NS_INST_PROJ(T, W)                                                                                     \
+  template void proj_dots<T, W>(const VParts<T>&, const T*, const T*, int64_t, int64_t, double*, double*,       \
+                                cudaStream_t);                                                                 \
+  template void proj_update<T, W>(const VParts<T>&, const double*, T*, T*, int64_t, int64_t, int, double*,      \
+                                  double*, unsigned*, const Red&, cudaStream_t);
 NS_INST_PROJ(double, 1)
 NS_INST_PROJ(double, 2)
 NS_INST_PROJ(double, 4)
 NS_INST_PROJ(double, 8)
+NS_INST_PROJ(double, 16)
 NS_INST_PROJ(float, 1)
 NS_INST_PROJ(float, 2)
 NS_INST_PROJ(float, 4)
 NS_INST_PROJ(float, 8)
+NS_INST_PROJ(float, 16)
 
 // ---------------------------------------------------------------------------
 // thick-restart GEMM: [Lnew | Znext] = Z(:, 0:R) V_Z(:, sel)

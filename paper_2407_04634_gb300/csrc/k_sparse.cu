@@ -67,17 +67,21 @@ __global__ void __launch_bounds__(kThreads) k_spmm_lanczos(Csr<T> M, const T* __
   for (int k = 0; k < NP; ++k) part[k] = T(0);
   for (int64_t tile = blockIdx.x; tile * RPB < M.nrows; tile += gridDim.x) {
     const int64_t row = tile * RPB + grp;
+    // epilogue operands do not depend on the gather: issue their loads first
+    T xi[D], qp[D];
+    T de = T(0);
+    const bool lead = (lane == 0 && row < M.nrows);
+    if (lead) {
+      load_row<T, D>(op.x + row * D, xi);
+      de = (T)op.eps * __ldg(op.Dv + row);
+      if (has_prev) load_row<T, D>(op.qprev + row * D, qp);
+    }
     T acc[D];
     row_product<T, D, V>(M, v, row, lane, acc);
-    if (lane == 0 && row < M.nrows) {
-      T xi[D];
-      load_row<T, D>(op.x + row * D, xi);
-      const T de = (T)op.eps * __ldg(op.Dv + row);
+    if (lead) {
 #pragma unroll
       for (int q = 0; q < D; ++q) acc[q] = fma(de, xi[q], acc[q]);
       if (has_prev) {
-        T qp[D];
-        load_row<T, D>(op.qprev + row * D, qp);
 #pragma unroll
         for (int r = 0; r < D; ++r)
 #pragma unroll
@@ -184,10 +188,42 @@ void spmm_coldot(const Csr<T>& M, const T* v, T* y, const T* w, int sq, double* 
 #undef CALL
 }
 
+// SpMM schedule autotuner: time y = M v for V in {1, 2, 4, 8, 16} lanes per row
+// on the actual matrix (CUDA events, one warm-up + two timed launches each) and
+// return the fastest.
+template <typename T, int D>
+int tune_lanes(Csr<T> M, const T* v, T* y, cudaStream_t s) {
+  if (M.nrows == 0) return 1;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  int best = M.V;
+  float best_ms = 1e30f;
+  for (int V = 1; V <= 16; V *= 2) {
+    M.V = V;
+    spmm_plain<T, D>(M, v, y, s);
+    cudaEventRecord(e0, s);
+    spmm_plain<T, D>(M, v, y, s);
+    spmm_plain<T, D>(M, v, y, s);
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = V;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return best;
+}
+
 #define NS_INST_SPMM(T, D)                                                                            \
   template void spmm_plain<T, D>(const Csr<T>&, const T*, T*, cudaStream_t);                          \
   template void spmm_lanczos<T, D>(const Csr<T>&, const T*, const StepOps<T>&, const Red&, cudaStream_t); \
-  template void spmm_coldot<T, D>(const Csr<T>&, const T*, T*, const T*, int, double*, const Red&, cudaStream_t);
+  template void spmm_coldot<T, D>(const Csr<T>&, const T*, T*, const T*, int, double*, const Red&, cudaStream_t); \
+  template int tune_lanes<T, D>(Csr<T>, const T*, T*, cudaStream_t);
 NS_INST_SPMM(double, 1)
 NS_INST_SPMM(double, 2)
 NS_INST_SPMM(double, 4)

