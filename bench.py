@@ -47,7 +47,7 @@ def peaks():
 
 
 def workload_params(args):
-    return dict(n=1_000_000, ncomp=500, seed=0x2407046340 + 1, solver_seed=1001, d=args.d, restart=120,
+    return dict(n=args.n, ncomp=args.components, seed=0x2407046340 + 1, solver_seed=1001, d=args.d, restart=120,
                 tol=1e-10, precision=args.precision)
 
 
@@ -194,6 +194,8 @@ def main():
     ap.add_argument("--profile-every", type=int, default=16)
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n", type=int, default=1_000_000, help="nodes (a smaller case is for profiling only)")
+    ap.add_argument("--components", type=int, default=500)
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
