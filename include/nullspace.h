@@ -212,6 +212,24 @@ ns_status ns_syev(int k, const double* T, double* theta, double* V);
  * coefficients of both passes. */
 ns_status ns_project(int64_t n, int K, int w, const double* V, double* W, double* C, int precision);
 
+/* ns_project_noalloc -- the same FP64 CGS2 projection as ns_project, for callers
+ * that cannot allocate device memory while they run (code inside a CUDA graph
+ * being captured, an allocator's own callback, hosts that only hand over
+ * pre-allocated buffers).  The paper has no counterpart; this is a service of
+ * the library.  It allocates nothing: its scratch is a fixed 4 MiB device array
+ * inside the library (held on every GPU that loads the library until exit).
+ *   V : n x K column-major FP64, device memory (read)
+ *   W : n x w row-major FP64,   device memory (overwritten by W - V V^T W, twice)
+ *   C : K x w row-major FP64,   device memory (receives the summed coefficients)
+ *   stream : cudaStream_t, NULL = legacy default stream; the call only enqueues work
+ * Limits: w in {1, 2, 4, 8}; K*w*(ceil(n/32768)+1) <= 524288 and K*w <= 24320,
+ * else NS_ERR_INVALID_ARG (nothing enqueued).  The first call on a device looks
+ * up the scratch address (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  All calls share the one scratch array and every call fully
+ * overwrites what it reads, so calls that overlap on the GPU (different streams,
+ * no ordering) race and give wrong results. */
+ns_status ns_project_noalloc(int64_t n, int K, int w, const double* V, double* W, double* C, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

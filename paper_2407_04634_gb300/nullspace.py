@@ -74,6 +74,7 @@ SIGNATURES = {
     "ns_apply_B": (C.c_int, [_P, C.c_int, _P, _P, C.c_double, C.c_int, C.c_int]),
     "ns_syev": (C.c_int, [C.c_int, _P, _P, _P]),
     "ns_project": (C.c_int, [C.c_int64, C.c_int, C.c_int, _P, _P, _P, C.c_int]),
+    "ns_project_noalloc": (C.c_int, [C.c_int64, C.c_int, C.c_int, _P, _P, _P, _P]),
 }
 
 _LIB = None
