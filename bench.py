@@ -6,12 +6,16 @@ components (power-law sizes, minimum 50), each the union of 4 random Hamiltonian
 cycles (mean degree 8), unit weights, FP64 CSR; B = A + eps D (SPD form), block
 size d = 1, restart length 120, lock tolerance 1e-10, plain FP64 GPU path.
 
+Other workloads: --workload incidence (8e6 x 2e6 incidence matrix, nullity 1000,
+d = 4, restart 160, mixed path) and --workload copies (3e6 x 2e6 matrix with 300
+planted column copies, d = 2, restart 150, mixed path).
+
 One step = one ns_solve (Lanczos with locking + FP64 refinement + re-
 orthonormalization) on the matrix already resident in HBM.  A step counts only
-if the nullity is 500 and max_j ||A x_j|| / ||A||_2 <= 1e-8.
+if the nullity equals the planted one and max_j ||A x_j|| / ||A||_2 <= 1e-8.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--precision fp64|mixed] [--d 1|4]
+                  [--workload laplacian|incidence|copies] [--precision fp64|mixed] [--d D]
 """
 
 from __future__ import annotations
@@ -46,19 +50,46 @@ def peaks():
     return p
 
 
+WORKLOADS = {
+    # configuration 2 (the default): graph Laplacian, SPD form, plain FP64 path
+    "laplacian": dict(cfg=2, mode="spd", d=1, restart=120, precision="fp64", cpu_scale=0.06, ref_scale=0.03),
+    # configuration 3: +-1 edge-vertex incidence matrix, normal form, precision form
+    "incidence": dict(cfg=3, mode="normal", d=4, restart=160, precision="mixed", cpu_scale=0.02, ref_scale=0.01),
+    # configuration 4: rectangular N(0,1) matrix with planted sign-flipped column copies
+    "copies": dict(cfg=4, mode="normal", d=2, restart=150, precision="mixed", cpu_scale=0.01, ref_scale=0.005),
+}
+
+
 def workload_params(args):
-    return dict(n=args.n, ncomp=args.components, seed=0x2407046340 + 1, solver_seed=1001, d=args.d, restart=120,
-                tol=1e-10, precision=args.precision)
+    wl = WORKLOADS[args.workload]
+    return dict(name=args.workload, cfg=wl["cfg"], mode=wl["mode"], scale=args.scale,
+                d=args.d or wl["d"], restart=wl["restart"], tol=1e-10,
+                precision=args.precision or wl["precision"], solver_seed=1000 + wl["cfg"] - 1,
+                cpu_scale=wl["cpu_scale"], ref_scale=wl["ref_scale"])
 
 
-def describe(p, A):
-    return {"workload": f"graph Laplacian n={p['n']:,} ({p['ncomp']} components, power-law sizes, mean degree 8), "
-                        f"SPD form A+eps*D, {p['precision'].upper()} path, d={p['d']}, restart {p['restart']}",
-            "n": p["n"], "nnz": int(A.nnz), "components": p["ncomp"], "d": p["d"], "restart_len": p["restart"],
-            "tol": p["tol"], "eps": 1e-3, "precision": p["precision"],
+def build_workload(p):
+    from workloads import make_config
+    w, _ = make_config(p["cfg"], p["scale"])
+    return w
+
+
+def describe(p, w):
+    A = w.A
+    kind = {"laplacian": "graph Laplacian (power-law component sizes, mean degree 8), SPD form A+eps*D",
+            "incidence": "oriented edge-vertex incidence matrix (mean degree 8, uniform component sizes), "
+                         "normal form A^T A+eps*D",
+            "copies": "rectangular sparse N(0,1) matrix, 12 nnz/row, planted sign-flipped column copies, "
+                      "normal form A^T A+eps*D"}[p["name"]]
+    vec = 4 if p["precision"] == "mixed" else 8
+    return {"workload": f"{kind}; m={A.m:,} n={A.n:,} nnz={A.nnz:,}, nullity {w.nullity}; "
+                        f"{p['precision'].upper()} path, d={p['d']}, restart {p['restart']}, tol {p['tol']:g}",
+            "m": int(A.m), "n": int(A.n), "nnz": int(A.nnz), "nullity": int(w.nullity), "d": p["d"],
+            "restart_len": p["restart"], "tol": p["tol"], "eps": 1e-3, "precision": p["precision"],
+            "mode": p["mode"],
             "l2": "inputs larger than L2 (Lanczos basis %.2f GB, locked set up to %.2f GB, matrix %.2f GB)"
-                  % (p["n"] * (p["restart"] + p["d"]) * 8 * 2 / 1e9, p["n"] * p["ncomp"] * 8 / 1e9,
-                     A.nnz * 12 / 1e9)}
+                  % (A.n * (p["restart"] + p["d"]) * vec * 2 / 1e9, A.n * w.nullity * vec / 1e9,
+                     A.nnz * (4 + vec) / 1e9)}
 
 
 # ---------------------------------------------------------------- clocks -----
@@ -119,35 +150,36 @@ ORACLE_SNIPPET = r"""
 import json, os, sys, time
 sys.path.insert(0, {root!r})
 import numpy as np
-from workloads import laplacian_cycle_components
+from workloads import make_config
 from oracle import lanczos_nullspace
-w = laplacian_cycle_components({seed}, {n}, {k}, 8, "powerlaw", 50)
+w, _ = make_config({cfg}, {scale})
 A = w.A.to_scipy()
 t = time.perf_counter()
-r = lanczos_nullspace(A, "spd", {d}, {restart}, tol={tol}, seed={sseed})
+r = lanczos_nullspace(A, {mode!r}, {d}, {restart}, tol={tol}, seed={sseed})
 dt = time.perf_counter() - t
 res = float(np.linalg.norm(A @ r.X) / r.normA) if r.N else 0.0
-print(json.dumps(dict(N=int(r.N), expect={k}, seconds=dt, matvecs=int(r.stats["matvecs"]), residual=res)))
+print(json.dumps(dict(N=int(r.N), expect=int(w.nullity), n=int(A.shape[1]), seconds=dt,
+                      matvecs=int(r.stats["matvecs"]), residual=res)))
 """
 
 
-def run_oracle_sample(p, n, k):
+def run_oracle_sample(p, scale):
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
-    code = ORACLE_SNIPPET.format(root=ROOT, seed=p["seed"], n=n, k=k, d=p["d"], restart=p["restart"],
-                                 tol=p["tol"], sseed=p["solver_seed"])
+    code = ORACLE_SNIPPET.format(root=ROOT, cfg=p["cfg"], scale=scale, mode=p["mode"], d=p["d"],
+                                 restart=p["restart"], tol=p["tol"], sseed=p["solver_seed"])
     out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
     if out.returncode != 0:
         raise RuntimeError(out.stderr[-2000:])
     return json.loads(out.stdout.strip().splitlines()[-1])
 
 
-def cpu_baseline(p, n=60_000, k=30):
-    r = run_oracle_sample(p, n, k)
+def cpu_baseline(p):
+    r = run_oracle_sample(p, p["cpu_scale"])
     return {"value": r["N"] / r["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"same generator at n={n:,}, {k} components (nullity {r['N']}, expected {k}), "
-                      f"single-threaded FP64 oracle, {r['seconds']:.1f} s, {r['matvecs']} matvecs, "
-                      f"residual {r['residual']:.1e}"}
+            "sample": f"same generator scaled by {p['cpu_scale']} (n={r['n']:,}, nullity {r['N']}, "
+                      f"expected {r['expect']}), single-threaded FP64 oracle, {r['seconds']:.1f} s, "
+                      f"{r['matvecs']} matvecs, residual {r['residual']:.1e}"}
 
 
 # ------------------------------------------------------------- reference ----
@@ -156,29 +188,47 @@ def bench_reference(args, rank):
     if rank != 0:
         return
     p = workload_params(args)
-    n, k = 30_000, 15
-    times, Ns = [], []
+    times, Ns, last = [], [], None
     for i in range(args.warmup + args.steps):
-        r = run_oracle_sample(p, n, k)
+        r = run_oracle_sample(p, p["ref_scale"])
+        last = r
         if i >= args.warmup:
             times.append(r["seconds"])
             Ns.append(r["N"])
     tot = sum(times)
     val = sum(Ns) / tot
+    sample = (f"same generator scaled by {p['ref_scale']} (n={last['n']:,}, nullity {last['N']}), "
+              f"single-threaded FP64 oracle")
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": describe(p, _FakeA(9 * p["n"]))["workload"],
-                                            "oracle_sample": f"n={n:,}, {k} components"},
-            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"same generator at n={n:,}, {k} components, single-threaded FP64 oracle"},
+            "data": "synthetic", "config": {"workload": f"{p['name']} (configuration {p['cfg']}), oracle sample",
+                                            "oracle_sample": sample},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-class _FakeA:
-    def __init__(self, nnz):
-        self.nnz = nnz
+def kernel_probe(ns, h, w, p):
+    """A handful of hot-kernel launches on the full-size inputs (for ncu captures):
+    three B-applies in each precision and two CGS2 projections against 256 vectors."""
+    import numpy as np
+    rng = np.random.default_rng(0)
+    n = w.A.n
+    out = {}
+    X = rng.standard_normal((n, p["d"]))
+    for prec in ("fp64", "mixed"):
+        t = time.perf_counter()
+        for _ in range(3):
+            h.apply_B(X, 1e-3, prec)
+        out[f"apply_B_{prec}_s"] = (time.perf_counter() - t) / 3
+    V, _ = np.linalg.qr(rng.standard_normal((n, 256)))
+    W = rng.standard_normal((n, 2))
+    for prec in ("fp64", "mixed"):
+        t = time.perf_counter()
+        ns.project(V, W, prec)
+        out[f"project_{prec}_s"] = time.perf_counter() - t
+    print(json.dumps({"kernel_probe": p["name"], **out}), flush=True)
 
 
 # -------------------------------------------------------------------- ours --
@@ -189,13 +239,14 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
-    ap.add_argument("--d", type=int, default=1)
+    ap.add_argument("--workload", default="laplacian", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default=None, choices=["fp64", "mixed"])
+    ap.add_argument("--d", type=int, default=None)
     ap.add_argument("--profile-every", type=int, default=16)
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--n", type=int, default=1_000_000, help="nodes (a smaller case is for profiling only)")
-    ap.add_argument("--components", type=int, default=500)
+    ap.add_argument("--scale", type=float, default=1.0, help="workload scale (< 1 is for profiling only)")
+    ap.add_argument("--kernel-probe", action="store_true", help="launch a few hot kernels, no bench line")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -215,20 +266,21 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     from paper_2407_04634_gb300 import nullspace as ns
-    from workloads import laplacian_cycle_components
-
     p = workload_params(args)
-    w = laplacian_cycle_components(p["seed"], p["n"], p["ncomp"], 8, "powerlaw", 50)
+    w = build_workload(p)
     A = w.A
-    h = ns.Handle(A.rowptr, A.colind, A.vals, A.m, A.n, p["solver_seed"], "spd")
+    h = ns.Handle(A.rowptr, A.colind, A.vals, A.m, A.n, p["solver_seed"], p["mode"])
     stream = torch.cuda.current_stream()
+    if args.kernel_probe:
+        kernel_probe(ns, h, w, p)
+        return
 
     def one_step(profile=0):
         r = h.solve(p["d"], p["restart"], p["tol"], check=False, precision=p["precision"], profile=profile)
         return r
 
     def valid(r):
-        return (r.status == ns.NS_OK and r.nullity == p["ncomp"] and r.stats.get("refine_resid_max", 1) <= 1e-8)
+        return (r.status == ns.NS_OK and r.nullity == w.nullity and r.stats.get("refine_resid_max", 1) <= 1e-8)
 
     for _ in range(args.warmup):
         one_step()
@@ -260,9 +312,12 @@ def main():
 
     # roofline of the dominant kernel class and of the B-apply (SpMM) class
     pk = peaks()
-    dom = max(prof, key=lambda c: c["ms_total_est"])
+    dom = max(prof, key=lambda c: (c["ms_total_est"], c["launches"]))
 
     def roof(c):
+        if not c["sampled"] or c["ms_per_launch"] <= 0:
+            return {"kernel": c["name"], "bound": None, "achieved": None, "peak": None, "unit": None,
+                    "frac": None, "traffic": None, "note": "not sampled (run with --profile-every > 0)"}
         if c["name"] == "b_apply":
             ach = c["bytes_per_launch"] / (c["ms_per_launch"] / 1e3) / 1e9
             return {"kernel": c["name"], "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
@@ -289,17 +344,17 @@ def main():
     rp = torch.from_numpy(A.rowptr).pin_memory()
     ci = torch.from_numpy(A.colind).pin_memory()
     va = torch.from_numpy(A.vals).pin_memory()
-    out = torch.empty((p["ncomp"], p["n"]), dtype=torch.float64).pin_memory()
+    out = torch.empty((w.nullity, A.n), dtype=torch.float64).pin_memory()
     h2d = rp.numel() * 8 + ci.numel() * 4 + va.numel() * 8
     d2h = out.numel() * 8
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     e2e_units = 0
     for _ in range(args.e2e_steps):
-        he = ns.Handle(rp.numpy(), ci.numpy(), va.numpy(), A.m, A.n, p["solver_seed"], "spd")
+        he = ns.Handle(rp.numpy(), ci.numpy(), va.numpy(), A.m, A.n, p["solver_seed"], p["mode"])
         r = he.solve(p["d"], p["restart"], p["tol"], check=False, precision=p["precision"])
         if valid(r):
-            he.lib.ns_basis(he.h, ns.C.c_void_p(out.data_ptr()), p["n"], 0)
+            he.lib.ns_basis(he.h, ns.C.c_void_p(out.data_ptr()), A.n, 0)
             e2e_units += r.nullity
         he.close()
     torch.cuda.synchronize()
@@ -321,7 +376,7 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if p["precision"] == "fp64" else "f32+f64",
-            "data": "synthetic", "config": describe(p, A), "valid": all_valid,
+            "data": "synthetic", "config": describe(p, w), "valid": all_valid,
             "gpu_launches": int(launches), "clocks": clk, "roofline": roofline, "spmm_roofline": spmm,
             "e2e": e2e, "cpu_baseline": cpu,
             "solve": {k: last.get(k) for k in ("nullity", "matvecs", "restarts", "reorth_X", "reorth_Z",
