@@ -60,6 +60,21 @@ WORKLOADS = {
 }
 
 
+def ncu_traffic_ratio(cls):
+    """DRAM bytes / algorithmic bytes of a kernel class from the committed ncu capture,
+    or None when the kernel sources changed since the capture (or no capture exists)."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
+            j = json.load(f)
+        h = hashlib.sha256(b"".join(open(os.path.join(ROOT, x), "rb").read() for x in j["source_files"])).hexdigest()
+        if h != j["source_sha256"] or cls not in j["classes"]:
+            return None
+        return float(j["classes"][cls]["ratio"])
+    except Exception:
+        return None
+
+
 def workload_params(args):
     wl = WORKLOADS[args.workload]
     return dict(name=args.workload, cfg=wl["cfg"], mode=wl["mode"], scale=args.scale,
@@ -314,6 +329,13 @@ def main():
     pk = peaks()
     dom = max(prof, key=lambda c: (c["ms_total_est"], c["launches"]))
 
+    def traffic(c):
+        key = c["name"] if c["name"] != "b_apply" else ("b_apply_fp64" if p["precision"] == "fp64" else "b_apply_mixed")
+        if key == "cgs2_project" and p["precision"] != "fp64":
+            key = None  # captured in FP64 only
+        r = ncu_traffic_ratio(key) if key else None
+        return None if r is None else r * c["bytes_per_launch"]
+
     def roof(c):
         if not c["sampled"] or c["ms_per_launch"] <= 0:
             return {"kernel": c["name"], "bound": None, "achieved": None, "peak": None, "unit": None,
@@ -321,19 +343,19 @@ def main():
         if c["name"] == "b_apply":
             ach = c["bytes_per_launch"] / (c["ms_per_launch"] / 1e3) / 1e9
             return {"kernel": c["name"], "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                    "frac": ach / pk["hbm_gbs"], "traffic": None, "peak_src": pk["src"],
+                    "frac": ach / pk["hbm_gbs"], "traffic": traffic(c), "peak_src": pk["src"],
                     "bytes_per_launch": c["bytes_per_launch"], "ms_per_launch": c["ms_per_launch"],
                     "launches": c["launches"], "sampled": c["sampled"]}
         if p["precision"] == "fp64":
             ach = c["flops_per_launch"] / (c["ms_per_launch"] / 1e3) / 1e12
             return {"kernel": c["name"], "bound": "alu", "achieved": ach, "peak": FP64_TFLOPS, "unit": "TFLOP/s",
-                    "frac": ach / FP64_TFLOPS, "traffic": None,
+                    "frac": ach / FP64_TFLOPS, "traffic": traffic(c),
                     "peak_src": "derived: 152 SMs x 4 FP64 flop/clk x 2.07 GHz",
                     "flops_per_launch": c["flops_per_launch"], "ms_per_launch": c["ms_per_launch"],
                     "launches": c["launches"], "sampled": c["sampled"]}
         ach = c["bytes_per_launch"] / (c["ms_per_launch"] / 1e3) / 1e9
         return {"kernel": c["name"], "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": ach / pk["hbm_gbs"], "traffic": None, "peak_src": pk["src"],
+                "frac": ach / pk["hbm_gbs"], "traffic": traffic(c), "peak_src": pk["src"],
                 "bytes_per_launch": c["bytes_per_launch"], "ms_per_launch": c["ms_per_launch"],
                 "launches": c["launches"], "sampled": c["sampled"]}
 
