@@ -736,17 +736,17 @@ void make_F(const double* Rr, const double* Gam_last, const double* VZ, const in
 }
 
 // ---------------------------------------------------------------------------
-// FP64 CG / CGLS refinement helpers on panels of width W
+// CG / CGLS refinement helpers on row-major panels of width W (T = float for
+// the inner iterations, double for the outer residual correction)
 // ---------------------------------------------------------------------------
-// delta += alpha p ; r -= alpha q ; rr_new[c] = sum_i r_i[c]^2
-template <int W>
-__global__ void __launch_bounds__(kThreads) k_cg_update(double* delta, const double* p, int64_t np_, double* r,
-                                                        const double* q, int64_t nr, const double* alpha, Red red,
-                                                        double* rr_new) {
+// delta += alpha p (np rows) ; r -= alpha q (nr rows) ; rr_new[c] = sum_i r_i[c]^2
+template <typename T, int W>
+__global__ void __launch_bounds__(kThreads) k_cg_update(T* delta, const T* p, int64_t np_, T* r, const T* q,
+                                                        int64_t nr, const double* alpha, Red red, double* rr_new) {
   __shared__ double red_s[(kThreads / 32) * W];
   __shared__ double tot[W];
-  __shared__ double al[W];
-  if (threadIdx.x < W) al[threadIdx.x] = alpha[threadIdx.x];
+  __shared__ T al[W];
+  if (threadIdx.x < W) al[threadIdx.x] = (T)alpha[threadIdx.x];
   __syncthreads();
   const int64_t nmax = np_ > nr ? np_ : nr;
   double part[W];
@@ -760,9 +760,9 @@ __global__ void __launch_bounds__(kThreads) k_cg_update(double* delta, const dou
     if (i < nr) {
 #pragma unroll
       for (int c = 0; c < W; ++c) {
-        const double v = fma(-al[c], q[i * W + c], r[i * W + c]);
+        const T v = fma(-al[c], q[i * W + c], r[i * W + c]);
         r[i * W + c] = v;
-        part[c] = fma(v, v, part[c]);
+        part[c] += (double)v * (double)v;
       }
     }
   }
@@ -772,24 +772,24 @@ __global__ void __launch_bounds__(kThreads) k_cg_update(double* delta, const dou
     if (threadIdx.x < W) rr_new[threadIdx.x] = tot[threadIdx.x];
 }
 
-template <int W>
-void cg_update2(double* delta, const double* p, int64_t np_, double* r, const double* q, int64_t nr,
-                const double* alpha, const Red& red, double* rr_new, cudaStream_t s) {
-  k_cg_update<W><<<persistent_rows(np_ > nr ? np_ : nr), kThreads, 0, s>>>(delta, p, np_, r, q, nr, alpha, red,
-                                                                             rr_new);
+template <typename T, int W>
+void cg_update2(T* delta, const T* p, int64_t np_, T* r, const T* q, int64_t nr, const double* alpha, const Red& red,
+                double* rr_new, cudaStream_t s) {
+  k_cg_update<T, W><<<persistent_rows(np_ > nr ? np_ : nr), kThreads, 0, s>>>(delta, p, np_, r, q, nr, alpha, red,
+                                                                                rr_new);
 }
 
-// p = s + beta p (columns with active == 0 keep p)
-template <int W>
-__global__ void k_cg_direction(double* p, const double* sres, const double* beta, int64_t n) {
+// p = s + beta p
+template <typename T, int W>
+__global__ void k_cg_direction(T* p, const T* sres, const double* beta, int64_t n) {
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n * W; t += (int64_t)gridDim.x * blockDim.x) {
     const int c = (int)(t % W);
-    p[t] = fma(beta[c], p[t], sres[t]);
+    p[t] = fma((T)beta[c], p[t], sres[t]);
   }
 }
-template <int W>
-void cg_direction2(double* p, const double* sres, const double* beta, int64_t n, cudaStream_t s) {
-  k_cg_direction<W><<<stream_grid(n * W), kThreads, 0, s>>>(p, sres, beta, n);
+template <typename T, int W>
+void cg_direction2(T* p, const T* sres, const double* beta, int64_t n, cudaStream_t s) {
+  k_cg_direction<T, W><<<stream_grid(n * W), kThreads, 0, s>>>(p, sres, beta, n);
 }
 
 // alpha[c] = num[c]/den[c] for active columns (else 0); same kernel for beta
@@ -802,37 +802,72 @@ void cg_scalars(const double* num, const double* den, const unsigned char* activ
   k_cg_scalars<<<1, 32, 0, s>>>(num, den, active, out, w);
 }
 
-// active[c] &= rr[c] > tol2 ; *nactive = count
-__global__ void k_cg_check(const double* rr, double tol2, unsigned char* active, int* nactive, int w) {
+// active[c] &= rr[c] > tol2[c] (tol2 per column, or the scalar tol2s when tol2 == null)
+__global__ void k_cg_check(const double* rr, const double* tol2, double tol2s, unsigned char* active, int* nactive,
+                           int w) {
   if (threadIdx.x == 0) {
     int cnt = 0;
     for (int c = 0; c < w; ++c) {
-      const unsigned char a = active[c] && (rr[c] > tol2);
+      const unsigned char a = active[c] && (rr[c] > (tol2 ? tol2[c] : tol2s));
       active[c] = a;
       cnt += a;
     }
     *nactive = cnt;
   }
 }
-void cg_check(const double* rr, double tol2, unsigned char* active, int* nactive, int w, cudaStream_t s) {
-  k_cg_check<<<1, 32, 0, s>>>(rr, tol2, active, nactive, w);
+void cg_check(const double* rr, const double* tol2, double tol2s, unsigned char* active, int* nactive, int w,
+              cudaStream_t s) {
+  k_cg_check<<<1, 32, 0, s>>>(rr, tol2, tol2s, active, nactive, w);
 }
 
-// X[:, c0 + c] = P[:, c] - Dl[:, c]   (refined column written back, FP64)
+// tol2[c] = f^2 rr[c]
+__global__ void k_scale_vec(const double* rr, double f2, double* out, int w) {
+  if (threadIdx.x < w) out[threadIdx.x] = f2 * rr[threadIdx.x];
+}
+void scale_vec(const double* rr, double f2, double* out, int w, cudaStream_t s) {
+  k_scale_vec<<<1, 32, 0, s>>>(rr, f2, out, w);
+}
+
+// columns [c0, c0+w) of X (FP64 column-major) into a zero-padded row-major panel of width W
 template <int W>
-__global__ void k_refined_to_cols(const double* P, const double* Dl, double* X, int c0, int w, int64_t n) {
+__global__ void k_cols_to_panel(const double* X, int c0, int w, int64_t n, double* P) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    for (int c = 0; c < w; ++c) X[(int64_t)(c0 + c) * n + i] = P[i * W + c] - Dl[i * W + c];
+#pragma unroll
+    for (int c = 0; c < W; ++c) P[i * W + c] = (c < w) ? X[(int64_t)(c0 + c) * n + i] : 0.0;
 }
 template <int W>
-void refined_to_cols(const double* P, const double* Dl, double* X, int c0, int w, int64_t n, cudaStream_t s) {
-  k_refined_to_cols<W><<<stream_grid(n), kThreads, 0, s>>>(P, Dl, X, c0, w, n);
+void cols_to_panel_w(const double* X, int c0, int w, int64_t n, double* P, cudaStream_t s) {
+  k_cols_to_panel<W><<<stream_grid(n), kThreads, 0, s>>>(X, c0, w, n, P);
 }
 
-template void cg_update2<8>(double*, const double*, int64_t, double*, const double*, int64_t, const double*,
-                            const Red&, double*, cudaStream_t);
-template void cg_direction2<8>(double*, const double*, const double*, int64_t, cudaStream_t);
-template void refined_to_cols<8>(const double*, const double*, double*, int, int, int64_t, cudaStream_t);
+// x -= delta (FP64 panel minus the FP32 correction)
+template <int W>
+__global__ void k_sub_correction(double* x, const float* dl, int64_t n) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n * W; t += (int64_t)gridDim.x * blockDim.x)
+    x[t] -= (double)dl[t];
+}
+template <int W>
+void sub_correction(double* x, const float* dl, int64_t n, cudaStream_t s) {
+  k_sub_correction<W><<<stream_grid(n * W), kThreads, 0, s>>>(x, dl, n);
+}
+
+// X[:, c0 + c] = P[:, c] for c < w
+template <int W>
+__global__ void k_panel_to_cols64(const double* P, double* X, int c0, int w, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    for (int c = 0; c < w; ++c) X[(int64_t)(c0 + c) * n + i] = P[i * W + c];
+}
+template <int W>
+void panel_to_cols64(const double* P, double* X, int c0, int w, int64_t n, cudaStream_t s) {
+  k_panel_to_cols64<W><<<stream_grid(n), kThreads, 0, s>>>(P, X, c0, w, n);
+}
+
+template void cg_update2<float, 16>(float*, const float*, int64_t, float*, const float*, int64_t, const double*,
+                                    const Red&, double*, cudaStream_t);
+template void cg_direction2<float, 16>(float*, const float*, const double*, int64_t, cudaStream_t);
+template void cols_to_panel_w<16>(const double*, int, int, int64_t, double*, cudaStream_t);
+template void sub_correction<16>(double*, const float*, int64_t, cudaStream_t);
+template void panel_to_cols64<16>(const double*, double*, int, int, int64_t, cudaStream_t);
 
 }  // namespace ns
 

@@ -232,6 +232,11 @@ NS_INST_SPMM(float, 1)
 NS_INST_SPMM(float, 2)
 NS_INST_SPMM(float, 4)
 NS_INST_SPMM(float, 8)
+// wide panels for the refinement (column dots only)
+template void spmm_coldot<double, 16>(const Csr<double>&, const double*, double*, const double*, int, double*,
+                                      const Red&, cudaStream_t);
+template void spmm_coldot<float, 16>(const Csr<float>&, const float*, float*, const float*, int, double*, const Red&,
+                                     cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // validation, norms, conversions

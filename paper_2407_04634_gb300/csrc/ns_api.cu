@@ -361,11 +361,13 @@ struct Solver {
     // SpMM schedule: lanes per row tuned on this matrix (operands: the basis buffers)
     ck(cudaMemsetAsync(Z[1], 0, zbytes, s), "memset");
     if (h->mode == NS_MODE_SPD) {
-      A.V = tune_lanes<T, D>(A, Z[1], qp.as<T>(), s);
+      A.V = tune_lanczos(A, Z[1]);
     } else {
       A.V = tune_lanes<T, D>(A, Z[1], ybuf.as<T>(), s);
-      At.V = tune_lanes<T, D>(At, ybuf.as<T>(), qp.as<T>(), s);
+      ck(cudaMemsetAsync(ybuf.p, 0, sizeof(T) * (size_t)m * D, s), "memset");
+      At.V = tune_lanczos(At, ybuf.as<T>());
     }
+    if (getenv("NS_DEBUG")) fprintf(stderr, "[ns] lanes per row: A %d, A^T %d\n", A.V, At.V);
     launches += (h->mode == NS_MODE_SPD ? 15 : 30);
     ck_launch("tune");
   }
@@ -415,6 +417,40 @@ struct Solver {
     alloc_proj();
     alloc_locked_meta(oldcap);
     ck(cudaStreamSynchronize(s), "sync");
+  }
+
+  // lanes per row of the fused Lanczos SpMM, timed on this matrix (CUDA events)
+  int tune_lanczos(Csr<T> M, const T* v) {
+    StepOps<T> op;
+    op.x = Z[1];
+    op.Dv = Dv;
+    op.eps = eps;
+    op.out = qp.as<T>();
+    op.xi = Xi + (size_t)nb * D * D;  // spare slot
+    op.xi_norm = nXi + nb;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int best = M.V;
+    float best_ms = 1e30f;
+    for (int V = 1; V <= 8; V *= 2) {
+      M.V = V;
+      spmm_lanczos<T, D>(M, v, op, red, s);
+      cudaEventRecord(e0, s);
+      spmm_lanczos<T, D>(M, v, op, red, s);
+      spmm_lanczos<T, D>(M, v, op, red, s);
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = V;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return best;
   }
 
   T* X() const { return xbuf.as<T>(); }
@@ -852,97 +888,116 @@ void Solver<T, D>::mat_small(const double* a, const double* b, double* c) {
 // ---------------------------------------------------------------------------
 // FP64 refinement: project every basis column onto null(A) (CG / CGLS)
 // ---------------------------------------------------------------------------
-// columns [c0, c0+w) of X into a zero-padded row-major panel of width 8
-__global__ void k_cols_to_panel8(const double* X, int c0, int w, int64_t n, double* P) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    for (int c = 0; c < 8; ++c) P[i * 8 + c] = (c < w) ? X[(int64_t)(c0 + c) * n + i] : 0.0;
-}
-
 struct RefineOut {
-  int64_t iters_max = 0;
-  double resid_max = 0.0;
+  int64_t iters_max = 0;  // largest number of inner iterations over all chunks
+  double resid_max = 0.0; // max_j ||A x_j|| / ||A||_2 after refinement (FP64)
   int failed = 0;
 };
 
+// Projection of every basis column onto null(A) (Remark after Alg. 1 motivates
+// removing the perturbation at the end): x <- x - delta with delta the minimum-norm
+// solution of A delta = A x (CG, SPD form) or min ||A delta - A x|| (CGLS, normal
+// form).  Mixed-precision iterative refinement: the residual r = A x and the update
+// x <- x - delta are FP64; each inner solve runs in FP32 and only has to reduce the
+// residual of its column by kInner; outer rounds repeat until ||A x|| <= tol ||A||.
 RefineOut refine(ns_handle* h, double* X, int64_t N, double normA, const ns_opts& o) {
   RefineOut out;
-  constexpr int W = 8;
+  constexpr int W = 16;
+  constexpr double kInner = 1e-4;
   cudaStream_t s = h->stream;
   const int64_t n = h->n, m = h->m;
-  Csr<double> A = csr_A<double>(h), At;
-  if (h->mode == NS_MODE_NORMAL) At = csr_At<double>(h);
-  Buf bx(h, sizeof(double) * n * W), bdl(h, sizeof(double) * n * W), bp(h, sizeof(double) * n * W),
-      bq(h, sizeof(double) * std::max(n, m) * W), br(h, sizeof(double) * std::max(n, m) * W),
-      bs(h, sizeof(double) * n * W), bred(h, sizeof(double) * (size_t)kMaxBlocks * 64 + 256), bsm(h, 4096);
+  const bool normal = h->mode == NS_MODE_NORMAL;
+  const int64_t nr = normal ? m : n;  // rows of the residual
+  ensure_fp32(h);
+  Csr<double> A64 = csr_A<double>(h);
+  Csr<float> A32 = csr_A<float>(h), At32;
+  if (normal) At32 = csr_At<float>(h);
+  Buf bx(h, sizeof(double) * n * W), br64(h, sizeof(double) * nr * W), bd(h, sizeof(float) * n * W),
+      bp(h, sizeof(float) * n * W), bq(h, sizeof(float) * nr * W), br(h, sizeof(float) * nr * W),
+      bs(h, sizeof(float) * n * W), bred(h, sizeof(double) * (size_t)kMaxBlocks * 64 + 256), bsm(h, 8192);
   Red red;
   red.part = bred.as<double>();
   double* sm = bsm.as<double>();
-  double *rr = sm, *rrn = sm + 8, *den = sm + 16, *alpha = sm + 24, *beta = sm + 32, *gam = sm + 40;
-  unsigned char* active = reinterpret_cast<unsigned char*>(sm + 48);
-  int* nact = reinterpret_cast<int*>(sm + 50);
-  red.ticket = reinterpret_cast<unsigned*>(sm + 52);
-  ck(cudaMemsetAsync(bsm.p, 0, 4096, s), "memset");
+  double *rr64 = sm, *rr = sm + 32, *rrn = sm + 64, *den = sm + 96, *alpha = sm + 128, *beta = sm + 160,
+         *gam = sm + 192, *tin = sm + 224;
+  unsigned char* act_out = reinterpret_cast<unsigned char*>(sm + 256);
+  unsigned char* act = reinterpret_cast<unsigned char*>(sm + 264);
+  int* nact = reinterpret_cast<int*>(sm + 272);
+  red.ticket = reinterpret_cast<unsigned*>(sm + 280);
+  ck(cudaMemsetAsync(bsm.p, 0, 8192, s), "memset");
   int* nact_h = nullptr;
-  ck(cudaMallocHost(&nact_h, 256), "cudaMallocHost");
-  double* rr_h = reinterpret_cast<double*>(nact_h + 4);
+  ck(cudaMallocHost(&nact_h, 1024), "cudaMallocHost");
+  double* rr_h = reinterpret_cast<double*>(nact_h + 8);
   const double tol2 = (o.refine_tol * normA) * (o.refine_tol * normA);
+  auto read_nact = [&]() {
+    ck(cudaMemcpyAsync(nact_h, nact, sizeof(int), cudaMemcpyDeviceToHost, s), "d2h");
+    ck(cudaStreamSynchronize(s), "sync");
+    return *nact_h;
+  };
   for (int64_t c0 = 0; c0 < N; c0 += W) {
     const int w = (int)std::min<int64_t>(W, N - c0);
-    k_cols_to_panel8<<<std::min<int64_t>(ceil_div(n, kThreads), 152 * 16), kThreads, 0, s>>>(X, (int)c0, w, n,
-                                                                                          bx.as<double>());
+    cols_to_panel_w<W>(X, (int)c0, w, n, bx.as<double>(), s);
+    std::vector<unsigned char> a0(W, 0);
+    for (int c = 0; c < w; ++c) a0[c] = 1;
+    ck(cudaMemcpyAsync(act_out, a0.data(), W, cudaMemcpyHostToDevice, s), "h2d");
     h->launches += 1;
-    ck_launch("refine panel");
-    std::vector<unsigned char> act(W, 0);
-    for (int c = 0; c < w; ++c) act[c] = 1;
-    ck(cudaMemcpyAsync(active, act.data(), W, cudaMemcpyHostToDevice, s), "h2d");
-    ck(cudaMemsetAsync(bdl.p, 0, bdl.bytes, s), "memset");
-    int it = 0;
-    if (h->mode == NS_MODE_SPD) {
-      // r = A x ; p = r
-      spmm_coldot<double, W>(A, bx.as<double>(), br.as<double>(), nullptr, 1, rr, red, s);
-      ck(cudaMemcpyAsync(bp.p, br.p, sizeof(double) * n * W, cudaMemcpyDeviceToDevice, s), "copy");
-      cg_check(rr, tol2, active, nact, W, s);
+    for (int outer = 0; outer < 8; ++outer) {
+      // FP64 residual of the current iterate
+      spmm_coldot<double, W>(A64, bx.as<double>(), br64.as<double>(), nullptr, 1, rr64, red, s);
+      cg_check(rr64, nullptr, tol2, act_out, nact, W, s);
       h->launches += 2;
-      for (; it < o.refine_maxit; ++it) {
-        ck(cudaMemcpyAsync(nact_h, nact, sizeof(int), cudaMemcpyDeviceToHost, s), "d2h");
-        ck(cudaStreamSynchronize(s), "sync");
-        if (*nact_h == 0) break;
-        spmm_coldot<double, W>(A, bp.as<double>(), bq.as<double>(), nullptr, 0, den, red, s);  // p^T A p
-        cg_scalars(rr, den, active, alpha, W, s);
-        cg_update2<W>(bdl.as<double>(), bp.as<double>(), n, br.as<double>(), bq.as<double>(), n, alpha, red, rrn, s);
-        cg_scalars(rrn, rr, active, beta, W, s);
-        cg_direction2<W>(bp.as<double>(), br.as<double>(), beta, n, s);
-        ck(cudaMemcpyAsync(rr, rrn, sizeof(double) * W, cudaMemcpyDeviceToDevice, s), "copy");
-        cg_check(rr, tol2, active, nact, W, s);
-        h->launches += 6;
+      if (read_nact() == 0) break;
+      // inner solve in FP32: delta with A delta ~ r (CG) or min ||A delta - r|| (CGLS)
+      convert_d2f(br64.as<double>(), br.as<float>(), nr * W, s);
+      ck(cudaMemsetAsync(bd.p, 0, bd.bytes, s), "memset");
+      ck(cudaMemcpyAsync(act, act_out, W, cudaMemcpyDeviceToDevice, s), "copy");
+      scale_vec(rr64, kInner * kInner, tin, W, s);
+      h->launches += 2;
+      int it = 0;
+      if (!normal) {
+        ck(cudaMemcpyAsync(bp.p, br.p, sizeof(float) * n * W, cudaMemcpyDeviceToDevice, s), "copy");
+        ck(cudaMemcpyAsync(rr, rr64, sizeof(double) * W, cudaMemcpyDeviceToDevice, s), "copy");
+        for (; it < o.refine_maxit; ++it) {
+          spmm_coldot<float, W>(A32, bp.as<float>(), bq.as<float>(), nullptr, 0, den, red, s);  // p^T A p
+          cg_scalars(rr, den, act, alpha, W, s);
+          cg_update2<float, W>(bd.as<float>(), bp.as<float>(), n, br.as<float>(), bq.as<float>(), n, alpha, red,
+                               rrn, s);
+          cg_scalars(rrn, rr, act, beta, W, s);
+          cg_direction2<float, W>(bp.as<float>(), br.as<float>(), beta, n, s);
+          ck(cudaMemcpyAsync(rr, rrn, sizeof(double) * W, cudaMemcpyDeviceToDevice, s), "copy");
+          cg_check(rr, tin, 0.0, act, nact, W, s);
+          h->launches += 6;
+          if ((it & 3) == 3 && read_nact() == 0) break;
+        }
+      } else {
+        spmm_coldot<float, W>(At32, br.as<float>(), bs.as<float>(), nullptr, 1, gam, red, s);  // s = A^T r
+        ck(cudaMemcpyAsync(bp.p, bs.p, sizeof(float) * n * W, cudaMemcpyDeviceToDevice, s), "copy");
+        h->launches += 1;
+        for (; it < o.refine_maxit; ++it) {
+          spmm_coldot<float, W>(A32, bp.as<float>(), bq.as<float>(), nullptr, 1, den, red, s);  // ||A p||^2
+          cg_scalars(gam, den, act, alpha, W, s);
+          cg_update2<float, W>(bd.as<float>(), bp.as<float>(), n, br.as<float>(), bq.as<float>(), m, alpha, red,
+                               rr, s);
+          spmm_coldot<float, W>(At32, br.as<float>(), bs.as<float>(), nullptr, 1, rrn, red, s);  // ||A^T r||^2
+          cg_scalars(rrn, gam, act, beta, W, s);
+          cg_direction2<float, W>(bp.as<float>(), bs.as<float>(), beta, n, s);
+          ck(cudaMemcpyAsync(gam, rrn, sizeof(double) * W, cudaMemcpyDeviceToDevice, s), "copy");
+          cg_check(rr, tin, 0.0, act, nact, W, s);
+          h->launches += 7;
+          if ((it & 3) == 3 && read_nact() == 0) break;
+        }
       }
-    } else {
-      // CGLS on min ||A delta - A x||: r = A x (m), s = A^T r, p = s
-      spmm_coldot<double, W>(A, bx.as<double>(), br.as<double>(), nullptr, 1, rr, red, s);
-      spmm_coldot<double, W>(At, br.as<double>(), bs.as<double>(), nullptr, 1, gam, red, s);
-      ck(cudaMemcpyAsync(bp.p, bs.p, sizeof(double) * n * W, cudaMemcpyDeviceToDevice, s), "copy");
-      cg_check(rr, tol2, active, nact, W, s);
-      h->launches += 3;
-      for (; it < o.refine_maxit; ++it) {
-        ck(cudaMemcpyAsync(nact_h, nact, sizeof(int), cudaMemcpyDeviceToHost, s), "d2h");
-        ck(cudaStreamSynchronize(s), "sync");
-        if (*nact_h == 0) break;
-        spmm_coldot<double, W>(A, bp.as<double>(), bq.as<double>(), nullptr, 1, den, red, s);  // ||A p||^2
-        cg_scalars(gam, den, active, alpha, W, s);
-        cg_update2<W>(bdl.as<double>(), bp.as<double>(), n, br.as<double>(), bq.as<double>(), m, alpha, red, rr, s);
-        spmm_coldot<double, W>(At, br.as<double>(), bs.as<double>(), nullptr, 1, rrn, red, s);  // ||A^T r||^2
-        cg_scalars(rrn, gam, active, beta, W, s);
-        cg_direction2<W>(bp.as<double>(), bs.as<double>(), beta, n, s);
-        ck(cudaMemcpyAsync(gam, rrn, sizeof(double) * W, cudaMemcpyDeviceToDevice, s), "copy");
-        cg_check(rr, tol2, active, nact, W, s);
-        h->launches += 7;
-      }
+      out.iters_max = std::max<int64_t>(out.iters_max, it + 1);
+      sub_correction<W>(bx.as<double>(), bd.as<float>(), n, s);  // x <- x - delta in FP64
+      h->launches += 1;
     }
-    refined_to_cols<W>(bx.as<double>(), bdl.as<double>(), X, (int)c0, w, n, s);
-    ck(cudaMemcpyAsync(rr_h, rr, sizeof(double) * W, cudaMemcpyDeviceToHost, s), "d2h");
+    // final FP64 residual for the statistics
+    spmm_coldot<double, W>(A64, bx.as<double>(), br64.as<double>(), nullptr, 1, rr64, red, s);
+    panel_to_cols64<W>(bx.as<double>(), X, (int)c0, w, n, s);
+    ck(cudaMemcpyAsync(rr_h, rr64, sizeof(double) * W, cudaMemcpyDeviceToHost, s), "d2h");
     ck(cudaStreamSynchronize(s), "sync");
     ck_launch("refine");
-    out.iters_max = std::max<int64_t>(out.iters_max, it);
+    h->launches += 2;
     for (int c = 0; c < w; ++c) {
       const double rel = std::sqrt(std::max(rr_h[c], 0.0)) / std::max(normA, 1e-300);
       out.resid_max = std::max(out.resid_max, rel);

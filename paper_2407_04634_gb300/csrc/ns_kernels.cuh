@@ -166,22 +166,29 @@ void make_F(const double* Rr, const double* Gam_last, const double* VZ, const in
 void syev(const double* T, int k, double* theta, double* V, double* work, cudaStream_t s);
 size_t syev_work_doubles(int k);
 
-// ---- FP64 CG / CGLS refinement helpers on panels of width W (k_dense.cu) ----
+// ---- CG / CGLS refinement helpers on row-major panels of width W (k_dense.cu) ----
 // delta += alpha p (np rows) ; r -= alpha q (nr rows) ; rr_new[c] = sum_i r_i[c]^2
-template <int W>
-void cg_update2(double* delta, const double* p, int64_t np_, double* r, const double* q, int64_t nr,
-                const double* alpha, const Red& red, double* rr_new, cudaStream_t s);
+template <typename T, int W>
+void cg_update2(T* delta, const T* p, int64_t np_, T* r, const T* q, int64_t nr, const double* alpha, const Red& red,
+                double* rr_new, cudaStream_t s);
 // p = s + beta p
-template <int W>
-void cg_direction2(double* p, const double* sres, const double* beta, int64_t n, cudaStream_t s);
+template <typename T, int W>
+void cg_direction2(T* p, const T* sres, const double* beta, int64_t n, cudaStream_t s);
 // out[c] = num[c] / den[c] on active columns, else 0
 void cg_scalars(const double* num, const double* den, const unsigned char* active, double* out, int w,
                 cudaStream_t s);
-// active[c] &= rr[c] > tol2 ; *nactive = number of active columns
-void cg_check(const double* rr, double tol2, unsigned char* active, int* nactive, int w, cudaStream_t s);
-// X[:, c0 + c] = P[:, c] - Dl[:, c] for c < w
+// active[c] &= rr[c] > tol2[c] (or > tol2s when tol2 is null) ; *nactive = number of active columns
+void cg_check(const double* rr, const double* tol2, double tol2s, unsigned char* active, int* nactive, int w,
+              cudaStream_t s);
+// out[c] = f2 * rr[c]
+void scale_vec(const double* rr, double f2, double* out, int w, cudaStream_t s);
+// FP64 column-major <-> zero-padded row-major panel of width W; x -= FP32 correction
 template <int W>
-void refined_to_cols(const double* P, const double* Dl, double* X, int c0, int w, int64_t n, cudaStream_t s);
+void cols_to_panel_w(const double* X, int c0, int w, int64_t n, double* P, cudaStream_t s);
+template <int W>
+void panel_to_cols64(const double* P, double* X, int c0, int w, int64_t n, cudaStream_t s);
+template <int W>
+void sub_correction(double* x, const float* dl, int64_t n, cudaStream_t s);
 
 }  // namespace ns
 
