@@ -80,7 +80,8 @@ typedef struct {
   double refine_tol;   /* stop when ||A x|| <= refine_tol * ||A||_2 (default 1e-10)    */
   int refine_maxit;    /* CG / CGLS iteration cap per column (default 500)             */
   int refine_chunk;    /* columns refined together: 8, 16 or 32 (default 16)           */
-  int use_graphs;      /* reserved, must be 0                                          */
+  int use_graphs;      /* ns_solve: unused; ns_batch_solve: >= 0 replays the captured
+                          graph (default 0), < 0 launches directly                  */
   int profile;         /* > 0: time every profile-th launch of each kernel class with
                           CUDA events on the library stream (ns_profile); 0 = off   */
 } ns_opts;
@@ -229,6 +230,79 @@ ns_status ns_project(int64_t n, int K, int w, const double* V, double* W, double
  * overwrites what it reads, so calls that overlap on the GPU (different streams,
  * no ordering) race and give wrong results. */
 ns_status ns_project_noalloc(int64_t n, int K, int w, const double* V, double* W, double* C, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Batched form: many independent symmetric PSD matrices (e.g. graph
+ * Laplacians), each solved with B_i = A_i + eps D_i (Sec. 5.1 form, d = 1), all
+ * in ONE persistent kernel launch replayed from a CUDA graph.  CTAs take
+ * instances from an atomic work queue, largest first; each CTA runs the whole
+ * method for its instance (Alg. 2 with the W recurrence of Sec. 4.2, locking,
+ * thick restart, the stopping rule of Sec. 4.3) with FP32 vectors and an FP64
+ * projected problem, then projects every locked vector onto null(A_i) by FP64
+ * CG and re-orthonormalizes in FP64.  Instance i draws D_i (Philox stream 0)
+ * and its start vector (stream 1) from key seed + i.
+ * ------------------------------------------------------------------------ */
+typedef struct ns_batch ns_batch;
+
+typedef struct {
+  int64_t count;          /* instances                                              */
+  int64_t total_nullity;  /* sum of the per-instance nullities                      */
+  int64_t failed;         /* instances whose status is not 0                        */
+  int64_t matvecs_total;  /* B applications summed over instances                   */
+  int64_t matvecs_max;
+  int64_t kernel_launches;/* library kernels launched by the last ns_batch_solve    */
+  int lanes;              /* threads per CSR row in the SpMV (autotuned: 1, 2 or 4) */
+  int grid;               /* CTAs of the persistent launch                          */
+  int blocks_per_sm;
+  int graph;              /* 1 when the launch was replayed from a CUDA graph       */
+  double t_solve_ms;      /* device time of the last solve (graph replay)          */
+  double t_tune_ms;       /* device time spent by the autotuner (first solve)       */
+} ns_batch_stats_t;
+
+/* ns_batch_create -- copy `count` CSR matrices (host memory) to the device.
+ *   n      : count row counts, each in [1, 2^31); every A_i is n_i x n_i
+ *   rowptr : the count local row-pointer arrays back to back (n_i + 1 int64 each,
+ *            starting at 0, non-decreasing)
+ *   colind : the entries' column indices back to back (int32, local to the instance)
+ *   vals   : the entries' values back to back (double, finite; also kept as FP32)
+ *   seed   : Philox key of instance 0 (instance i uses seed + i)
+ *   env    : allocator / stream as for ns_create, may be NULL (the library then
+ *            uses its own non-blocking stream)
+ * A_i must be symmetric PSD (not checked).  Errors: NS_ERR_INVALID_ARG (bad
+ * count, size or CSR structure; nothing allocated), NS_ERR_OOM, NS_ERR_CUDA. */
+ns_status ns_batch_create(ns_batch** out, int64_t count, const int64_t* n, const int64_t* rowptr,
+                          const int32_t* colind, const double* vals, uint64_t seed, const ns_env* env);
+
+/* ns_batch_solve -- solve every instance.  d must be 1; restart_len in [8, 64]
+ * and every n_i >= restart_len + 34 (the basis, its next vector and up to 32
+ * locked vectors must fit); tol > 0 (lock when the Ritz residual is at most
+ * max(tol, 1e-5) ||B_i||, FP32 vectors).  From opts (NULL = defaults) it reads
+ * eps, max_matvec (<= 0: min(100 n_i + 50 restart_len, 1e6) per instance),
+ * stop_factor, refine_tol (||A x|| <= refine_tol * ||A_i||_2), refine_maxit;
+ * precision is ignored (the batched form is always the mixed one); use_graphs
+ * >= 0 (default) replays the captured graph {queue reset, persistent launch},
+ * re-capturing it only when an argument changed, use_graphs < 0 launches
+ * directly.  The first
+ * solve autotunes the SpMV lanes on a sample of instances.  Returns NS_OK when
+ * every instance has status 0, else the first non-zero status among
+ * NS_ERR_NOT_CONVERGED (max_matvec reached, or more than 32 null vectors) and
+ * NS_ERR_REFINE; per-instance results stay readable either way. */
+ns_status ns_batch_solve(ns_batch* hb, int d, int restart_len, double tol, const ns_opts* opts);
+
+/* Per-instance results of the last solve (host arrays of `count` entries; any
+ * pointer may be NULL): nullity, status (0 ok, 4 max_matvec reached, 7
+ * refinement missed its tolerance, 8 more than 32 null vectors) and, in istats
+ * (count x 5, row-major), matvecs, restarts, partial reorthogonalizations, the
+ * largest refinement iteration count and the SM clock cycles the instance took. */
+ns_status ns_batch_results(const ns_batch* hb, int32_t* nullity, int32_t* status, int64_t* istats);
+
+/* Null-space basis of instance i: n_i x N_i column-major FP64 into out with
+ * leading dimension ld >= n_i (host memory, or device memory if out_on_device). */
+ns_status ns_batch_basis(const ns_batch* hb, int64_t i, double* out, int64_t ld, int out_on_device);
+
+ns_status ns_batch_stats(const ns_batch* hb, ns_batch_stats_t* s);
+const char* ns_batch_last_error(const ns_batch* hb);
+void ns_batch_destroy(ns_batch* hb);
 
 #ifdef __cplusplus
 }

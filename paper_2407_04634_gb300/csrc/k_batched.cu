@@ -1,0 +1,731 @@
+// Batched form: thousands of independent SPD matrices (graph Laplacians) solved in
+// ONE persistent launch.  Each CTA pops an instance index from an atomic work queue
+// (instances ordered by decreasing nnz) and runs the whole method for it on its
+// own: B = A + eps D applied by a CTA-wide SpMV, the single-vector Lanczos
+// recurrence (d = 1), the W recurrence of Sec. 4.2 with partial
+// reorthogonalization, the projected eigenproblem (FP64 parallel Jacobi in shared
+// memory), locking, thick restart (Sec. 4.1, retention capped at dimK/2), the
+// stopping rule of Sec. 4.3, and the FP64 CG projection onto null(A) followed by
+// FP64 re-orthonormalization.  Vectors are FP32, every scalar of the projected
+// problem FP64.  No CTA ever waits for another one.
+#include "../../include/nullspace.h"
+#include "ns_common.cuh"
+#include "ns_kernels.cuh"
+#include "ns_batch.cuh"
+
+namespace ns {
+
+// ---------------------------------------------------------------------------
+// CTA-level helpers (every thread of the block calls them)
+// ---------------------------------------------------------------------------
+struct CtaRed {
+  double w[kBThreads / 32];
+  double out[4];
+};
+
+__device__ inline double cta_sum(double v, CtaRed& r) {
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) r.w[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += r.w[k];
+    r.out[0] = s;
+  }
+  __syncthreads();
+  const double res = r.out[0];
+  __syncthreads();
+  return res;
+}
+
+__device__ inline double cta_max(double v, CtaRed& r) {
+  v = warp_max(v);
+  if ((threadIdx.x & 31) == 0) r.w[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s = fmax(s, r.w[k]);
+    r.out[0] = s;
+  }
+  __syncthreads();
+  const double res = r.out[0];
+  __syncthreads();
+  return res;
+}
+
+// two sums at once
+__device__ inline void cta_sum2(double a, double b, CtaRed& r, double& ra, double& rb) {
+  a = warp_sum(a);
+  b = warp_sum(b);
+  __shared__ double w2[kBThreads / 32];
+  if ((threadIdx.x & 31) == 0) {
+    r.w[threadIdx.x >> 5] = a;
+    w2[threadIdx.x >> 5] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0, t = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+      s += r.w[k];
+      t += w2[k];
+    }
+    r.out[0] = s;
+    r.out[1] = t;
+  }
+  __syncthreads();
+  ra = r.out[0];
+  rb = r.out[1];
+  __syncthreads();
+}
+
+// Philox normals of the start / replacement vectors (same recipe as the streams of
+// the single-instance path: Box-Muller on pairs, element e takes the pair e/2)
+__device__ inline float gauss_at(uint64_t seed, uint32_t stream, int64_t e) {
+  const U4 w = philox_at(seed, stream, (uint64_t)(e >> 1));
+  const uint64_t w0 = (uint64_t)w.x | ((uint64_t)w.y << 32);
+  const uint64_t w1 = (uint64_t)w.z | ((uint64_t)w.w << 32);
+  const double u1 = (double)((w0 >> 11) + 1) * 0x1.0p-53;
+  const double u2 = (double)(w1 >> 11) * 0x1.0p-53;
+  const double r = sqrt(-2.0 * log(u1));
+  double sn, cs;
+  sincospi(2.0 * u2, &sn, &cs);
+  return (float)((e & 1) ? r * sn : r * cs);
+}
+
+// y_i = sum_k a_ik x_k + eps D_i x_i - beta xprev_i ; returns per-thread partial of x_i y_i.
+// LANES threads share one row.
+template <int LANES>
+__device__ inline double cta_apply(const int64_t* __restrict__ rp, const int* __restrict__ col,
+                                   const float* __restrict__ val, int n, const float* __restrict__ x,
+                                   const float* __restrict__ Dv, float eps, const float* __restrict__ xprev,
+                                   float beta, float* __restrict__ y) {
+  const int lane = threadIdx.x % LANES, grp = threadIdx.x / LANES, ngrp = blockDim.x / LANES;
+  float part = 0.f;
+  for (int base = 0; base < n; base += ngrp) {  // uniform trip count for the shuffles
+    const int i = base + grp;
+    float s = 0.f;
+    if (i < n) {
+      const int64_t e = rp[i + 1];
+      for (int64_t k = rp[i] + lane; k < e; k += LANES) s = fmaf(__ldg(val + k), x[__ldg(col + k)], s);
+    }
+    if constexpr (LANES > 1) {
+#pragma unroll
+      for (int o = LANES / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    }
+    if (lane == 0 && i < n) {
+      const float xi = x[i];
+      s = fmaf(eps * Dv[i], xi, s);
+      if (xprev) s = fmaf(-beta, xprev[i], s);
+      y[i] = s;
+      part = fmaf(xi, s, part);
+    }
+  }
+  return (double)part;
+}
+
+// FP64 SpMV y = A x for the refinement (LANES = 1, thread per row)
+__device__ inline void cta_spmv64(const int64_t* __restrict__ rp, const int* __restrict__ col,
+                                  const double* __restrict__ val, int n, const double* __restrict__ x,
+                                  double* __restrict__ y) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double s = 0.0;
+    for (int64_t k = rp[i]; k < rp[i + 1]; ++k) s = fma(__ldg(val + k), x[__ldg(col + k)], s);
+    y[i] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// projected eigenproblem: cyclic Jacobi with the round-robin ordering (R/2
+// disjoint rotations per round, applied in parallel), FP64, shared memory.
+// A (R x R, row-major) is destroyed; on return th[] holds the eigenvalues in
+// ascending order and V[i*R + k] component i of eigenvector k.
+// ---------------------------------------------------------------------------
+struct JacobiScratch {
+  int p[kBMaxR / 2 + 1], q[kBMaxR / 2 + 1];
+  double c[kBMaxR / 2 + 1], s[kBMaxR / 2 + 1];
+  int perm[kBMaxR];
+};
+
+__device__ void cta_jacobi(double* A, double* V, double* th, int R, JacobiScratch& js, CtaRed& cr) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int t = tid; t < R * R; t += nt) V[t] = (t / R == t % R) ? 1.0 : 0.0;
+  __syncthreads();
+  const int Rp = R + (R & 1);  // one dummy index when R is odd
+  const int np = Rp / 2;
+  for (int sweep = 0; sweep < 20; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int t = tid; t < R * R; t += nt) {
+      const double a = A[t];
+      tot += a * a;
+      if (t / R != t % R) off += a * a;
+    }
+    cta_sum2(off, tot, cr, off, tot);
+    if (off <= 1e-30 * tot || off == 0.0) break;
+    for (int round = 0; round < Rp - 1; ++round) {
+      if (tid < np) {  // circle method: position 0 fixed, the others rotate
+        const int k = tid;
+        const int a = (k == 0) ? 0 : 1 + (k - 1 + round) % (Rp - 1);
+        const int kk = Rp - 1 - k;
+        const int b = 1 + (kk - 1 + round) % (Rp - 1);
+        const int pp = a < b ? a : b, qq = a < b ? b : a;
+        double c = 1.0, sn = 0.0;
+        if (qq < R) {
+          const double apq = A[pp * R + qq];
+          if (apq != 0.0) {
+            const double theta = (A[qq * R + qq] - A[pp * R + pp]) / (2.0 * apq);
+            const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+            c = 1.0 / sqrt(t * t + 1.0);
+            sn = t * c;
+          }
+        }
+        js.p[k] = pp;
+        js.q[k] = qq < R ? qq : pp;
+        js.c[k] = c;
+        js.s[k] = (qq < R) ? sn : 0.0;
+      }
+      __syncthreads();
+      for (int t = tid; t < np * R; t += nt) {  // rows p, q  (A <- J^T A)
+        const int k = t / R, j = t % R;
+        const int pp = js.p[k], qq = js.q[k];
+        if (pp == qq) continue;
+        const double c = js.c[k], sn = js.s[k];
+        const double apj = A[pp * R + j], aqj = A[qq * R + j];
+        A[pp * R + j] = c * apj - sn * aqj;
+        A[qq * R + j] = sn * apj + c * aqj;
+      }
+      __syncthreads();
+      for (int t = tid; t < np * R; t += nt) {  // columns p, q  (A <- A J, V <- V J)
+        const int k = t / R, i = t % R;
+        const int pp = js.p[k], qq = js.q[k];
+        if (pp == qq) continue;
+        const double c = js.c[k], sn = js.s[k];
+        const double aip = A[i * R + pp], aiq = A[i * R + qq];
+        A[i * R + pp] = c * aip - sn * aiq;
+        A[i * R + qq] = sn * aip + c * aiq;
+        const double vip = V[i * R + pp], viq = V[i * R + qq];
+        V[i * R + pp] = c * vip - sn * viq;
+        V[i * R + qq] = sn * vip + c * viq;
+      }
+      __syncthreads();
+    }
+  }
+  if (tid == 0) {  // ascending order (insertion sort on indices)
+    for (int i = 0; i < R; ++i) js.perm[i] = i;
+    for (int i = 1; i < R; ++i) {
+      const int key = js.perm[i];
+      const double kv = A[key * R + key];
+      int j = i - 1;
+      while (j >= 0 && A[js.perm[j] * R + js.perm[j]] > kv) {
+        js.perm[j + 1] = js.perm[j];
+        --j;
+      }
+      js.perm[j + 1] = key;
+    }
+  }
+  __syncthreads();
+  for (int k = tid; k < R; k += nt) th[k] = A[js.perm[k] * R + js.perm[k]];
+  __syncthreads();
+  for (int t = tid; t < R * R; t += nt) A[t] = V[(t / R) * R + js.perm[t % R]];
+  __syncthreads();
+  for (int t = tid; t < R * R; t += nt) V[t] = A[t];
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// one classical Gram-Schmidt pass of q against X(:, 0:kx) and Z(:, 0:kz)
+// (column-major, leading dimension n); coefficients accumulated in FP64
+// ---------------------------------------------------------------------------
+constexpr int kBChunk = 8;
+
+__device__ void cta_cgs(float* q, const float* X, int kx, const float* Z, int kz, int n, double* coef,
+                        CtaRed& cr) {
+  __shared__ double w8[kBThreads / 32][kBChunk];
+  const int K = kx + kz;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int k0 = 0; k0 < K; k0 += kBChunk) {
+    float acc[kBChunk];
+#pragma unroll
+    for (int c = 0; c < kBChunk; ++c) acc[c] = 0.f;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const float qi = q[i];
+#pragma unroll
+      for (int c = 0; c < kBChunk; ++c) {
+        const int k = k0 + c;
+        if (k < K) {
+          const float v = (k < kx) ? X[(int64_t)k * n + i] : Z[(int64_t)(k - kx) * n + i];
+          acc[c] = fmaf(v, qi, acc[c]);
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < kBChunk; ++c) {
+      const double v = warp_sum((double)acc[c]);
+      if (lane == 0) w8[warp][c] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < kBChunk && k0 + (int)threadIdx.x < K) {
+      double sm = 0.0;
+      for (int w = 0; w < nw; ++w) sm += w8[w][threadIdx.x];
+      coef[k0 + threadIdx.x] = sm;
+    }
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    float v = q[i];
+    for (int k = 0; k < K; ++k) {
+      const float b = (k < kx) ? X[(int64_t)k * n + i] : Z[(int64_t)(k - kx) * n + i];
+      v = fmaf(-(float)coef[k], b, v);
+    }
+    q[i] = v;
+  }
+  __syncthreads();
+  (void)cr;
+}
+
+// ||q||_2 (FP64 accumulation of FP32 squares)
+__device__ inline double cta_norm(const float* q, int n, CtaRed& cr) {
+  double loc = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) loc += (double)q[i] * (double)q[i];
+  return sqrt(cta_sum(loc, cr));
+}
+
+__device__ inline void cta_scale_to(const float* q, float* out, float f, int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) out[i] = q[i] * f;
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// one instance, the whole method (all threads of the CTA)
+// ---------------------------------------------------------------------------
+struct BState {
+  double alpha[kBMaxR + 1], beta[kBMaxR + 1];  // Xi_j, Gamma_j (d = 1)
+  double theta_keep[kBMaxR], F[kBMaxR];        // retained Ritz values and the arrow row
+  double th[kBMaxR], res[kBMaxR];              // eigenvalues of T, Ritz residuals
+  double wz[3][kBMaxR + 1];                    // rotating columns of W (active blocks)
+  double wx[3][kBMaxLock];                     // ... rows of the locked vectors
+  double xth[kBMaxLock], xrho[kBMaxLock];
+  double coef[kBMaxR + kBMaxLock + kBChunk];
+  int lock_list[kBMaxR], keep_list[kBMaxR];
+  int ncand, nkeep, nsmall, flags;
+};
+
+__device__ void replace_vec(float* dst, uint64_t seed, uint32_t stream, int n, const float* X, int nlock,
+                            const float* Z, int kz, BState& S, CtaRed& cr) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = gauss_at(seed, stream, i);
+  __syncthreads();
+  cta_cgs(dst, X, nlock, Z, kz, n, S.coef, cr);
+  cta_cgs(dst, X, nlock, Z, kz, n, S.coef, cr);
+  const double nr = cta_norm(dst, n, cr);
+  cta_scale_to(dst, dst, (float)(1.0 / nr), n);
+}
+
+template <int LANES>
+__device__ void solve_instance(const BatchArgs& a, int inst, float* ws32, double* ws64, double* As, double* Vs,
+                               BState& S, JacobiScratch& js, CtaRed& cr) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const long long clk0 = clock64();
+  const int n = a.nrows[inst];
+  const int64_t* rp = a.rowptr + a.rp_off[inst];
+  const int* col = a.col + a.nz_off[inst];
+  const float* val = a.val + a.nz_off[inst];
+  const double* val64 = a.val64 + a.nz_off[inst];
+  const int R = a.R;
+  const uint64_t seed = a.seed + (uint64_t)inst;  // instance i draws from the streams of seed + i
+  float* Z = ws32;                        // n x (R+1) Lanczos basis, column-major
+  float* Zt = Z + (int64_t)n * (R + 1);   // n x R restart / locking scratch
+  float* X = Zt + (int64_t)n * R;         // n x kBMaxLock locked vectors
+  float* Dv = X + (int64_t)n * kBMaxLock; // perturbation diagonal
+  float* qp = Dv + n;                     // Q'
+  const float eps = (float)a.eps;
+
+  // ||A||_inf and the longest row, D ~ U[0,1), start vector ~ N(0,1)
+  double mx = 0.0, ml = 0.0;
+  for (int i = tid; i < n; i += nt) {
+    double sm = 0.0;
+    for (int64_t k = rp[i]; k < rp[i + 1]; ++k) sm += fabs(val64[k]);
+    mx = fmax(mx, sm);
+    ml = fmax(ml, (double)(rp[i + 1] - rp[i]));
+    const U4 w = philox_at(seed, 0u, (uint64_t)i);
+    Dv[i] = (float)u53(w.x, w.y);
+    Z[i] = gauss_at(seed, 1u, i);
+  }
+  const double normB = cta_max(mx, cr) + a.eps;
+  const double maxrow = cta_max(ml, cr);
+  const double u = 0x1.0p-23;
+  const double u_d = sqrt(fmax(maxrow, 1.0)) * u * normB, u_ro = sqrt(u), bd_tol = 100.0 * u_d;
+  const double tol_eff = fmax(a.tol, 1e-5);
+  const long long max_mv = a.max_matvec > 0 ? (long long)a.max_matvec : min(100LL * n + 50LL * R, 1000000LL);
+  {
+    const double nq = cta_norm(Z, n, cr);
+    cta_scale_to(Z, Z, (float)(1.0 / nq), n);
+  }
+  int k0 = 0, nlock = 0, status = 0;
+  uint32_t bdcount = 0;
+  long long matvecs = 0, restarts = 0, reorths = 0, ev_first = -1, ev_last = -1;
+  int ev_first_k = 0, ev_total = 0, ev_count = 0;
+  double theta_max = 0.0;
+  while (true) {
+    const int r0 = k0;
+    // ---- first step of the cycle (Alg. 2 lines 6-8) ----
+    {
+      const float* q = Z + (int64_t)r0 * n;
+      const double al = cta_sum(cta_apply<LANES>(rp, col, val, n, q, Dv, eps, nullptr, 0.f, qp), cr);
+      ++matvecs;
+      cta_cgs(qp, X, nlock, Z, r0 + 1, n, S.coef, cr);
+      cta_cgs(qp, X, nlock, Z, r0 + 1, n, S.coef, cr);
+      double b = cta_norm(qp, n, cr);
+      float* qn = Z + (int64_t)(r0 + 1) * n;
+      if (b <= bd_tol) {
+        replace_vec(qn, seed, 2u + bdcount++, n, X, nlock, Z, r0 + 1, S, cr);
+        b = 0.0;
+      } else {
+        cta_scale_to(qp, qn, (float)(1.0 / b), n);
+      }
+      if (tid == 0) {
+        S.alpha[r0] = al;
+        S.beta[r0] = b;
+      }
+      for (int t = tid; t <= r0; t += nt) {
+        if (t < r0) S.wz[r0 % 3][t] = u_d;
+        S.wz[(r0 + 1) % 3][t] = u_d;
+      }
+      for (int k = tid; k < nlock; k += nt) S.wx[r0 % 3][k] = S.wx[(r0 + 1) % 3][k] = u_d;
+      __syncthreads();
+    }
+    // ---- inner steps (Alg. 2 lines 9-12) ----
+    for (int j = r0 + 1; j < R; ++j) {
+      float* qj = Z + (int64_t)j * n;
+      const float* qm = Z + (int64_t)(j - 1) * n;
+      float* qn = Z + (int64_t)(j + 1) * n;
+      const double al = cta_sum(cta_apply<LANES>(rp, col, val, n, qj, Dv, eps, qm, (float)S.beta[j - 1], qp), cr);
+      ++matvecs;
+      double loc = 0.0;
+      for (int i = tid; i < n; i += nt) {
+        const float v = fmaf(-(float)al, qj[i], qp[i]);
+        qp[i] = v;
+        loc += (double)v * (double)v;
+      }
+      const double b = sqrt(cta_sum(loc, cr));
+      if (tid == 0) S.alpha[j] = al;
+      if (b <= bd_tol) {  // breakdown: fresh direction, coupling zero, column j+1 of W reset
+        replace_vec(qn, seed, 2u + bdcount++, n, X, nlock, Z, j + 1, S, cr);
+        if (tid == 0) S.beta[j] = 0.0;
+        for (int t = tid; t <= j; t += nt) S.wz[(j + 1) % 3][t] = u_d;
+        for (int k = tid; k < nlock; k += nt) S.wx[(j + 1) % 3][k] = u_d;
+        __syncthreads();
+        continue;
+      }
+      cta_scale_to(qp, qn, (float)(1.0 / b), n);
+      if (tid == 0) {
+        S.beta[j] = b;
+        S.flags = 0;
+      }
+      __syncthreads();
+      // W recurrence, column j+1 (Sec. 4.2; d = 1 so every block norm is a scalar)
+      const double g = 1.0 / b, nXj = fabs(al), nGjm1 = S.beta[j - 1], ud2 = 2.0 * u_d;
+      double* cj = S.wz[j % 3];
+      double* cjm1 = S.wz[(j + 2) % 3];
+      double* cn = S.wz[(j + 1) % 3];
+#define WB(row, colp, colidx) ((row) < (colidx) ? (colp)[row] : 0.0)
+      double sumF = 0.0;
+      for (int i = 0; i < r0; ++i) sumF += cj[i] * fabs(S.F[i]);
+      int tz = 0, tx = 0;
+      for (int bb = tid; bb <= j; bb += nt) {
+        double v;
+        if (bb < r0)
+          v = WB(bb, cj, j) * (fabs(S.theta_keep[bb]) + nXj) + WB(r0, cj, j) * fabs(S.F[bb]) +
+              WB(bb, cjm1, j - 1) * nGjm1 + ud2;
+        else if (bb == r0)
+          v = WB(bb, cj, j) * (fabs(S.alpha[bb]) + nXj) + sumF + WB(bb + 1, cj, j) * S.beta[bb] +
+              WB(bb, cjm1, j - 1) * nGjm1 + ud2;
+        else
+          v = WB(bb, cj, j) * (fabs(S.alpha[bb]) + nXj) + WB(bb + 1, cj, j) * S.beta[bb] +
+              WB(bb - 1, cj, j) * S.beta[bb - 1] + WB(bb, cjm1, j - 1) * nGjm1 + ud2;
+        cn[bb] = g * v;
+        if (!(g * v <= u_ro)) tz = 1;
+      }
+#undef WB
+      double* xj = S.wx[j % 3];
+      double* xjm1 = S.wx[(j + 2) % 3];
+      double* xn = S.wx[(j + 1) % 3];
+      for (int k = tid; k < nlock; k += nt) {
+        const double v = g * (xj[k] * (S.xth[k] + nXj) + S.xrho[k] + xjm1[k] * nGjm1 + ud2);
+        xn[k] = v;
+        if (!(v <= u_ro)) tx = 1;
+      }
+      if (tz) atomicOr(&S.flags, 1);
+      if (tx) atomicOr(&S.flags, 2);
+      __syncthreads();
+      const int fl = S.flags;
+      if (fl) {  // one CGS pass of Q_j and Q_{j+1} against [X, Z_{j-1}] (semi-orthogonal blocks)
+        const int kx = (fl & 2) ? nlock : 0, kz = (fl & 1) ? j : 0;
+        cta_cgs(qj, X, kx, Z, kz, n, S.coef, cr);
+        double nr = cta_norm(qj, n, cr);
+        cta_scale_to(qj, qj, (float)(1.0 / nr), n);
+        cta_cgs(qn, X, kx, Z, kz, n, S.coef, cr);
+        nr = cta_norm(qn, n, cr);
+        cta_scale_to(qn, qn, (float)(1.0 / nr), n);
+        if (fl & 1)
+          for (int t = tid; t <= j; t += nt) {
+            if (t < j) cj[t] = u_d;
+            cn[t] = u_d;
+          }
+        if (fl & 2)
+          for (int k = tid; k < nlock; k += nt) xj[k] = xn[k] = u_d;
+        ++reorths;
+        __syncthreads();
+      }
+    }
+    // ---- restart (Alg. 2 lines 13-17) with locking ----
+    for (int t = tid; t < R * R; t += nt) {
+      const int r = t / R, c = t % R;
+      double v = 0.0;
+      if (r == c) v = (r < r0) ? S.theta_keep[r] : S.alpha[r];
+      else if (r < r0 && c == r0) v = S.F[r];
+      else if (c < r0 && r == r0) v = S.F[c];
+      else if (r >= r0 && c >= r0 && (r == c + 1 || c == r + 1)) v = S.beta[r < c ? r : c];
+      As[t] = v;
+    }
+    __syncthreads();
+    cta_jacobi(As, Vs, S.th, R, js, cr);
+    for (int c = tid; c < R; c += nt) S.res[c] = S.beta[R - 1] * fabs(Vs[(R - 1) * R + c]);
+    __syncthreads();
+    theta_max = fmax(theta_max, S.th[R - 1]);
+    if (tid == 0) {
+      int nsm = 0, nc = 0;
+      for (int c = 0; c < R; ++c)
+        if (S.th[c] < 3.0 * a.eps) {
+          ++nsm;
+          if (S.res[c] <= tol_eff * normB) S.lock_list[nc++] = c;
+        }
+      S.nsmall = nsm;
+      S.ncand = nc;
+    }
+    __syncthreads();
+    const int ncand = S.ncand;
+    int locked_now = 0;
+    for (int ci = 0; ci < ncand; ++ci) {
+      if (nlock >= kBMaxLock) {
+        status = 8;  // more null vectors than the per-instance capacity
+        break;
+      }
+      const int c = S.lock_list[ci];
+      for (int i = tid; i < n; i += nt) {
+        float sm = 0.f;
+        for (int jj = 0; jj < R; ++jj) sm = fmaf(Z[(int64_t)jj * n + i], (float)Vs[jj * R + c], sm);
+        Zt[i] = sm;
+      }
+      __syncthreads();
+      const double n0 = cta_norm(Zt, n, cr);
+      cta_cgs(Zt, X, nlock, Z, 0, n, S.coef, cr);
+      cta_cgs(Zt, X, nlock, Z, 0, n, S.coef, cr);
+      const double n1 = cta_norm(Zt, n, cr);
+      if (!(n1 >= 0.5 * n0)) continue;  // a copy of a locked vector (ghost)
+      cta_scale_to(Zt, X + (int64_t)nlock * n, (float)(1.0 / n1), n);
+      if (tid == 0) {
+        S.xth[nlock] = S.th[c];
+        S.xrho[nlock] = S.res[c];
+      }
+      ++nlock;
+      ++locked_now;
+    }
+    if (locked_now) {
+      if (ev_first < 0) {
+        ev_first = matvecs;
+        ev_first_k = locked_now;
+      }
+      ev_last = matvecs;
+      ev_total += locked_now;
+      ++ev_count;
+    }
+    const int n_unl = S.nsmall - ncand;
+    if (tid == 0) {  // retained set: capped at dimK/2, most converged small pairs first
+      int nk = (n_unl + R) / 2;
+      nk = max(nk, 1);
+      nk = min(nk, R - 2);
+      nk = min(nk, R / 2);
+      int cnt = 0;
+      // small, not candidates, by residual
+      for (int pass = 0; pass < 2; ++pass) {
+        for (int c = 0; c < R && cnt < R; ++c) {
+          bool cand = false;
+          for (int ci = 0; ci < ncand; ++ci) cand |= (S.lock_list[ci] == c);
+          if (cand) continue;
+          const bool sm = S.th[c] < 3.0 * a.eps;
+          if ((pass == 0) != sm) continue;
+          S.keep_list[cnt++] = c;
+        }
+        if (pass == 0) {  // insertion sort of the small ones by residual
+          for (int x = 1; x < cnt; ++x) {
+            const int key = S.keep_list[x];
+            int y = x - 1;
+            while (y >= 0 && S.res[S.keep_list[y]] > S.res[key]) {
+              S.keep_list[y + 1] = S.keep_list[y];
+              --y;
+            }
+            S.keep_list[y + 1] = key;
+          }
+        }
+      }
+      S.nkeep = min(nk, cnt);
+    }
+    __syncthreads();
+    const int nk = S.nkeep;
+    for (int i = tid; i < n; i += nt) {  // Z_new = Z V(:, keep)
+      for (int c = 0; c < nk; ++c) {
+        const int kc = S.keep_list[c];
+        float sm = 0.f;
+        for (int jj = 0; jj < R; ++jj) sm = fmaf(Z[(int64_t)jj * n + i], (float)Vs[jj * R + kc], sm);
+        Zt[(int64_t)c * n + i] = sm;
+      }
+      for (int c = 0; c < nk; ++c) Z[(int64_t)c * n + i] = Zt[(int64_t)c * n + i];
+    }
+    __syncthreads();
+    {  // Q_{l+1} against [X, Z_new] -> block nk (Alg. 2 line 16)
+      float* ql = Z + (int64_t)R * n;
+      cta_cgs(ql, X, nlock, Z, nk, n, S.coef, cr);
+      cta_cgs(ql, X, nlock, Z, nk, n, S.coef, cr);
+      double rho = cta_norm(ql, n, cr);
+      float* qk = Z + (int64_t)nk * n;
+      if (rho <= bd_tol) {
+        replace_vec(qk, seed, 2u + bdcount++, n, X, nlock, Z, nk, S, cr);
+        rho = 0.0;
+      } else {
+        cta_scale_to(ql, qk, (float)(1.0 / rho), n);
+      }
+      for (int c = tid; c < nk; c += nt) {
+        const int kc = S.keep_list[c];
+        S.F[c] = rho * S.beta[R - 1] * Vs[(R - 1) * R + kc];
+        S.theta_keep[c] = S.th[kc];
+      }
+      __syncthreads();
+    }
+    k0 = nk;
+    ++restarts;
+    // stopping rule (Sec. 4.3)
+    double sv = (double)R;
+    if (ev_count >= 2) sv = (double)(ev_last - ev_first) / fmax(1.0, (double)(ev_total - ev_first_k));
+    sv = fmax(sv, (double)R);
+    const long long since = matvecs - (ev_last >= 0 ? ev_last : 0);
+    if (status) break;
+    if (n_unl == 0 && locked_now == 0 && (double)since > a.stop_factor * sv) break;
+    if (matvecs >= max_mv) {
+      status = 4;
+      break;
+    }
+  }
+  // ---- FP64 projection of every locked vector onto null(A), then MGS twice ----
+  double* out = a.basis + a.out_off[inst];
+  double* r = ws64;
+  double* p = r + n;
+  double* Ap = p + n;
+  const double tol2 = (a.refine_tol * theta_max) * (a.refine_tol * theta_max);
+  long long iters_max = 0;
+  for (int k = 0; k < nlock; ++k) {
+    double* z = out + (int64_t)k * n;  // CG on A z = 0 from z = x keeps the null component of x
+    for (int i = tid; i < n; i += nt) z[i] = (double)X[(int64_t)k * n + i];
+    __syncthreads();
+    cta_spmv64(rp, col, val64, n, z, Ap);
+    double loc = 0.0;
+    for (int i = tid; i < n; i += nt) {
+      r[i] = -Ap[i];
+      p[i] = r[i];
+      loc += r[i] * r[i];
+    }
+    double rr = cta_sum(loc, cr);
+    int it = 0;
+    for (; it < a.refine_maxit && rr > tol2; ++it) {
+      cta_spmv64(rp, col, val64, n, p, Ap);
+      double l2 = 0.0;
+      for (int i = tid; i < n; i += nt) l2 += p[i] * Ap[i];
+      const double pAp = cta_sum(l2, cr);
+      if (!(pAp > 0.0)) break;
+      const double alpha = rr / pAp;
+      double l3 = 0.0;
+      for (int i = tid; i < n; i += nt) {
+        z[i] += alpha * p[i];
+        r[i] -= alpha * Ap[i];
+        l3 += r[i] * r[i];
+      }
+      const double rn = cta_sum(l3, cr);
+      const double beta = rn / rr;
+      for (int i = tid; i < n; i += nt) p[i] = r[i] + beta * p[i];
+      rr = rn;
+      __syncthreads();
+    }
+    iters_max = max(iters_max, (long long)it);
+    if (rr > tol2 && status == 0) status = 7;
+  }
+  for (int k = 0; k < nlock; ++k) {
+    double* zk = out + (int64_t)k * n;
+    for (int pass = 0; pass < 2; ++pass)
+      for (int jj = 0; jj < k; ++jj) {
+        const double* zj = out + (int64_t)jj * n;
+        double loc = 0.0;
+        for (int i = tid; i < n; i += nt) loc += zj[i] * zk[i];
+        const double c = cta_sum(loc, cr);
+        for (int i = tid; i < n; i += nt) zk[i] -= c * zj[i];
+        __syncthreads();
+      }
+    double loc = 0.0;
+    for (int i = tid; i < n; i += nt) loc += zk[i] * zk[i];
+    const double nr = sqrt(cta_sum(loc, cr));
+    for (int i = tid; i < n; i += nt) zk[i] /= nr;
+    __syncthreads();
+  }
+  if (tid == 0) {
+    a.nullity[inst] = nlock;
+    a.status[inst] = status;
+    long long* st = a.istats + kBStats * (int64_t)inst;
+    st[0] = matvecs;
+    st[1] = restarts;
+    st[2] = reorths;
+    st[3] = iters_max;
+    st[4] = clock64() - clk0;
+  }
+  __syncthreads();
+}
+
+template <int LANES>
+__global__ void __launch_bounds__(kBThreads) k_batched(BatchArgs a) {
+  extern __shared__ __align__(16) double dyn[];
+  __shared__ BState S;
+  __shared__ JacobiScratch js;
+  __shared__ CtaRed cr;
+  __shared__ int next;
+  double* As = dyn;
+  double* Vs = dyn + a.R * a.R;
+  float* ws32 = a.ws32 + (int64_t)blockIdx.x * a.ws32_stride;
+  double* ws64 = a.ws64 + (int64_t)blockIdx.x * a.ws64_stride;
+  while (true) {  // work queue: no CTA waits for another
+    if (threadIdx.x == 0) next = (int)atomicAdd(a.queue, 1u);
+    __syncthreads();
+    const int k = next;
+    __syncthreads();
+    if (k >= a.count) break;
+    solve_instance<LANES>(a, a.order[k], ws32, ws64, As, Vs, S, js, cr);
+  }
+}
+
+cudaError_t batched_prepare(int lanes, int R, int* blocks_per_sm) {
+  const int smem = (int)(sizeof(double) * 2 * (size_t)R * R);
+  const void* f = lanes == 1 ? (const void*)k_batched<1> : lanes == 2 ? (const void*)k_batched<2>
+                                                                        : (const void*)k_batched<4>;
+  cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * kBMaxR * kBMaxR * 8);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, kBThreads, smem);
+}
+
+void batched_launch(const BatchArgs& a, int lanes, int grid, cudaStream_t s) {
+  const size_t smem = sizeof(double) * 2 * (size_t)a.R * a.R;
+  switch (lanes) {
+    case 1: k_batched<1><<<grid, kBThreads, smem, s>>>(a); break;
+    case 2: k_batched<2><<<grid, kBThreads, smem, s>>>(a); break;
+    default: k_batched<4><<<grid, kBThreads, smem, s>>>(a); break;
+  }
+}
+
+size_t batched_ws32_per_slot(int nmax, int R) { return (size_t)nmax * (2 * R + 1 + kBMaxLock + 2) + 64; }
+size_t batched_ws64_per_slot(int nmax) { return (size_t)nmax * 3 + 64; }
+
+}  // namespace ns

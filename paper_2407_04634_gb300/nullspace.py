@@ -49,6 +49,16 @@ class NsStats(C.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class NsBatchStats(C.Structure):
+    _fields_ = [("count", C.c_int64), ("total_nullity", C.c_int64), ("failed", C.c_int64),
+                ("matvecs_total", C.c_int64), ("matvecs_max", C.c_int64), ("kernel_launches", C.c_int64),
+                ("lanes", C.c_int), ("grid", C.c_int), ("blocks_per_sm", C.c_int), ("graph", C.c_int),
+                ("t_solve_ms", C.c_double), ("t_tune_ms", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 # exported symbols and their prototypes (kept in sync with include/nullspace.h)
 class NsKernelProf(C.Structure):
     _fields_ = [("name", C.c_char * 24), ("launches", C.c_int64), ("sampled", C.c_int64),
@@ -75,6 +85,13 @@ SIGNATURES = {
     "ns_syev": (C.c_int, [C.c_int, _P, _P, _P]),
     "ns_project": (C.c_int, [C.c_int64, C.c_int, C.c_int, _P, _P, _P, C.c_int]),
     "ns_project_noalloc": (C.c_int, [C.c_int64, C.c_int, C.c_int, _P, _P, _P, _P]),
+    "ns_batch_create": (C.c_int, [C.POINTER(_P), C.c_int64, _P, _P, _P, _P, C.c_uint64, C.POINTER(NsEnv)]),
+    "ns_batch_solve": (C.c_int, [_P, C.c_int, C.c_int, C.c_double, C.POINTER(NsOpts)]),
+    "ns_batch_results": (C.c_int, [_P, _P, _P, _P]),
+    "ns_batch_basis": (C.c_int, [_P, C.c_int64, _P, C.c_int64, C.c_int]),
+    "ns_batch_stats": (C.c_int, [_P, C.POINTER(NsBatchStats)]),
+    "ns_batch_last_error": (C.c_char_p, [_P]),
+    "ns_batch_destroy": (None, [_P]),
 }
 
 _LIB = None
@@ -280,3 +297,78 @@ def project(V: np.ndarray, W: np.ndarray, precision: str = "fp64"):
     if st != NS_OK:
         raise NullspaceError(st, "ns_project")
     return Wc, Cc
+
+
+BATCH_STATUS = {0: "ok", 4: "max_matvec reached", 7: "refinement missed its tolerance", 8: "more than 32 null vectors"}
+
+
+class Batch:
+    """Many independent symmetric PSD matrices solved in one persistent launch (ns_batch_*).
+
+    mats: sequence of (rowptr, colind, vals) host arrays (square CSR, local column
+    indices), or objects with .rowptr/.colind/.vals.  Instance i uses Philox key
+    seed + i.
+    """
+
+    def __init__(self, mats, seed: int, env: str | None = "torch"):
+        self.lib = load()
+        rps, cis, vas, ns_ = [], [], [], []
+        for M in mats:
+            rp, ci, va = (M.rowptr, M.colind, M.vals) if hasattr(M, "rowptr") else M
+            rps.append(np.asarray(rp, dtype=np.int64))
+            cis.append(np.asarray(ci, dtype=np.int32))
+            vas.append(np.asarray(va, dtype=np.float64))
+            ns_.append(len(rp) - 1)
+        self.count = len(ns_)
+        self.n = np.asarray(ns_, dtype=np.int64)
+        self._keep = (np.ascontiguousarray(self.n), np.ascontiguousarray(np.concatenate(rps)),
+                      np.ascontiguousarray(np.concatenate(cis)), np.ascontiguousarray(np.concatenate(vas)))
+        self._env = torch_env() if env == "torch" else None
+        h = C.c_void_p()
+        st = self.lib.ns_batch_create(C.byref(h), self.count, *[_ptr(a) for a in self._keep], C.c_uint64(seed),
+                                      C.byref(self._env) if self._env is not None else None)
+        if st != NS_OK:
+            raise NullspaceError(st, "ns_batch_create failed")
+        self.h = h
+
+    def _check(self, st, what):
+        if st != NS_OK:
+            raise NullspaceError(st, f"{what}: {self.lib.ns_batch_last_error(self.h).decode()}")
+
+    def solve(self, restart_len: int, tol: float, check: bool = True, **opts) -> int:
+        o = default_opts(**opts)
+        st = self.lib.ns_batch_solve(self.h, 1, int(restart_len), float(tol), C.byref(o))
+        if check:
+            self._check(st, "ns_batch_solve")
+        return st
+
+    def results(self):
+        """(nullity[count], status[count], istats[count, 5]) of the last solve."""
+        N = np.zeros(self.count, dtype=np.int32)
+        S = np.zeros(self.count, dtype=np.int32)
+        I = np.zeros((self.count, 5), dtype=np.int64)
+        self._check(self.lib.ns_batch_results(self.h, _ptr(N), _ptr(S), _ptr(I)), "ns_batch_results")
+        return N, S, I
+
+    def basis(self, i: int) -> np.ndarray:
+        N, _, _ = self.results()
+        n = int(self.n[i])
+        X = np.zeros((int(N[i]), n), dtype=np.float64)
+        self._check(self.lib.ns_batch_basis(self.h, int(i), _ptr(X), n, 0), "ns_batch_basis")
+        return X.T
+
+    def stats(self) -> dict:
+        s = NsBatchStats()
+        self._check(self.lib.ns_batch_stats(self.h, C.byref(s)), "ns_batch_stats")
+        return s.as_dict()
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.ns_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
