@@ -57,6 +57,9 @@ WORKLOADS = {
     "incidence": dict(cfg=3, mode="normal", d=4, restart=160, precision="mixed", cpu_scale=0.02, ref_scale=0.01),
     # configuration 4: rectangular N(0,1) matrix with planted sign-flipped column copies
     "copies": dict(cfg=4, mode="normal", d=2, restart=150, precision="mixed", cpu_scale=0.01, ref_scale=0.005),
+    # configuration 5: 4,096 independent Laplacians in one persistent launch (batched form)
+    "batched": dict(cfg=5, mode="spd", d=1, restart=40, precision="mixed", cpu_scale=0.01, ref_scale=0.005,
+                    tol=1e-5),
 }
 
 
@@ -78,7 +81,7 @@ def ncu_traffic_ratio(cls):
 def workload_params(args):
     wl = WORKLOADS[args.workload]
     return dict(name=args.workload, cfg=wl["cfg"], mode=wl["mode"], scale=args.scale,
-                d=args.d or wl["d"], restart=wl["restart"], tol=1e-10,
+                d=args.d or wl["d"], restart=wl["restart"], tol=wl.get("tol", 1e-10),
                 precision=args.precision or wl["precision"], solver_seed=1000 + wl["cfg"] - 1,
                 cpu_scale=wl["cpu_scale"], ref_scale=wl["ref_scale"])
 
@@ -181,16 +184,43 @@ print(json.dumps(dict(N=int(r.N), expect=int(w.nullity), n=int(A.shape[1]), seco
 def run_oracle_sample(p, scale):
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
-    code = ORACLE_SNIPPET.format(root=ROOT, cfg=p["cfg"], scale=scale, mode=p["mode"], d=p["d"],
-                                 restart=p["restart"], tol=p["tol"], sseed=p["solver_seed"])
+    snippet = BATCH_ORACLE_SNIPPET if p["cfg"] == 5 else ORACLE_SNIPPET
+    code = snippet.format(root=ROOT, cfg=p["cfg"], scale=scale, mode=p["mode"], d=p["d"],
+                          restart=p["restart"], tol=p["tol"], sseed=p["solver_seed"])
     out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
     if out.returncode != 0:
         raise RuntimeError(out.stderr[-2000:])
     return json.loads(out.stdout.strip().splitlines()[-1])
 
 
+BATCH_ORACLE_SNIPPET = r"""
+import json, os, sys, time
+sys.path.insert(0, {root!r})
+import numpy as np
+from workloads import make_config
+from oracle import lanczos_nullspace
+ws, _ = make_config(5, {scale})
+N = E = n = mv = 0
+res = 0.0
+t = time.perf_counter()
+for i, w in enumerate(ws):
+    A = w.A.to_scipy()
+    r = lanczos_nullspace(A, "spd", 1, {restart}, tol={tol}, seed={sseed} + i)
+    N += int(r.N); E += int(w.nullity); n += int(A.shape[1]); mv += int(r.stats["matvecs"])
+    if r.N:
+        res = max(res, float(np.linalg.norm(A @ r.X) / r.normA))
+dt = time.perf_counter() - t
+print(json.dumps(dict(N=N, expect=E, n=n, seconds=dt, matvecs=mv, residual=res, instances=len(ws))))
+"""
+
+
 def cpu_baseline(p):
     r = run_oracle_sample(p, p["cpu_scale"])
+    if p["cfg"] == 5:
+        return {"value": r["N"] / r["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": f"the first {r['instances']} of the 4,096 instances (sum n={r['n']:,}, nullity "
+                          f"{r['N']}, expected {r['expect']}), single-threaded FP64 oracle, {r['seconds']:.1f} s, "
+                          f"{r['matvecs']} matvecs, residual {r['residual']:.1e}"}
     return {"value": r["N"] / r["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"same generator scaled by {p['cpu_scale']} (n={r['n']:,}, nullity {r['N']}, "
                       f"expected {r['expect']}), single-threaded FP64 oracle, {r['seconds']:.1f} s, "
@@ -212,8 +242,12 @@ def bench_reference(args, rank):
             Ns.append(r["N"])
     tot = sum(times)
     val = sum(Ns) / tot
-    sample = (f"same generator scaled by {p['ref_scale']} (n={last['n']:,}, nullity {last['N']}), "
-              f"single-threaded FP64 oracle")
+    if p["cfg"] == 5:
+        sample = (f"the first {last['instances']} of the 4,096 instances (sum n={last['n']:,}, nullity "
+                  f"{last['N']}), single-threaded FP64 oracle, one solve per instance")
+    else:
+        sample = (f"same generator scaled by {p['ref_scale']} (n={last['n']:,}, nullity {last['N']}), "
+                  f"single-threaded FP64 oracle")
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -246,6 +280,183 @@ def kernel_probe(ns, h, w, p):
     print(json.dumps({"kernel_probe": p["name"], **out}), flush=True)
 
 
+# ----------------------------------------------------------------- batched --
+
+def bench_batched(args, world, rank, local):
+    """Configuration 5: 4,096 Laplacians (n log-uniform in [200, 20000], 1-8 cycle-union
+    components each) in one persistent launch per step, replayed from a CUDA graph.
+    Ranks take disjoint slices of the instance list (weak scaling, no collective)."""
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2407_04634_gb300 import nullspace as ns
+    from workloads import make_config
+    from oracle import norm2_A  # validity check of sampled outputs, outside the timed region
+
+    p = workload_params(args)
+    ws_all, _ = make_config(5, args.scale)
+    lo, hi = rank * len(ws_all) // world, (rank + 1) * len(ws_all) // world
+    ws = ws_all[lo:hi]  # contiguous slice: global instance i keeps the key solver_seed + i
+    seed = p["solver_seed"] + lo
+    n = np.array([w.A.n for w in ws], dtype=np.int64)
+    rp = np.concatenate([w.A.rowptr for w in ws])
+    ci = np.concatenate([w.A.colind for w in ws])
+    va = np.concatenate([w.A.vals for w in ws])
+    nnz = np.array([w.A.nnz for w in ws], dtype=np.int64)
+    expect = np.array([w.nullity for w in ws])
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        b = ns.Batch.from_arrays(n, rp, ci, va, seed)
+
+        def step(**kw):
+            st = b.solve(p["restart"], p["tol"], check=False, eps=1e-3, batch_block=args.batch_block, **kw)
+            N, S, I = b.results()
+            return st, N, S, I
+
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        clocks = ClockSampler(local)
+        clocks.start()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        outs = [step() for _ in range(args.steps)]
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    bst = b.stats()
+
+    def valid(o):
+        st, N, S, _ = o
+        return st == ns.NS_OK and (S == 0).all() and (N == expect).all()
+
+    units = float(sum(int(o[1].sum()) for o in outs if valid(o)))
+    all_valid = all(valid(o) for o in outs)
+    # sampled residual check of the last step (outside the timed region)
+    worst = 0.0
+    for k in range(0, len(ws), max(1, len(ws) // 24)):
+        X = b.basis(k)
+        A = ws[k].A.to_scipy()
+        if X.shape[1]:
+            worst = max(worst, float(np.linalg.norm(A @ X) / norm2_A(A, "spd")))
+    all_valid = all_valid and worst <= 1e-8
+    t_max = ms
+    if dist:
+        tt = torch.tensor([ms, units], device="cuda", dtype=torch.float64)
+        tmax = tt.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tt, op=dist.ReduceOp.SUM)
+        t_max, units = float(tmax[0]), float(tt[1])
+    value = units / (t_max / 1e3) if all_valid else 0.0
+
+    # roofline of the persistent kernel: algorithmic bytes of the B applications
+    I = outs[-1][3]
+    mv = I[:, 0].astype(np.float64)
+    bytes_step = float((mv * (8.0 * nnz + 28.0 * n)).sum())
+    ms_kernel = bst["t_solve_ms"]
+    ach = bytes_step / (ms_kernel / 1e3) / 1e9
+    pk = peaks()
+    roofline = {"kernel": "k_batched", "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / pk["hbm_gbs"], "traffic": None, "peak_src": pk["src"],
+                "bytes_per_launch": bytes_step, "ms_per_launch": ms_kernel,
+                "note": "bytes = sum_i matvecs_i (8 nnz_i + 28 n_i); each CTA's instance is largely L2-resident, "
+                        "so the kernel is bound by CTA-wide reductions, not HBM"}
+
+    # end-to-end: pinned host CSR -> ns_batch_create -> ns_batch_solve -> every basis to pinned host
+    rp_p = torch.from_numpy(rp).pin_memory()
+    ci_p = torch.from_numpy(ci).pin_memory()
+    va_p = torch.from_numpy(va).pin_memory()
+    out = torch.empty(int((n * expect).sum()), dtype=torch.float64).pin_memory()
+    offs = np.concatenate([[0], np.cumsum(n * expect)[:-1]])
+    h2d = rp.nbytes + ci.nbytes + va.nbytes + n.nbytes
+    d2h = out.numel() * 8 + len(ws) * (4 + 4 + 40)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_units = 0
+    for _ in range(args.e2e_steps):
+        with torch.cuda.stream(stream):
+            be = ns.Batch.from_arrays(n, rp_p.numpy(), ci_p.numpy(), va_p.numpy(), seed)
+            st = be.solve(p["restart"], p["tol"], check=False, eps=1e-3, batch_block=args.batch_block)
+            N, S, _ = be.results()
+            if st == ns.NS_OK and (N == expect).all():
+                base = out.data_ptr()
+                for k in range(len(ws)):
+                    be.lib.ns_batch_basis(be.h, k, ns.C.c_void_p(base + 8 * int(offs[k])), int(n[k]), 0)
+                e2e_units += int(N.sum())
+            be.close()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": e2e_units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+           "steps": args.e2e_steps}
+
+    # the same instances through the single-instance FP64 path, one ns_solve each (a sample)
+    loop_t, loop_N, loop_ok, picked = 0.0, 0, True, list(range(0, len(ws), max(1, len(ws) // 32)))
+    with torch.cuda.stream(stream):
+        for k in picked:
+            A = ws[k].A
+            hk = ns.Handle(A.rowptr, A.colind, A.vals, A.m, A.n, seed + k, "spd")
+            hk.solve(1, p["restart"], p["tol"], check=False, precision="fp64")  # warm-up of this handle
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = hk.solve(1, p["restart"], p["tol"], check=False, precision="fp64")
+            e1.record(stream)
+            torch.cuda.synchronize()
+            loop_t += e0.elapsed_time(e1) / 1e3
+            loop_ok = loop_ok and r.status == ns.NS_OK and r.nullity == ws[k].nullity
+            loop_N += r.nullity
+            hk.close()
+    loop = {"value": loop_N / loop_t if loop_t > 0 else None, "unit": UNIT, "valid": bool(loop_ok),
+            "sample": f"{len(picked)} of the {len(ws)} instances (every {max(1, len(ws) // 32)}th), "
+                      f"one FP64 ns_solve each (d=1, restart {p['restart']}, tol {p['tol']:g}), "
+                      f"CUDA-event time of the solve, warm handle"}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        try:
+            cpu = cpu_baseline(p)
+        except Exception as e:  # reported, not hidden
+            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
+    mats = 8 * int(nnz.sum()) + 12 * int(n.sum())
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": f"{len(ws_all):,} independent graph Laplacians, n log-uniform in [200, 20000], "
+                                   f"1-8 components of 3 random Hamiltonian cycles each (mean degree 6), "
+                                   f"sum n={int(sum(w.A.n for w in ws_all)):,}, sum nnz="
+                                   f"{int(sum(w.A.nnz for w in ws_all)):,}, total nullity "
+                                   f"{int(sum(w.nullity for w in ws_all))}; batched persistent launch "
+                                   f"(graph replay), d=1, restart {p['restart']}, tol {p['tol']:g}",
+                       "instances": len(ws_all), "d": 1, "restart_len": p["restart"], "tol": p["tol"],
+                       "eps": 1e-3, "precision": "mixed", "mode": "spd",
+                       "l2": "inputs larger than L2 (matrices %.2f GB on the device)" % (mats / 1e9)},
+            "valid": bool(all_valid), "residual_max_sampled": worst,
+            "gpu_launches": int(bst["kernel_launches"]) * args.steps, "clocks": clk, "roofline": roofline,
+            "e2e": e2e, "cpu_baseline": cpu, "loop_fp64": loop,
+            "batched_vs_loop_fp64": (value / loop["value"]) if loop["value"] else None,
+            "batch": {k: bst[k] for k in ("lanes", "block", "grid", "blocks_per_sm", "graph", "t_solve_ms", "t_tune_ms",
+                                          "matvecs_total", "matvecs_max", "total_nullity", "failed")},
+            "phase_share": {k: float(I[:, 5 + j].sum() / max(1, I[:, 4].sum()))
+                            for j, k in enumerate(ns.BATCH_ISTATS[5:11])},
+            "jacobi_sweeps_per_restart": {"fp32": float(I[:, 11].sum() / max(1, I[:, 1].sum())),
+                                          "fp64": float(I[:, 12].sum() / max(1, I[:, 1].sum()))}}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
 # -------------------------------------------------------------------- ours --
 
 def main():
@@ -262,6 +473,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--scale", type=float, default=1.0, help="workload scale (< 1 is for profiling only)")
     ap.add_argument("--kernel-probe", action="store_true", help="launch a few hot kernels, no bench line")
+    ap.add_argument("--batch-block", type=int, default=0, choices=[0, 128, 256],
+                    help="threads per CTA of the batched kernel (0 = library default)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -269,6 +482,9 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         bench_reference(args, rank)
+        return
+    if args.workload == "batched":
+        bench_batched(args, world, rank, local)
         return
 
     import numpy as np

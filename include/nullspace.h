@@ -84,6 +84,7 @@ typedef struct {
                           graph (default 0), < 0 launches directly                  */
   int profile;         /* > 0: time every profile-th launch of each kernel class with
                           CUDA events on the library stream (ns_profile); 0 = off   */
+  int batch_block;     /* ns_batch_solve: threads per CTA, 128 or 256; 0 = default (128) */
 } ns_opts;
 
 typedef struct {
@@ -254,6 +255,7 @@ typedef struct {
   int lanes;              /* threads per CSR row in the SpMV (autotuned: 1, 2 or 4) */
   int grid;               /* CTAs of the persistent launch                          */
   int blocks_per_sm;
+  int block;              /* threads per CTA                                        */
   int graph;              /* 1 when the launch was replayed from a CUDA graph       */
   double t_solve_ms;      /* device time of the last solve (graph replay)          */
   double t_tune_ms;       /* device time spent by the autotuner (first solve)       */
@@ -292,8 +294,11 @@ ns_status ns_batch_solve(ns_batch* hb, int d, int restart_len, double tol, const
 /* Per-instance results of the last solve (host arrays of `count` entries; any
  * pointer may be NULL): nullity, status (0 ok, 4 max_matvec reached, 7
  * refinement missed its tolerance, 8 more than 32 null vectors) and, in istats
- * (count x 5, row-major), matvecs, restarts, partial reorthogonalizations, the
- * largest refinement iteration count and the SM clock cycles the instance took. */
+ * (count x 13, row-major), matvecs, restarts, partial reorthogonalizations, the
+ * largest refinement iteration count, the SM clock cycles the instance took,
+ * those cycles split by phase (Lanczos steps, partial reorthogonalization,
+ * projected eigenproblem, locking, thick restart, refinement), and the FP32 and
+ * FP64 Jacobi sweeps spent on the projected problems. */
 ns_status ns_batch_results(const ns_batch* hb, int32_t* nullity, int32_t* status, int64_t* istats);
 
 /* Null-space basis of instance i: n_i x N_i column-major FP64 into out with

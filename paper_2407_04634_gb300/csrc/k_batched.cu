@@ -99,8 +99,54 @@ __device__ inline double cta_apply(const int64_t* __restrict__ rp, const int* __
                                    const float* __restrict__ val, int n, const float* __restrict__ x,
                                    const float* __restrict__ Dv, float eps, const float* __restrict__ xprev,
                                    float beta, float* __restrict__ y) {
-  const int lane = threadIdx.x % LANES, grp = threadIdx.x / LANES, ngrp = blockDim.x / LANES;
   float part = 0.f;
+  if constexpr (LANES == 1) {  // thread per row, two rows at a time, four entries of each per round
+    const int nt = blockDim.x;
+    for (int i0 = threadIdx.x; i0 < n; i0 += 2 * nt) {
+      const int i1 = i0 + nt;
+      const bool h1 = i1 < n;
+      int64_t k0 = rp[i0];
+      const int64_t e0 = rp[i0 + 1];
+      int64_t k1 = h1 ? rp[i1] : 0;
+      const int64_t e1 = h1 ? rp[i1 + 1] : 0;
+      float s0 = 0.f, s1 = 0.f;
+      while (k0 < e0 || k1 < e1) {
+        int c0[4], c1[4];
+        float v0[4], v1[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const bool a0 = k0 + u < e0, a1 = k1 + u < e1;
+          c0[u] = a0 ? __ldg(col + k0 + u) : i0;
+          v0[u] = a0 ? __ldg(val + k0 + u) : 0.f;
+          c1[u] = a1 ? __ldg(col + k1 + u) : i0;
+          v1[u] = a1 ? __ldg(val + k1 + u) : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          s0 = fmaf(v0[u], x[c0[u]], s0);
+          s1 = fmaf(v1[u], x[c1[u]], s1);
+        }
+        k0 += 4;
+        k1 += 4;
+      }
+      {
+        const float xi = x[i0];
+        s0 = fmaf(eps * Dv[i0], xi, s0);
+        if (xprev) s0 = fmaf(-beta, xprev[i0], s0);
+        y[i0] = s0;
+        part = fmaf(xi, s0, part);
+      }
+      if (h1) {
+        const float xi = x[i1];
+        s1 = fmaf(eps * Dv[i1], xi, s1);
+        if (xprev) s1 = fmaf(-beta, xprev[i1], s1);
+        y[i1] = s1;
+        part = fmaf(xi, s1, part);
+      }
+    }
+    return (double)part;
+  }
+  const int lane = threadIdx.x % LANES, grp = threadIdx.x / LANES, ngrp = blockDim.x / LANES;
   for (int base = 0; base < n; base += ngrp) {  // uniform trip count for the shuffles
     const int i = base + grp;
     float s = 0.f;
@@ -146,21 +192,29 @@ struct JacobiScratch {
   int perm[kBMaxR];
 };
 
-__device__ void cta_jacobi(double* A, double* V, double* th, int R, JacobiScratch& js, CtaRed& cr) {
+// Cyclic Jacobi sweeps in precision F on A (R x R, row-major, symmetric); V
+// accumulates the rotations (V <- V J).  Stops when the squared off-diagonal
+// mass is at most rel * the squared Frobenius norm, or after max_sweeps.
+template <typename F>
+__device__ int cta_jacobi_sweeps(F* A, F* V, int R, bool init_identity, double rel, int max_sweeps,
+                                 JacobiScratch& js, CtaRed& cr) {
   const int tid = threadIdx.x, nt = blockDim.x;
-  for (int t = tid; t < R * R; t += nt) V[t] = (t / R == t % R) ? 1.0 : 0.0;
-  __syncthreads();
+  if (init_identity) {
+    for (int t = tid; t < R * R; t += nt) V[t] = (t / R == t % R) ? F(1) : F(0);
+    __syncthreads();
+  }
   const int Rp = R + (R & 1);  // one dummy index when R is odd
   const int np = Rp / 2;
-  for (int sweep = 0; sweep < 20; ++sweep) {
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
     double off = 0.0, tot = 0.0;
     for (int t = tid; t < R * R; t += nt) {
-      const double a = A[t];
+      const double a = (double)A[t];
       tot += a * a;
       if (t / R != t % R) off += a * a;
     }
     cta_sum2(off, tot, cr, off, tot);
-    if (off <= 1e-30 * tot || off == 0.0) break;
+    if (off <= rel * tot || off == 0.0) break;
     for (int round = 0; round < Rp - 1; ++round) {
       if (tid < np) {  // circle method: position 0 fixed, the others rotate
         const int k = tid;
@@ -168,28 +222,28 @@ __device__ void cta_jacobi(double* A, double* V, double* th, int R, JacobiScratc
         const int kk = Rp - 1 - k;
         const int b = 1 + (kk - 1 + round) % (Rp - 1);
         const int pp = a < b ? a : b, qq = a < b ? b : a;
-        double c = 1.0, sn = 0.0;
+        F c = F(1), sn = F(0);
         if (qq < R) {
-          const double apq = A[pp * R + qq];
-          if (apq != 0.0) {
-            const double theta = (A[qq * R + qq] - A[pp * R + pp]) / (2.0 * apq);
-            const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-            c = 1.0 / sqrt(t * t + 1.0);
+          const F apq = A[pp * R + qq];
+          if (apq != F(0)) {
+            const F theta = (A[qq * R + qq] - A[pp * R + pp]) / (F(2) * apq);
+            const F t = (theta >= F(0) ? F(1) : F(-1)) / (fabs(theta) + sqrt(theta * theta + F(1)));
+            c = F(1) / sqrt(t * t + F(1));
             sn = t * c;
           }
         }
         js.p[k] = pp;
         js.q[k] = qq < R ? qq : pp;
-        js.c[k] = c;
-        js.s[k] = (qq < R) ? sn : 0.0;
+        js.c[k] = (double)c;
+        js.s[k] = (qq < R) ? (double)sn : 0.0;
       }
       __syncthreads();
       for (int t = tid; t < np * R; t += nt) {  // rows p, q  (A <- J^T A)
         const int k = t / R, j = t % R;
         const int pp = js.p[k], qq = js.q[k];
         if (pp == qq) continue;
-        const double c = js.c[k], sn = js.s[k];
-        const double apj = A[pp * R + j], aqj = A[qq * R + j];
+        const F c = (F)js.c[k], sn = (F)js.s[k];
+        const F apj = A[pp * R + j], aqj = A[qq * R + j];
         A[pp * R + j] = c * apj - sn * aqj;
         A[qq * R + j] = sn * apj + c * aqj;
       }
@@ -198,24 +252,91 @@ __device__ void cta_jacobi(double* A, double* V, double* th, int R, JacobiScratc
         const int k = t / R, i = t % R;
         const int pp = js.p[k], qq = js.q[k];
         if (pp == qq) continue;
-        const double c = js.c[k], sn = js.s[k];
-        const double aip = A[i * R + pp], aiq = A[i * R + qq];
+        const F c = (F)js.c[k], sn = (F)js.s[k];
+        const F aip = A[i * R + pp], aiq = A[i * R + qq];
         A[i * R + pp] = c * aip - sn * aiq;
         A[i * R + qq] = sn * aip + c * aiq;
-        const double vip = V[i * R + pp], viq = V[i * R + qq];
+        const F vip = V[i * R + pp], viq = V[i * R + qq];
         V[i * R + pp] = c * vip - sn * viq;
         V[i * R + qq] = sn * vip + c * viq;
       }
       __syncthreads();
     }
   }
+  return sweep;
+}
+
+// Projected eigenproblem of T (Alg. 2 line 13), FP64 result at a fraction of the
+// FP64 work of a cold FP64 Jacobi:
+//   1. Jacobi in FP32 on a rounded copy of T           -> V32 (orthogonal to ~1e-7)
+//   2. FP64: V = V32 (3I - V32^T V32)/2 (one Newton-Schulz step, orthonormal in FP64)
+//   3. FP64: B = V^T T V (T applied from its arrow + tridiagonal structure)
+//   4. FP64 Jacobi on B (nearly diagonal: one or two sweeps) -> Q
+//   5. eigenvalues diag(B), eigenvectors V Q, sorted ascending.
+// As holds T on entry (row-major) and is destroyed; Wt is R*R doubles of scratch.
+// On return th[k] is the k-th smallest eigenvalue and Vs[i*R + k] component i of
+// its eigenvector.
+__device__ int2 cta_eig(double* As, double* Vs, double* Wt, double* th, int R, int r0, const double* diag,
+                        const double* F, const double* beta, JacobiScratch& js, CtaRed& cr) {
+  const int tid = threadIdx.x, nt = blockDim.x, RR = R * R;
+  float* A32 = reinterpret_cast<float*>(Wt);
+  float* V32 = A32 + RR;
+  for (int t = tid; t < RR; t += nt) A32[t] = (float)As[t];
+  __syncthreads();
+  const int sw32 = cta_jacobi_sweeps<float>(A32, V32, R, true, 1e-11, 12, js, cr);
+  for (int t = tid; t < RR; t += nt) Vs[t] = (double)V32[t];
+  __syncthreads();
+  for (int t = tid; t < RR; t += nt) {  // As = 1.5 I - 0.5 V^T V
+    const int r = t / R, c = t % R;
+    double g = 0.0;
+    for (int k = 0; k < R; ++k) g = fma(Vs[k * R + r], Vs[k * R + c], g);
+    As[t] = (r == c ? 1.5 : 0.0) - 0.5 * g;
+  }
+  __syncthreads();
+  for (int t = tid; t < RR; t += nt) {  // Wt = V As
+    const int r = t / R, c = t % R;
+    double g = 0.0;
+    for (int k = 0; k < R; ++k) g = fma(Vs[r * R + k], As[k * R + c], g);
+    Wt[t] = g;
+  }
+  __syncthreads();
+  for (int t = tid; t < RR; t += nt) {  // Vs = T Wt
+    const int r = t / R, c = t % R;
+    double g = diag[r] * Wt[t];
+    if (r < r0) g = fma(F[r], Wt[r0 * R + c], g);
+    if (r == r0)
+      for (int i = 0; i < r0; ++i) g = fma(F[i], Wt[i * R + c], g);
+    if (r >= r0 && r + 1 < R) g = fma(beta[r], Wt[(r + 1) * R + c], g);
+    if (r - 1 >= r0) g = fma(beta[r - 1], Wt[(r - 1) * R + c], g);
+    Vs[t] = g;
+  }
+  __syncthreads();
+  for (int t = tid; t < RR; t += nt) {  // As = Wt^T (T Wt)
+    const int r = t / R, c = t % R;
+    double g = 0.0;
+    for (int k = 0; k < R; ++k) g = fma(Wt[k * R + r], Vs[k * R + c], g);
+    As[t] = g;
+  }
+  __syncthreads();
+  for (int t = tid; t < RR; t += nt) {  // exact symmetry
+    const int r = t / R, c = t % R;
+    if (r < c) {
+      const double m = 0.5 * (As[t] + As[c * R + r]);
+      As[t] = m;
+      As[c * R + r] = m;
+    }
+  }
+  __syncthreads();
+  const int sw64 = cta_jacobi_sweeps<double>(As, Vs, R, true, 1e-28, 20, js, cr);
+  for (int k = tid; k < R; k += nt) th[k] = As[k * R + k];
+  __syncthreads();
   if (tid == 0) {  // ascending order (insertion sort on indices)
     for (int i = 0; i < R; ++i) js.perm[i] = i;
     for (int i = 1; i < R; ++i) {
       const int key = js.perm[i];
-      const double kv = A[key * R + key];
+      const double kv = th[key];
       int j = i - 1;
-      while (j >= 0 && A[js.perm[j] * R + js.perm[j]] > kv) {
+      while (j >= 0 && th[js.perm[j]] > kv) {
         js.perm[j + 1] = js.perm[j];
         --j;
       }
@@ -223,12 +344,19 @@ __device__ void cta_jacobi(double* A, double* V, double* th, int R, JacobiScratc
     }
   }
   __syncthreads();
-  for (int k = tid; k < R; k += nt) th[k] = A[js.perm[k] * R + js.perm[k]];
+  for (int t = tid; t < RR; t += nt) {  // As = Wt Q, columns in ascending order
+    const int r = t / R, c = js.perm[t % R];
+    double g = 0.0;
+    for (int k = 0; k < R; ++k) g = fma(Wt[r * R + k], Vs[k * R + c], g);
+    As[t] = g;
+  }
   __syncthreads();
-  for (int t = tid; t < R * R; t += nt) A[t] = V[(t / R) * R + js.perm[t % R]];
+  for (int k = tid; k < R; k += nt) Wt[k] = th[js.perm[k]];
   __syncthreads();
-  for (int t = tid; t < R * R; t += nt) V[t] = A[t];
+  for (int k = tid; k < R; k += nt) th[k] = Wt[k];
+  for (int t = tid; t < RR; t += nt) Vs[t] = As[t];
   __syncthreads();
+  return make_int2(sw32, sw64);
 }
 
 // ---------------------------------------------------------------------------
@@ -236,50 +364,95 @@ __device__ void cta_jacobi(double* A, double* V, double* th, int R, JacobiScratc
 // (column-major, leading dimension n); coefficients accumulated in FP64
 // ---------------------------------------------------------------------------
 constexpr int kBChunk = 8;
+constexpr int kBCoef = kBMaxR + kBMaxLock + kBChunk;  // coefficient slots per vector
 
-__device__ void cta_cgs(float* q, const float* X, int kx, const float* Z, int kz, int n, double* coef,
-                        CtaRed& cr) {
-  __shared__ double w8[kBThreads / 32][kBChunk];
+__device__ inline float warp_sum_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// One classical Gram-Schmidt pass of NV (1 or 2) vectors against X(:, 0:kx) and
+// Z(:, 0:kz) (column-major, leading dimension n), FP32 throughout.  Both vectors
+// share every column load; each row issues kBChunk (dots) or 16 (update)
+// independent loads before its FMA chain, so L2 latency overlaps.
+template <int NV>
+__device__ void cta_cgs_n(float* q0, float* q1, const float* X, int kx, const float* Z, int kz, int n,
+                          float* coef) {
+  __shared__ float w8[kBThreads / 32][2 * kBChunk];
   const int K = kx + kz;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int k0 = 0; k0 < K; k0 += kBChunk) {
-    float acc[kBChunk];
+    const float* cp[kBChunk];
 #pragma unroll
-    for (int c = 0; c < kBChunk; ++c) acc[c] = 0.f;
+    for (int c = 0; c < kBChunk; ++c) {
+      const int k = min(k0 + c, K - 1);
+      cp[c] = (k < kx) ? X + (int64_t)k * n : Z + (int64_t)(k - kx) * n;
+    }
+    float acc[NV][kBChunk];
+#pragma unroll
+    for (int t = 0; t < NV; ++t)
+#pragma unroll
+      for (int c = 0; c < kBChunk; ++c) acc[t][c] = 0.f;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      const float qi = q[i];
+      float v[kBChunk];
 #pragma unroll
-      for (int c = 0; c < kBChunk; ++c) {
-        const int k = k0 + c;
-        if (k < K) {
-          const float v = (k < kx) ? X[(int64_t)k * n + i] : Z[(int64_t)(k - kx) * n + i];
-          acc[c] = fmaf(v, qi, acc[c]);
-        }
+      for (int c = 0; c < kBChunk; ++c) v[c] = cp[c][i];
+      const float qa = q0[i];
+#pragma unroll
+      for (int c = 0; c < kBChunk; ++c) acc[0][c] = fmaf(v[c], qa, acc[0][c]);
+      if constexpr (NV > 1) {
+        const float qb = q1[i];
+#pragma unroll
+        for (int c = 0; c < kBChunk; ++c) acc[NV - 1][c] = fmaf(v[c], qb, acc[NV - 1][c]);
       }
     }
 #pragma unroll
-    for (int c = 0; c < kBChunk; ++c) {
-      const double v = warp_sum((double)acc[c]);
-      if (lane == 0) w8[warp][c] = v;
-    }
+    for (int t = 0; t < NV; ++t)
+#pragma unroll
+      for (int c = 0; c < kBChunk; ++c) {
+        const float r = warp_sum_f(acc[t][c]);
+        if (lane == 0) w8[warp][t * kBChunk + c] = r;
+      }
     __syncthreads();
-    if (threadIdx.x < kBChunk && k0 + (int)threadIdx.x < K) {
-      double sm = 0.0;
-      for (int w = 0; w < nw; ++w) sm += w8[w][threadIdx.x];
-      coef[k0 + threadIdx.x] = sm;
+    if (threadIdx.x < NV * kBChunk) {
+      const int t = threadIdx.x / kBChunk, c = threadIdx.x % kBChunk;
+      if (k0 + c < K) {
+        float sm = 0.f;
+        for (int w = 0; w < nw; ++w) sm += w8[w][threadIdx.x];
+        coef[t * kBCoef + k0 + c] = sm;
+      }
     }
     __syncthreads();
   }
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    float v = q[i];
-    for (int k = 0; k < K; ++k) {
-      const float b = (k < kx) ? X[(int64_t)k * n + i] : Z[(int64_t)(k - kx) * n + i];
-      v = fmaf(-(float)coef[k], b, v);
+    float va = q0[i], vb = 0.f;
+    if constexpr (NV > 1) vb = q1[i];
+    for (int k0 = 0; k0 < K; k0 += 16) {
+      float b[16];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        const int k = k0 + c;
+        b[c] = (k < K) ? ((k < kx) ? X[(int64_t)k * n + i] : Z[(int64_t)(k - kx) * n + i]) : 0.f;
+      }
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        const int k = k0 + c;
+        if (k < K) {
+          va = fmaf(-coef[k], b[c], va);
+          if constexpr (NV > 1) vb = fmaf(-coef[kBCoef + k], b[c], vb);
+        }
+      }
     }
-    q[i] = v;
+    q0[i] = va;
+    if constexpr (NV > 1) q1[i] = vb;
   }
   __syncthreads();
-  (void)cr;
+}
+
+__device__ inline void cta_cgs(float* q, const float* X, int kx, const float* Z, int kz, int n, float* coef,
+                               CtaRed&) {
+  cta_cgs_n<1>(q, nullptr, X, kx, Z, kz, n, coef);
 }
 
 // ||q||_2 (FP64 accumulation of FP32 squares)
@@ -301,10 +474,11 @@ struct BState {
   double alpha[kBMaxR + 1], beta[kBMaxR + 1];  // Xi_j, Gamma_j (d = 1)
   double theta_keep[kBMaxR], F[kBMaxR];        // retained Ritz values and the arrow row
   double th[kBMaxR], res[kBMaxR];              // eigenvalues of T, Ritz residuals
+  double tdiag[kBMaxR];                        // diagonal of T
   double wz[3][kBMaxR + 1];                    // rotating columns of W (active blocks)
   double wx[3][kBMaxLock];                     // ... rows of the locked vectors
   double xth[kBMaxLock], xrho[kBMaxLock];
-  double coef[kBMaxR + kBMaxLock + kBChunk];
+  float coef[2 * kBCoef];
   int lock_list[kBMaxR], keep_list[kBMaxR];
   int ncand, nkeep, nsmall, flags;
 };
@@ -321,7 +495,7 @@ __device__ void replace_vec(float* dst, uint64_t seed, uint32_t stream, int n, c
 
 template <int LANES>
 __device__ void solve_instance(const BatchArgs& a, int inst, float* ws32, double* ws64, double* As, double* Vs,
-                               BState& S, JacobiScratch& js, CtaRed& cr) {
+                               double* Wt, BState& S, JacobiScratch& js, CtaRed& cr) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const long long clk0 = clock64();
   const int n = a.nrows[inst];
@@ -360,6 +534,18 @@ __device__ void solve_instance(const BatchArgs& a, int inst, float* ws32, double
     cta_scale_to(Z, Z, (float)(1.0 / nq), n);
   }
   int k0 = 0, nlock = 0, status = 0;
+  // SM cycles by phase (thread 0; every boundary follows a barrier):
+  // 0 Lanczos steps, 1 partial reorthogonalization, 2 projected eigenproblem,
+  // 3 locking, 4 thick restart, 5 refinement
+  long long cyc[6] = {0, 0, 0, 0, 0, 0};
+  long long tmark = clock64();
+  long long sweeps32 = 0, sweeps64 = 0;
+#define PHASE(k)                      \
+  do {                                \
+    const long long tnow = clock64(); \
+    cyc[k] += tnow - tmark;           \
+    tmark = tnow;                     \
+  } while (0)
   uint32_t bdcount = 0;
   long long matvecs = 0, restarts = 0, reorths = 0, ev_first = -1, ev_last = -1;
   int ev_first_k = 0, ev_total = 0, ev_count = 0;
@@ -458,11 +644,11 @@ __device__ void solve_instance(const BatchArgs& a, int inst, float* ws32, double
       __syncthreads();
       const int fl = S.flags;
       if (fl) {  // one CGS pass of Q_j and Q_{j+1} against [X, Z_{j-1}] (semi-orthogonal blocks)
+        PHASE(0);
         const int kx = (fl & 2) ? nlock : 0, kz = (fl & 1) ? j : 0;
-        cta_cgs(qj, X, kx, Z, kz, n, S.coef, cr);
+        cta_cgs_n<2>(qj, qn, X, kx, Z, kz, n, S.coef);
         double nr = cta_norm(qj, n, cr);
         cta_scale_to(qj, qj, (float)(1.0 / nr), n);
-        cta_cgs(qn, X, kx, Z, kz, n, S.coef, cr);
         nr = cta_norm(qn, n, cr);
         cta_scale_to(qn, qn, (float)(1.0 / nr), n);
         if (fl & 1)
@@ -474,9 +660,11 @@ __device__ void solve_instance(const BatchArgs& a, int inst, float* ws32, double
           for (int k = tid; k < nlock; k += nt) xj[k] = xn[k] = u_d;
         ++reorths;
         __syncthreads();
+        PHASE(1);
       }
     }
     // ---- restart (Alg. 2 lines 13-17) with locking ----
+    PHASE(0);
     for (int t = tid; t < R * R; t += nt) {
       const int r = t / R, c = t % R;
       double v = 0.0;
@@ -487,7 +675,12 @@ __device__ void solve_instance(const BatchArgs& a, int inst, float* ws32, double
       As[t] = v;
     }
     __syncthreads();
-    cta_jacobi(As, Vs, S.th, R, js, cr);
+    for (int r = tid; r < R; r += nt) S.tdiag[r] = (r < r0) ? S.theta_keep[r] : S.alpha[r];
+    __syncthreads();
+    const int2 sw = cta_eig(As, Vs, Wt, S.th, R, r0, S.tdiag, S.F, S.beta, js, cr);
+    sweeps32 += sw.x;
+    sweeps64 += sw.y;
+    PHASE(2);
     for (int c = tid; c < R; c += nt) S.res[c] = S.beta[R - 1] * fabs(Vs[(R - 1) * R + c]);
     __syncthreads();
     theta_max = fmax(theta_max, S.th[R - 1]);
@@ -503,6 +696,9 @@ __device__ void solve_instance(const BatchArgs& a, int inst, float* ws32, double
     }
     __syncthreads();
     const int ncand = S.ncand;
+    float* V32 = reinterpret_cast<float*>(As);  // FP32 copy of the eigenvectors (As is free now)
+    for (int t = tid; t < R * R; t += nt) V32[t] = (float)Vs[t];
+    __syncthreads();
     int locked_now = 0;
     for (int ci = 0; ci < ncand; ++ci) {
       if (nlock >= kBMaxLock) {
@@ -512,7 +708,7 @@ __device__ void solve_instance(const BatchArgs& a, int inst, float* ws32, double
       const int c = S.lock_list[ci];
       for (int i = tid; i < n; i += nt) {
         float sm = 0.f;
-        for (int jj = 0; jj < R; ++jj) sm = fmaf(Z[(int64_t)jj * n + i], (float)Vs[jj * R + c], sm);
+        for (int jj = 0; jj < R; ++jj) sm = fmaf(Z[(int64_t)jj * n + i], V32[jj * R + c], sm);
         Zt[i] = sm;
       }
       __syncthreads();
@@ -539,6 +735,7 @@ __device__ void solve_instance(const BatchArgs& a, int inst, float* ws32, double
       ++ev_count;
     }
     const int n_unl = S.nsmall - ncand;
+    PHASE(3);
     if (tid == 0) {  // retained set: capped at dimK/2, most converged small pairs first
       int nk = (n_unl + R) / 2;
       nk = max(nk, 1);
@@ -571,12 +768,23 @@ __device__ void solve_instance(const BatchArgs& a, int inst, float* ws32, double
     }
     __syncthreads();
     const int nk = S.nkeep;
-    for (int i = tid; i < n; i += nt) {  // Z_new = Z V(:, keep)
-      for (int c = 0; c < nk; ++c) {
-        const int kc = S.keep_list[c];
-        float sm = 0.f;
-        for (int jj = 0; jj < R; ++jj) sm = fmaf(Z[(int64_t)jj * n + i], (float)Vs[jj * R + kc], sm);
-        Zt[(int64_t)c * n + i] = sm;
+    for (int i = tid; i < n; i += nt) {  // Z_new = Z V(:, keep), eight kept columns per pass over row i
+      for (int c0 = 0; c0 < nk; c0 += 8) {
+        float acc[8];
+        int kc[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          acc[c] = 0.f;
+          kc[c] = S.keep_list[min(c0 + c, nk - 1)];
+        }
+        for (int jj = 0; jj < R; ++jj) {
+          const float z = Z[(int64_t)jj * n + i];
+#pragma unroll
+          for (int c = 0; c < 8; ++c) acc[c] = fmaf(z, V32[jj * R + kc[c]], acc[c]);
+        }
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+          if (c0 + c < nk) Zt[(int64_t)(c0 + c) * n + i] = acc[c];
       }
       for (int c = 0; c < nk; ++c) Z[(int64_t)c * n + i] = Zt[(int64_t)c * n + i];
     }
@@ -601,6 +809,7 @@ __device__ void solve_instance(const BatchArgs& a, int inst, float* ws32, double
       __syncthreads();
     }
     k0 = nk;
+    PHASE(4);
     ++restarts;
     // stopping rule (Sec. 4.3)
     double sv = (double)R;
@@ -615,6 +824,7 @@ __device__ void solve_instance(const BatchArgs& a, int inst, float* ws32, double
     }
   }
   // ---- FP64 projection of every locked vector onto null(A), then MGS twice ----
+  PHASE(4);
   double* out = a.basis + a.out_off[inst];
   double* r = ws64;
   double* p = r + n;
@@ -682,12 +892,17 @@ __device__ void solve_instance(const BatchArgs& a, int inst, float* ws32, double
     st[2] = reorths;
     st[3] = iters_max;
     st[4] = clock64() - clk0;
+    PHASE(5);
+    for (int k = 0; k < 6; ++k) st[5 + k] = cyc[k];
+    st[11] = sweeps32;
+    st[12] = sweeps64;
   }
   __syncthreads();
+#undef PHASE
 }
 
-template <int LANES>
-__global__ void __launch_bounds__(kBThreads) k_batched(BatchArgs a) {
+template <int LANES, int BT>
+__global__ void __launch_bounds__(BT, BT <= 128 ? 4 : 2) k_batched(BatchArgs a) {
   extern __shared__ __align__(16) double dyn[];
   __shared__ BState S;
   __shared__ JacobiScratch js;
@@ -695,6 +910,7 @@ __global__ void __launch_bounds__(kBThreads) k_batched(BatchArgs a) {
   __shared__ int next;
   double* As = dyn;
   double* Vs = dyn + a.R * a.R;
+  double* Wt = Vs + a.R * a.R;
   float* ws32 = a.ws32 + (int64_t)blockIdx.x * a.ws32_stride;
   double* ws64 = a.ws64 + (int64_t)blockIdx.x * a.ws64_stride;
   while (true) {  // work queue: no CTA waits for another
@@ -703,25 +919,42 @@ __global__ void __launch_bounds__(kBThreads) k_batched(BatchArgs a) {
     const int k = next;
     __syncthreads();
     if (k >= a.count) break;
-    solve_instance<LANES>(a, a.order[k], ws32, ws64, As, Vs, S, js, cr);
+    solve_instance<LANES>(a, a.order[k], ws32, ws64, As, Vs, Wt, S, js, cr);
   }
 }
 
-cudaError_t batched_prepare(int lanes, int R, int* blocks_per_sm) {
-  const int smem = (int)(sizeof(double) * 2 * (size_t)R * R);
-  const void* f = lanes == 1 ? (const void*)k_batched<1> : lanes == 2 ? (const void*)k_batched<2>
-                                                                        : (const void*)k_batched<4>;
-  cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * kBMaxR * kBMaxR * 8);
-  if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, kBThreads, smem);
+template <int L, int BT>
+static const void* kfun() {
+  return reinterpret_cast<const void*>(k_batched<L, BT>);
 }
 
-void batched_launch(const BatchArgs& a, int lanes, int grid, cudaStream_t s) {
-  const size_t smem = sizeof(double) * 2 * (size_t)a.R * a.R;
-  switch (lanes) {
-    case 1: k_batched<1><<<grid, kBThreads, smem, s>>>(a); break;
-    case 2: k_batched<2><<<grid, kBThreads, smem, s>>>(a); break;
-    default: k_batched<4><<<grid, kBThreads, smem, s>>>(a); break;
+static const void* batched_fn(int lanes, int block) {
+  if (block == 128) return lanes == 1 ? kfun<1, 128>() : lanes == 2 ? kfun<2, 128>() : kfun<4, 128>();
+  return lanes == 1 ? kfun<1, 256>() : lanes == 2 ? kfun<2, 256>() : kfun<4, 256>();
+}
+
+cudaError_t batched_prepare(int lanes, int block, int R, int* blocks_per_sm) {
+  const int smem = (int)(sizeof(double) * 3 * (size_t)R * R);
+  const void* f = batched_fn(lanes, block);
+  cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 3 * kBMaxR * kBMaxR * 8);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, block, smem);
+}
+
+void batched_launch(const BatchArgs& a, int lanes, int block, int grid, cudaStream_t s) {
+  const size_t smem = sizeof(double) * 3 * (size_t)a.R * a.R;
+  if (block == 128) {
+    switch (lanes) {
+      case 1: k_batched<1, 128><<<grid, 128, smem, s>>>(a); break;
+      case 2: k_batched<2, 128><<<grid, 128, smem, s>>>(a); break;
+      default: k_batched<4, 128><<<grid, 128, smem, s>>>(a); break;
+    }
+  } else {
+    switch (lanes) {
+      case 1: k_batched<1, 256><<<grid, 256, smem, s>>>(a); break;
+      case 2: k_batched<2, 256><<<grid, 256, smem, s>>>(a); break;
+      default: k_batched<4, 256><<<grid, 256, smem, s>>>(a); break;
+    }
   }
 }
 

@@ -1205,6 +1205,7 @@ void ns_default_opts(ns_opts* o) {
   o->refine_maxit = 500;
   o->refine_chunk = 8;
   o->use_graphs = 0;
+  o->batch_block = 0;
   o->profile = 0;
 }
 

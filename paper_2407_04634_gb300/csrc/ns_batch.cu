@@ -40,12 +40,12 @@ struct ns_batch {
   double* ws64 = nullptr;
   size_t ws32_bytes = 0, ws64_bytes = 0;
   // schedule
-  int lanes = 0, bps = 0, grid = 0;
+  int lanes = 0, bps = 0, grid = 0, tuned_block = 0;
   double t_tune_ms = 0.0;
   // graph of the last solve
   cudaGraphExec_t gexec = nullptr;
   ns::BatchArgs gargs{};
-  int glanes = 0, ggrid = 0;
+  int glanes = 0, ggrid = 0, gblock = 0;
   // results
   bool solved = false;
   std::vector<int> nullity_h, status_h;
@@ -218,6 +218,9 @@ ns_status ns_batch_solve(ns_batch* h, int d, int restart_len, double tol, const 
   if (opts) o = *opts;
   if (!(o.eps >= 0.0) || !(o.stop_factor > 0.0) || !(o.refine_tol > 0.0) || o.refine_maxit < 0)
     return bset_err(h, NS_ERR_INVALID_ARG, "bad opts");
+  if (!(o.batch_block == 0 || o.batch_block == 128 || o.batch_block == 256))
+    return bset_err(h, NS_ERR_INVALID_ARG, "batch_block must be 0, 128 or 256");
+  const int block = o.batch_block ? o.batch_block : 128;
   const int R = restart_len;
   try {
     int dev = 0, sms = 0;
@@ -225,7 +228,7 @@ ns_status ns_batch_solve(ns_batch* h, int d, int restart_len, double tol, const 
     bck(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
     int bps[5] = {0, 0, 0, 0, 0};
     for (int L : {1, 2, 4}) {
-      bck(ns::batched_prepare(L, R, &bps[L]), "batched_prepare");
+      bck(ns::batched_prepare(L, block, R, &bps[L]), "batched_prepare");
       if (bps[L] < 1) throw BFail{NS_ERR_CUDA, "batched kernel does not fit on an SM"};
     }
     const int bps_max = std::max(bps[1], std::max(bps[2], bps[4]));
@@ -278,7 +281,7 @@ ns_status ns_batch_solve(ns_batch* h, int d, int restart_len, double tol, const 
     int64_t launches = 0;
     // ---- autotuner: SpMV lanes per row, judged by the SM cycles the sampled
     // instances take while running side by side (first solve only) ----
-    if (h->lanes == 0) {
+    if (h->lanes == 0 || h->tuned_block != block) {
       ns::BatchArgs t = a;
       t.order = h->order_sample;
       t.count = h->sample_count;
@@ -291,7 +294,7 @@ ns_status ns_batch_solve(ns_batch* h, int d, int restart_len, double tol, const 
       for (int L : {1, 2, 4}) {
         const int g = (int)std::min<int64_t>(t.count, (int64_t)bps[L] * sms);
         bck(cudaMemsetAsync(h->queue, 0, sizeof(unsigned), h->stream), "queue reset");
-        ns::batched_launch(t, L, g, h->stream);
+        ns::batched_launch(t, L, block, g, h->stream);
         bck(cudaGetLastError(), "k_batched (tuning)");
         launches += 1;
         bck(cudaMemcpyAsync(st.data(), h->istats, sizeof(long long) * st.size(), cudaMemcpyDeviceToHost, h->stream),
@@ -310,6 +313,7 @@ ns_status ns_batch_solve(ns_batch* h, int d, int restart_len, double tol, const 
       bck(cudaEventElapsedTime(&ms, h->ev0, h->ev1), "event");
       h->t_tune_ms = ms;
       h->lanes = best_l;
+      h->tuned_block = block;
     }
     h->bps = bps[h->lanes];
     h->grid = (int)std::min<int64_t>(h->count, (int64_t)h->bps * sms);
@@ -318,12 +322,13 @@ ns_status ns_batch_solve(ns_batch* h, int d, int restart_len, double tol, const 
     const bool want_graph = o.use_graphs >= 0;
     bool replayed = false;
     if (want_graph) {
-      if (!h->gexec || !same_args(h->gargs, a) || h->glanes != h->lanes || h->ggrid != h->grid) {
+      if (!h->gexec || !same_args(h->gargs, a) || h->glanes != h->lanes || h->ggrid != h->grid ||
+          h->gblock != block) {
         drop_graph(h);
         cudaGraph_t g = nullptr;
         bck(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
         cudaMemsetAsync(h->queue, 0, sizeof(unsigned), h->stream);
-        ns::batched_launch(a, h->lanes, h->grid, h->stream);
+        ns::batched_launch(a, h->lanes, block, h->grid, h->stream);
         const cudaError_t le = cudaGetLastError();
         const cudaError_t ce = cudaStreamEndCapture(h->stream, &g);
         bck(le, "k_batched (capture)");
@@ -334,6 +339,7 @@ ns_status ns_batch_solve(ns_batch* h, int d, int restart_len, double tol, const 
         h->gargs = a;
         h->glanes = h->lanes;
         h->ggrid = h->grid;
+        h->gblock = block;
       }
       bck(cudaEventRecord(h->ev0, h->stream), "event");
       bck(cudaGraphLaunch(h->gexec, h->stream), "graph launch");
@@ -341,7 +347,7 @@ ns_status ns_batch_solve(ns_batch* h, int d, int restart_len, double tol, const 
     } else {
       bck(cudaEventRecord(h->ev0, h->stream), "event");
       bck(cudaMemsetAsync(h->queue, 0, sizeof(unsigned), h->stream), "queue reset");
-      ns::batched_launch(a, h->lanes, h->grid, h->stream);
+      ns::batched_launch(a, h->lanes, block, h->grid, h->stream);
       bck(cudaGetLastError(), "k_batched");
     }
     launches += 1;
@@ -378,6 +384,7 @@ ns_status ns_batch_solve(ns_batch* h, int d, int restart_len, double tol, const 
     S.lanes = h->lanes;
     S.grid = h->grid;
     S.blocks_per_sm = h->bps;
+    S.block = block;
     S.graph = replayed ? 1 : 0;
     S.t_solve_ms = ms;
     S.t_tune_ms = h->t_tune_ms;

@@ -9,8 +9,8 @@ namespace ns {
 
 constexpr int kBMaxR = 64;     // restart length limit of the batched kernel
 constexpr int kBMaxLock = 32;  // nullity limit per instance
-constexpr int kBThreads = 256;
-constexpr int kBStats = 5;     // per-instance counters in BatchArgs::istats
+constexpr int kBThreads = 256;    // largest CTA size (128 and 256 are built)
+constexpr int kBStats = 13;    // per-instance counters in BatchArgs::istats
 
 struct BatchArgs {
   // concatenated CSR: instance i has n[i] rows, local row pointers at rowptr + rp_off[i],
@@ -41,14 +41,17 @@ struct BatchArgs {
   double* basis;
   int* nullity;
   int* status;
-  long long* istats;  // per instance: matvecs, restarts, reorths, refine iterations, SM clock cycles
+  long long* istats;  // per instance: matvecs, restarts, reorths, refine iterations, SM clock cycles,
+                      // then the cycles of six phases (steps, reorth, eig, locking, restart, refine),
+                      // then the FP32 and FP64 Jacobi sweeps of the projected problems
   unsigned* queue;
 };
 
-// Kernel attributes for the chosen LANES variant and the CTAs one SM holds.
-cudaError_t batched_prepare(int lanes, int R, int* blocks_per_sm);
-// One persistent launch of grid CTAs over the queue a.queue (which must read 0).
-void batched_launch(const BatchArgs& a, int lanes, int grid, cudaStream_t s);
+// Kernel attributes for the (LANES, block) variant and the CTAs one SM holds.
+cudaError_t batched_prepare(int lanes, int block, int R, int* blocks_per_sm);
+// One persistent launch of grid CTAs of `block` threads (128 or 256) over the
+// queue a.queue (which must read 0).
+void batched_launch(const BatchArgs& a, int lanes, int block, int grid, cudaStream_t s);
 // Workspace per CTA slot, in elements.
 size_t batched_ws32_per_slot(int nmax, int R);
 size_t batched_ws64_per_slot(int nmax);

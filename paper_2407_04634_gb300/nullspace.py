@@ -35,7 +35,7 @@ class NsOpts(C.Structure):
     _fields_ = [("eps", C.c_double), ("precision", C.c_int), ("reorth", C.c_int), ("max_matvec", C.c_int64),
                 ("stop_factor", C.c_double), ("lock_tol_mixed", C.c_double), ("refine", C.c_int),
                 ("refine_tol", C.c_double), ("refine_maxit", C.c_int), ("refine_chunk", C.c_int),
-                ("use_graphs", C.c_int), ("profile", C.c_int)]
+                ("use_graphs", C.c_int), ("profile", C.c_int), ("batch_block", C.c_int)]
 
 
 class NsStats(C.Structure):
@@ -52,7 +52,8 @@ class NsStats(C.Structure):
 class NsBatchStats(C.Structure):
     _fields_ = [("count", C.c_int64), ("total_nullity", C.c_int64), ("failed", C.c_int64),
                 ("matvecs_total", C.c_int64), ("matvecs_max", C.c_int64), ("kernel_launches", C.c_int64),
-                ("lanes", C.c_int), ("grid", C.c_int), ("blocks_per_sm", C.c_int), ("graph", C.c_int),
+                ("lanes", C.c_int), ("grid", C.c_int), ("blocks_per_sm", C.c_int), ("block", C.c_int),
+                ("graph", C.c_int),
                 ("t_solve_ms", C.c_double), ("t_tune_ms", C.c_double)]
 
     def as_dict(self):
@@ -299,6 +300,8 @@ def project(V: np.ndarray, W: np.ndarray, precision: str = "fp64"):
     return Wc, Cc
 
 
+BATCH_ISTATS = ("matvecs", "restarts", "reorths", "refine_iters", "cycles", "cyc_steps", "cyc_reorth", "cyc_eig",
+                "cyc_lock", "cyc_restart", "cyc_refine", "sweeps32", "sweeps64")
 BATCH_STATUS = {0: "ok", 4: "max_matvec reached", 7: "refinement missed its tolerance", 8: "more than 32 null vectors"}
 
 
@@ -319,10 +322,22 @@ class Batch:
             cis.append(np.asarray(ci, dtype=np.int32))
             vas.append(np.asarray(va, dtype=np.float64))
             ns_.append(len(rp) - 1)
-        self.count = len(ns_)
-        self.n = np.asarray(ns_, dtype=np.int64)
-        self._keep = (np.ascontiguousarray(self.n), np.ascontiguousarray(np.concatenate(rps)),
-                      np.ascontiguousarray(np.concatenate(cis)), np.ascontiguousarray(np.concatenate(vas)))
+        self._create(np.asarray(ns_, dtype=np.int64), np.concatenate(rps), np.concatenate(cis),
+                     np.concatenate(vas), seed, env)
+
+    @classmethod
+    def from_arrays(cls, n, rowptr, colind, vals, seed: int, env: str | None = "torch") -> "Batch":
+        """Already concatenated host arrays (the layout ns_batch_create takes)."""
+        b = cls.__new__(cls)
+        b.lib = load()
+        b._create(np.asarray(n, dtype=np.int64), rowptr, colind, vals, seed, env)
+        return b
+
+    def _create(self, n, rowptr, colind, vals, seed, env):
+        self.count = len(n)
+        self.n = n
+        self._keep = (np.ascontiguousarray(n, dtype=np.int64), np.ascontiguousarray(rowptr, dtype=np.int64),
+                      np.ascontiguousarray(colind, dtype=np.int32), np.ascontiguousarray(vals, dtype=np.float64))
         self._env = torch_env() if env == "torch" else None
         h = C.c_void_p()
         st = self.lib.ns_batch_create(C.byref(h), self.count, *[_ptr(a) for a in self._keep], C.c_uint64(seed),
@@ -343,10 +358,11 @@ class Batch:
         return st
 
     def results(self):
-        """(nullity[count], status[count], istats[count, 5]) of the last solve."""
+        """(nullity[count], status[count], istats[count, 11]) of the last solve; istats columns
+        are BATCH_ISTATS."""
         N = np.zeros(self.count, dtype=np.int32)
         S = np.zeros(self.count, dtype=np.int32)
-        I = np.zeros((self.count, 5), dtype=np.int64)
+        I = np.zeros((self.count, len(BATCH_ISTATS)), dtype=np.int64)
         self._check(self.lib.ns_batch_results(self.h, _ptr(N), _ptr(S), _ptr(I)), "ns_batch_results")
         return N, S, I
 

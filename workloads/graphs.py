@@ -339,7 +339,7 @@ CONFIGS = {
     2: dict(d=1, restart=120, tol=1e-10, precision="fp64"),
     3: dict(d=4, restart=160, tol=1e-10, precision="mixed"),
     4: dict(d=2, restart=150, tol=1e-10, precision="mixed"),
-    5: dict(d=1, restart=40, tol=1e-10, precision="mixed"),
+    5: dict(d=1, restart=40, tol=1e-5, precision="mixed"),
 }
 
 
