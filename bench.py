@@ -181,6 +181,23 @@ print(json.dumps(dict(N=int(r.N), expect=int(w.nullity), n=int(A.shape[1]), seco
 """
 
 
+def rank_slice(count: int, world: int, rank: int) -> tuple[int, int]:
+    """Contiguous, balanced slice [lo, hi) of `count` independent instances for `rank`."""
+    return rank * count // world, (rank + 1) * count // world
+
+
+def reduce_over_ranks(ms: float, units: float, dist, device) -> tuple[float, float]:
+    """(max over ranks of the timed milliseconds, sum over ranks of the converged units)."""
+    if dist is None:
+        return ms, units
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(u[0])
+
+
 def run_oracle_sample(p, scale):
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
@@ -300,7 +317,7 @@ def bench_batched(args, world, rank, local):
 
     p = workload_params(args)
     ws_all, _ = make_config(5, args.scale)
-    lo, hi = rank * len(ws_all) // world, (rank + 1) * len(ws_all) // world
+    lo, hi = rank_slice(len(ws_all), world, rank)
     ws = ws_all[lo:hi]  # contiguous slice: global instance i keeps the key solver_seed + i
     seed = p["solver_seed"] + lo
     n = np.array([w.A.n for w in ws], dtype=np.int64)
@@ -349,13 +366,7 @@ def bench_batched(args, world, rank, local):
         if X.shape[1]:
             worst = max(worst, float(np.linalg.norm(A @ X) / norm2_A(A, "spd")))
     all_valid = all_valid and worst <= 1e-8
-    t_max = ms
-    if dist:
-        tt = torch.tensor([ms, units], device="cuda", dtype=torch.float64)
-        tmax = tt.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(tt, op=dist.ReduceOp.SUM)
-        t_max, units = float(tmax[0]), float(tt[1])
+    t_max, units = reduce_over_ranks(ms, units, dist, "cuda")
     value = units / (t_max / 1e3) if all_valid else 0.0
 
     # roofline of the persistent kernel: algorithmic bytes of the B applications
@@ -531,13 +542,7 @@ def main():
     prof = h.profile()  # kernel classes of the last timed step
     units = sum(r.nullity for r in results if valid(r))
     all_valid = all(valid(r) for r in results)
-    t_max = ms
-    if dist:
-        tt = torch.tensor([ms, float(units)], device="cuda", dtype=torch.float64)
-        tmax = tt.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(tt, op=dist.ReduceOp.SUM)
-        t_max, units = float(tmax[0]), float(tt[1])
+    t_max, units = reduce_over_ranks(ms, float(units), dist, "cuda")
     value = units / (t_max / 1e3)
     launches = sum(r.stats.get("kernel_launches", 0) for r in results)
 
