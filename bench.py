@@ -410,7 +410,9 @@ def bench_batched(args, world, rank, local):
            "steps": args.e2e_steps}
 
     # the same instances through the single-instance FP64 path, one ns_solve each (a sample)
-    loop_t, loop_N, loop_ok, picked = 0.0, 0, True, list(range(0, len(ws), max(1, len(ws) // 32)))
+    every = max(1, len(ws) // max(1, args.loop_sample))
+    loop_t, loop_N, loop_ok = 0.0, 0, True
+    picked = list(range(0, len(ws), every)) if args.loop_sample > 0 else []
     with torch.cuda.stream(stream):
         for k in picked:
             A = ws[k].A
@@ -426,7 +428,7 @@ def bench_batched(args, world, rank, local):
             loop_N += r.nullity
             hk.close()
     loop = {"value": loop_N / loop_t if loop_t > 0 else None, "unit": UNIT, "valid": bool(loop_ok),
-            "sample": f"{len(picked)} of the {len(ws)} instances (every {max(1, len(ws) // 32)}th), "
+            "sample": f"{len(picked)} of the {len(ws)} instances (every {every}th), "
                       f"one FP64 ns_solve each (d=1, restart {p['restart']}, tol {p['tol']:g}), "
                       f"CUDA-event time of the solve, warm handle"}
 
@@ -484,6 +486,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--scale", type=float, default=1.0, help="workload scale (< 1 is for profiling only)")
     ap.add_argument("--kernel-probe", action="store_true", help="launch a few hot kernels, no bench line")
+    ap.add_argument("--loop-sample", type=int, default=32,
+                    help="batched workload: instances solved one by one with the FP64 path for comparison")
     ap.add_argument("--batch-block", type=int, default=0, choices=[0, 128, 256],
                     help="threads per CTA of the batched kernel (0 = library default)")
     args = ap.parse_args()
