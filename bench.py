@@ -288,6 +288,8 @@ def kernel_probe(ns, h, w, p):
         for _ in range(3):
             h.apply_B(X, 1e-3, prec)
         out[f"apply_B_{prec}_s"] = (time.perf_counter() - t) / 3
+        for sched in (64, 1, 2, 4, 8):  # every SpMM schedule once (TMA-staged, lanes per row)
+            h.apply_B(X, 1e-3, prec, sched)
     V, _ = np.linalg.qr(rng.standard_normal((n, 256)))
     W = rng.standard_normal((n, 2))
     for prec in ("fp64", "mixed"):

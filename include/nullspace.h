@@ -196,12 +196,18 @@ ns_status ns_start_block(const ns_handle* h, int d, double* Omega);
  *   X, Y       : n*d doubles, host or device memory (on_device)
  *   eps        : perturbation strength
  *   precision  : NS_FP64 or NS_MIXED (X rounded to FP32, FP32 arithmetic with
- *                FP32 values of A; Y returned widened to FP64) */
+ *                FP32 values of A; Y returned widened to FP64)
+ *   schedule   : SpMM schedule: -1 the library's default for this matrix, 1, 2, 4,
+ *                8, 16 or 32 threads per CSR row, or 64 the TMA-staged schedule
+ *                (each CTA bulk-copies a 256-row tile's col/val into shared memory,
+ *                a thread per row); anything else gives NS_ERR_INVALID_ARG.
+ * A bounded device wait that expires gives NS_ERR_TIMEOUT (no hang). */
 ns_status ns_apply_B(ns_handle* h, int d, const double* X, double* Y, double eps,
-                     int precision, int on_device);
+                     int precision, int on_device, int schedule);
 
 /* Eigen-decomposition of a symmetric k x k matrix (k <= 512) on the device with
- * the library's one-CTA FP64 solver (Householder tridiagonalization + implicit QL),
+ * the library's FP64 solver (Householder tridiagonalization in one CTA, Sturm
+ * multisection and inverse iteration spread over the SMs),
  * the solver used for the projected matrix T of Alg. 2 line 13.
  *   T     : k*k doubles, column-major, host memory (only the lower triangle is read)
  *   theta : k eigenvalues, ascending;  V : k*k column-major eigenvectors */

@@ -1,5 +1,7 @@
 // Sparse kernels: CSR validation, transpose, norms and the SpMM products of the
 // operator B = A^T A + eps D (or A + eps D), Eq. (defB) and Alg. 1 line 1.
+#include <algorithm>
+
 #include "ns_common.cuh"
 #include "ns_kernels.cuh"
 
@@ -147,6 +149,271 @@ __global__ void __launch_bounds__(kThreads) k_spmm_coldot(Csr<T> M, const T* __r
   }
 }
 
+// ---------------------------------------------------------------------------
+// TMA-staged schedule (lanes code kSchedTma): a CTA takes kTmaRows consecutive
+// rows per tile.  One thread copies the tile's col/val segment (the 16-byte
+// aligned span around it; the CSR arrays carry kCsrPad entries of padding) into
+// shared memory with cp.async.bulk, completing on an mbarrier, one tile ahead of
+// the CTA (double buffer).  Every thread then owns one row: its col/val come
+// from shared memory, so the only global loads left in the loop are the x
+// gathers, up to eight of them in flight per thread.  A tile whose segment exceeds
+// kTmaCap entries is read from global memory directly.  The mbarrier wait is
+// bounded: on expiry the kernel counts it in g_wait_timeouts and the CTA stops.
+// ---------------------------------------------------------------------------
+constexpr int kTmaRows = kThreads;
+constexpr int kTmaCap = 3072;
+constexpr int kTmaSlot = kTmaCap + 8;  // aligned span of kTmaCap entries + slack
+constexpr unsigned kWaitLimit = 1u << 22;  // tries of a bounded mbarrier wait
+
+__device__ unsigned g_wait_timeouts;
+
+struct TmaTile {
+  int64_t s, e;    // segment of the tile
+  int64_t cs, vs;  // first staged entry of col / val
+  int staged;
+  int pad;
+};
+
+template <typename T>
+constexpr size_t tma_smem_bytes() {
+  return 256 + 2 * (size_t)kTmaSlot * (sizeof(int) + sizeof(T));
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// non-blocking test with a short sleep between tries: at most kWaitLimit tries
+// (well under a second), then false
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+  for (unsigned it = 0; it < kWaitLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (it > 64) __nanosleep(64);
+  }
+  return false;
+}
+
+// thread 0: describe tile `tile` in info and, if it fits, start its bulk copies
+template <typename T>
+__device__ __forceinline__ void tma_issue(const Csr<T>& M, int64_t tile, TmaTile& info, int* col_s, T* val_s,
+                                          uint32_t bar) {
+  const int64_t r0 = tile * kTmaRows;
+  const int64_t r1 = (r0 + kTmaRows < M.nrows) ? r0 + kTmaRows : M.nrows;
+  const int64_t s = __ldg(M.rowptr + r0), e = __ldg(M.rowptr + r1);
+  constexpr int64_t va = 16 / (int64_t)sizeof(T);  // entries per 16 bytes
+  const int64_t cs = s & ~(int64_t)3, ce = (e + 3) & ~(int64_t)3;
+  const int64_t vs = s & ~(va - 1), ve = (e + va - 1) & ~(va - 1);
+  info.s = s;
+  info.e = e;
+  info.cs = cs;
+  info.vs = vs;
+  info.staged = (e > s && e - s <= kTmaCap) ? 1 : 0;
+  if (!info.staged) return;
+  const uint32_t bc = (uint32_t)(4 * (ce - cs)), bv = (uint32_t)(sizeof(T) * (ve - vs));
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bc + bv) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(col_s)),
+               "l"(M.col + cs), "r"(bc), "r"(bar)
+               : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(val_s)),
+               "l"(M.val + vs), "r"(bv), "r"(bar)
+               : "memory");
+}
+
+// LANCZOS = true: the fused Lanczos step (eps D x, -Q_{j-1} Gamma^T, Xi partials);
+// false: y = M v.
+template <typename T, int D, bool LANCZOS>
+__global__ void __launch_bounds__(kThreads) k_spmm_tma(Csr<T> M, const T* __restrict__ v, StepOps<T> op, T* y,
+                                                       Red red) {
+  constexpr int NP = D * D;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);     // 2 mbarriers
+  TmaTile* info = reinterpret_cast<TmaTile*>(smem_raw + 64);  // 2 tiles
+  int* col_s = reinterpret_cast<int*>(smem_raw + 256);        // 2 x kTmaSlot
+  T* val_s = reinterpret_cast<T*>(smem_raw + 256 + 2 * (size_t)kTmaSlot * sizeof(int));
+  __shared__ double red_s[(kThreads / 32) * NP];
+  __shared__ double tot[NP];
+  __shared__ T g_s[D * D];
+  __shared__ int abort_s;
+  const int tid = threadIdx.x;
+  const int64_t ntiles = (M.nrows + kTmaRows - 1) / kTmaRows;
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bars)) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bars + 1)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    abort_s = 0;
+  }
+  if constexpr (LANCZOS) {
+    if (tid < D * D) g_s[tid] = op.gprev ? (T)op.gprev[tid] : T(0);
+  }
+  __syncthreads();
+  if (tid == 0 && (int64_t)blockIdx.x < ntiles) tma_issue<T>(M, blockIdx.x, info[0], col_s, val_s, smem_u32(bars));
+  __syncthreads();
+  const bool has_prev = LANCZOS && op.qprev != nullptr;
+  T part[NP];
+#pragma unroll
+  for (int k = 0; k < NP; ++k) part[k] = T(0);
+  uint32_t par0 = 0u, par1 = 0u;  // phase parity of each mbarrier
+  int it = 0;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+    const int b = it & 1;
+    if (tid == 0 && tile + gridDim.x < ntiles)  // next tile into the other buffer (consumed last iteration)
+      tma_issue<T>(M, tile + gridDim.x, info[b ^ 1], col_s + (b ^ 1) * kTmaSlot, val_s + (b ^ 1) * kTmaSlot,
+                   smem_u32(bars + (b ^ 1)));
+    const int64_t row = tile * kTmaRows + tid;
+    const bool own = row < M.nrows;
+    int64_t rs = 0, re = 0;
+    T xi[D], qp[D];
+    T de = T(0);
+    if (own) {  // row bounds and epilogue operands first: independent of the staging
+      rs = __ldg(M.rowptr + row);
+      re = __ldg(M.rowptr + row + 1);
+      if constexpr (LANCZOS) {
+        load_row<T, D>(op.x + row * D, xi);
+        de = (T)op.eps * __ldg(op.Dv + row);
+        if (has_prev) load_row<T, D>(op.qprev + row * D, qp);
+      }
+    }
+    const TmaTile ti = info[b];
+    const bool prefetched = tile + gridDim.x < ntiles && info[b ^ 1].staged;
+    if (ti.staged) {
+      if (!mbar_wait_bounded(smem_u32(bars + b), b ? par1 : par0)) {
+        if (tid == 0) atomicAdd(&g_wait_timeouts, 1u);
+        abort_s = 1;
+      }
+      if (b)
+        par1 ^= 1u;
+      else
+        par0 ^= 1u;
+    }
+    __syncthreads();
+    if (abort_s) {  // leave no bulk copy in flight into this CTA's shared memory
+      if (tid == 0 && prefetched) mbar_wait_bounded(smem_u32(bars + (b ^ 1)), b ? par0 : par1);
+      return;
+    }
+    T acc[D];
+#pragma unroll
+    for (int q = 0; q < D; ++q) acc[q] = T(0);
+    if (own) {
+      const int* cp = ti.staged ? col_s + b * kTmaSlot - ti.cs : M.col;
+      const T* vp = ti.staged ? val_s + b * kTmaSlot - ti.vs : M.val;
+      constexpr int U = D >= 8 ? 2 : (D >= 4 ? 4 : 8);  // independent gathers in flight per thread
+      int64_t k = rs;
+      for (; k + U <= re; k += U) {
+        int c[U];
+        T a[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          c[u] = cp[k + u];
+          a[u] = vp[k + u];
+        }
+        T xv[U][D];
+#pragma unroll
+        for (int u = 0; u < U; ++u) load_row<T, D>(v + (int64_t)c[u] * D, xv[u]);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+          for (int q = 0; q < D; ++q) acc[q] = fma(a[u], xv[u][q], acc[q]);
+      }
+      if (k < re) {  // tail of fewer than U entries, loads first
+        const int nt = (int)(re - k);
+        int c[U];
+        T a[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          c[u] = u < nt ? cp[k + u] : 0;
+          a[u] = u < nt ? vp[k + u] : T(0);
+        }
+        T xv[U][D];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          if (u < nt) {
+            load_row<T, D>(v + (int64_t)c[u] * D, xv[u]);
+          } else {
+#pragma unroll
+            for (int q = 0; q < D; ++q) xv[u][q] = T(0);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+          for (int q = 0; q < D; ++q) acc[q] = fma(a[u], xv[u][q], acc[q]);
+      }
+      if constexpr (LANCZOS) {
+#pragma unroll
+        for (int q = 0; q < D; ++q) acc[q] = fma(de, xi[q], acc[q]);
+        if (has_prev) {
+#pragma unroll
+          for (int r = 0; r < D; ++r)
+#pragma unroll
+            for (int c = 0; c < D; ++c) acc[r] = fma(-qp[c], g_s[r * D + c], acc[r]);
+        }
+        store_row<T, D>(op.out + row * D, acc);
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+#pragma unroll
+          for (int bb = 0; bb < D; ++bb) part[a * D + bb] = fma(xi[a], acc[bb], part[a * D + bb]);
+      } else {
+        store_row<T, D>(y + row * D, acc);
+      }
+    }
+    __syncthreads();  // buffer b is refilled next iteration
+  }
+  if constexpr (LANCZOS) {
+    double pd[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) pd[k] = (double)part[k];
+    block_sum<NP>(pd, red_s, tot);
+    if (threadIdx.x < NP) red.part[(size_t)blockIdx.x * NP + threadIdx.x] = tot[threadIdx.x];
+    if (last_block_reduce(red.part, NP, red.ticket, tot, red_s)) {
+      if (threadIdx.x == 0) {
+        double X[D * D];
+        for (int a = 0; a < D; ++a)
+          for (int bb = 0; bb < D; ++bb) X[a * D + bb] = 0.5 * (tot[a * D + bb] + tot[bb * D + a]);
+        for (int k = 0; k < D * D; ++k) op.xi[k] = X[k];
+        *op.xi_norm = sym_norm2(X, D);
+      }
+    }
+  }
+}
+
+template <typename T, int D, bool LANCZOS>
+static void launch_tma(const Csr<T>& M, const T* v, const StepOps<T>& op, T* y, const Red& red, cudaStream_t s) {
+  static int cap = 0;  // resident CTAs of this instantiation (looked up once)
+  const void* fn = reinterpret_cast<const void*>(k_spmm_tma<T, D, LANCZOS>);
+  if (cap == 0) {
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma_smem_bytes<T>());
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, tma_smem_bytes<T>());
+    cap = std::max(1, std::min(per_sm, 8)) * std::max(sms, 1);
+  }
+  const int64_t ntiles = (M.nrows + kTmaRows - 1) / kTmaRows;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, cap));
+  k_spmm_tma<T, D, LANCZOS><<<grid, kThreads, tma_smem_bytes<T>(), s>>>(M, v, op, y, red);
+}
+
+unsigned spmm_wait_timeouts(bool clear) {
+  unsigned v = 0;
+  cudaMemcpyFromSymbol(&v, g_wait_timeouts, sizeof(unsigned));
+  if (clear && v) {
+    const unsigned z = 0;
+    cudaMemcpyToSymbol(g_wait_timeouts, &z, sizeof(unsigned));
+  }
+  return v;
+}
+
 #define NS_LANES_SWITCH(V, CALL) \
   switch (V) {                   \
     case 1: CALL(1); break;      \
@@ -160,6 +427,10 @@ __global__ void __launch_bounds__(kThreads) k_spmm_coldot(Csr<T> M, const T* __r
 template <typename T, int D>
 void spmm_plain(const Csr<T>& M, const T* v, T* y, cudaStream_t s) {
   if (M.nrows == 0) return;
+  if (M.V == kSchedTma) {
+    launch_tma<T, D, false>(M, v, StepOps<T>{}, y, Red{}, s);
+    return;
+  }
   const int grid = ceil_div(M.nrows * (int64_t)M.V, kThreads);
 #define CALL(VV) k_spmm_plain<T, D, VV><<<grid, kThreads, 0, s>>>(M, v, y)
   NS_LANES_SWITCH(M.V, CALL)
@@ -173,6 +444,10 @@ static int persistent_grid(int64_t nrows, int V) {
 
 template <typename T, int D>
 void spmm_lanczos(const Csr<T>& M, const T* v, const StepOps<T>& op, const Red& red, cudaStream_t s) {
+  if (M.V == kSchedTma) {
+    launch_tma<T, D, true>(M, v, op, nullptr, red, s);
+    return;
+  }
   const int grid = persistent_grid(M.nrows, M.V);
 #define CALL(VV) k_spmm_lanczos<T, D, VV><<<grid, kThreads, 0, s>>>(M, v, op, red)
   NS_LANES_SWITCH(M.V, CALL)
@@ -182,13 +457,15 @@ void spmm_lanczos(const Csr<T>& M, const T* v, const StepOps<T>& op, const Red& 
 template <typename T, int D>
 void spmm_coldot(const Csr<T>& M, const T* v, T* y, const T* w, int sq, double* dots, const Red& red,
                  cudaStream_t s) {
-  const int grid = persistent_grid(M.nrows, M.V);
+  const int V = M.V == kSchedTma ? 1 : M.V;  // the staged schedule serves the step products only
+  const int grid = persistent_grid(M.nrows, V);
 #define CALL(VV) k_spmm_coldot<T, D, VV><<<grid, kThreads, 0, s>>>(M, v, y, w, sq, red, dots)
-  NS_LANES_SWITCH(M.V, CALL)
+  NS_LANES_SWITCH(V, CALL)
 #undef CALL
 }
 
-// SpMM schedule autotuner: time y = M v for V in {1, 2, 4, 8, 16} lanes per row
+// SpMM schedule autotuner: time y = M v for the TMA-staged schedule and V in
+// {1, 2, 4, 8, 16} lanes per row
 // on the actual matrix (CUDA events, one warm-up + two timed launches each) and
 // return the fastest.
 template <typename T, int D>
@@ -199,7 +476,7 @@ int tune_lanes(Csr<T> M, const T* v, T* y, cudaStream_t s) {
   cudaEventCreate(&e1);
   int best = M.V;
   float best_ms = 1e30f;
-  for (int V = 1; V <= 16; V *= 2) {
+  for (int V : {kSchedTma, 1, 2, 4, 8, 16}) {
     M.V = V;
     spmm_plain<T, D>(M, v, y, s);
     cudaEventRecord(e0, s);

@@ -121,6 +121,7 @@ struct ns_handle {
   ns_stats_t stats{};
   long long launches = 0;
   Prof prof;
+  std::vector<std::pair<void*, size_t>> owned;  // matrix-side arrays and their sizes, freed by ns_destroy
 };
 
 // ---------------------------------------------------------------------------
@@ -156,6 +157,17 @@ void dfree(ns_handle* h, void* p, size_t bytes) {
   else
     cudaFree(p);
 }
+
+// allocation that lives as long as the handle (its size is kept for the free callback)
+void* dalloc_own(ns_handle* h, size_t bytes) {
+  void* p = dalloc(h, bytes);
+  h->owned.emplace_back(p, bytes ? bytes : 256);
+  return p;
+}
+
+// CSR col/val arrays end with kCsrPad entries of padding: the TMA-staged SpMM copies
+// the 16-byte aligned span around each tile's segment
+size_t csr_entries(int64_t nnz) { return (size_t)std::max<int64_t>(nnz, 1) + kCsrPad; }
 
 void ck_at(cudaError_t e, const char* what, int line) {
   if (e != cudaSuccess)
@@ -212,13 +224,13 @@ struct Prec<float> {
 
 void ensure_fp32(ns_handle* h) {
   if (!h->val32) {
-    h->val32 = (float*)dalloc(h, sizeof(float) * (size_t)std::max<int64_t>(h->nnz, 1));
+    h->val32 = (float*)dalloc_own(h, sizeof(float) * csr_entries(h->nnz));
     convert_d2f(h->val, h->val32, h->nnz, h->stream);
     if (h->mode == NS_MODE_NORMAL) {
-      h->val_t32 = (float*)dalloc(h, sizeof(float) * (size_t)std::max<int64_t>(h->nnz, 1));
+      h->val_t32 = (float*)dalloc_own(h, sizeof(float) * csr_entries(h->nnz));
       convert_d2f(h->val_t, h->val_t32, h->nnz, h->stream);
     }
-    h->D32 = (float*)dalloc(h, sizeof(float) * (size_t)h->n);
+    h->D32 = (float*)dalloc_own(h, sizeof(float) * (size_t)h->n);
     convert_d2f(h->D64, h->D32, h->n, h->stream);
     ck_launch("fp32 copies");
   }
@@ -433,7 +445,7 @@ struct Solver {
     cudaEventCreate(&e1);
     int best = M.V;
     float best_ms = 1e30f;
-    for (int V = 1; V <= 8; V *= 2) {
+    for (int V : {kSchedTma, 1, 2, 4, 8}) {  // the TMA-staged schedule and 1..8 lanes per row
       M.V = V;
       spmm_lanczos<T, D>(M, v, op, red, s);
       cudaEventRecord(e0, s);
@@ -1122,7 +1134,7 @@ static ns_status solve_typed(ns_handle* h, int R, double tol, const ns_opts& o) 
 }
 
 template <typename T, int D>
-static void apply_B_typed(ns_handle* h, const T* x, T* y, double eps, Red red) {
+static void apply_B_typed(ns_handle* h, const T* x, T* y, double eps, Red red, int schedule) {
   StepOps<T> op;
   op.x = x;
   op.Dv = Prec<T>::D(h);
@@ -1132,12 +1144,14 @@ static void apply_B_typed(ns_handle* h, const T* x, T* y, double eps, Red red) {
   op.xi = xi.as<double>();
   op.xi_norm = xi.as<double>() + 64;
   Csr<T> A = csr_A<T>(h);
+  Csr<T> At = h->mode == NS_MODE_SPD ? A : csr_At<T>(h);
+  if (schedule >= 0) A.V = At.V = schedule;
   if (h->mode == NS_MODE_SPD) {
     spmm_lanczos<T, D>(A, x, op, red, h->stream);
   } else {
     Buf yb(h, sizeof(T) * h->m * D);
     spmm_plain<T, D>(A, x, yb.as<T>(), h->stream);
-    spmm_lanczos<T, D>(csr_At<T>(h), yb.as<T>(), op, red, h->stream);
+    spmm_lanczos<T, D>(At, yb.as<T>(), op, red, h->stream);
     ck(cudaStreamSynchronize(h->stream), "sync");
   }
   ck(cudaStreamSynchronize(h->stream), "sync");
@@ -1272,9 +1286,9 @@ ns_status ns_create(ns_handle** out, int64_t m, int64_t n, const int64_t* rowptr
     h->nnz = nnz;
     cudaStream_t s = h->stream;
     const cudaMemcpyKind kind = inputs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    h->rowptr = (int64_t*)dalloc(h, sizeof(int64_t) * (m + 1));
-    h->col = (int*)dalloc(h, sizeof(int) * std::max<int64_t>(nnz, 1));
-    h->val = (double*)dalloc(h, sizeof(double) * std::max<int64_t>(nnz, 1));
+    h->rowptr = (int64_t*)dalloc_own(h, sizeof(int64_t) * (m + 1));
+    h->col = (int*)dalloc_own(h, sizeof(int) * csr_entries(nnz));
+    h->val = (double*)dalloc_own(h, sizeof(double) * csr_entries(nnz));
     ck(cudaMemcpyAsync(h->rowptr, rowptr, sizeof(int64_t) * (m + 1), kind, s), "copy rowptr");
     if (nnz) {
       ck(cudaMemcpyAsync(h->col, colind, sizeof(int) * nnz, kind, s), "copy colind");
@@ -1299,9 +1313,9 @@ ns_status ns_create(ns_handle** out, int64_t m, int64_t n, const int64_t* rowptr
     csr_max_abs_row_sum(h->rowptr, h->val, m, norms, red, s);
     h->launches += 1;
     if (mode == NS_MODE_NORMAL) {
-      h->rowptr_t = (int64_t*)dalloc(h, sizeof(int64_t) * (n + 1));
-      h->col_t = (int*)dalloc(h, sizeof(int) * std::max<int64_t>(nnz, 1));
-      h->val_t = (double*)dalloc(h, sizeof(double) * std::max<int64_t>(nnz, 1));
+      h->rowptr_t = (int64_t*)dalloc_own(h, sizeof(int64_t) * (n + 1));
+      h->col_t = (int*)dalloc_own(h, sizeof(int) * csr_entries(nnz));
+      h->val_t = (double*)dalloc_own(h, sizeof(double) * csr_entries(nnz));
       Buf wc(h, sizeof(int) * (n + 1)), wcur(h, sizeof(int64_t) * n), wp(h, sizeof(int64_t) * std::max<int64_t>(nnz, 1)),
           wr(h, sizeof(int) * std::max<int64_t>(nnz, 1)), wb(h, sizeof(int64_t) * (n / 4096 + 2));
       TransposeWork tw{wc.as<int>(), wcur.as<int64_t>(), wp.as<int64_t>(), wr.as<int>(), wb.as<int64_t>()};
@@ -1313,7 +1327,7 @@ ns_status ns_create(ns_handle** out, int64_t m, int64_t n, const int64_t* rowptr
       ck(cudaStreamSynchronize(s), "sync");
       for (int64_t r = 0; r < n; ++r) h->maxrow_At = std::max(h->maxrow_At, rpt[r + 1] - rpt[r]);
     }
-    h->D64 = (double*)dalloc(h, sizeof(double) * n);
+    h->D64 = (double*)dalloc_own(h, sizeof(double) * n);
     rng_uniform<double>(seed, 0u, h->D64, n, s);  // Alg. 2 line 1: D ~ U[0,1]
     double nr[2] = {0.0, 0.0};
     ck(cudaMemcpyAsync(nr, norms, sizeof(double) * 2, cudaMemcpyDeviceToHost, s), "d2h");
@@ -1363,6 +1377,10 @@ ns_status ns_solve(ns_handle* h, int d, int restart_len, double tol, const ns_op
       }
     }
     h->stats.kernel_launches = h->launches;
+    if (spmm_wait_timeouts(true)) {
+      h->solved = false;
+      return set_err(h, NS_ERR_TIMEOUT, "a bounded device wait of the SpMM expired; results discarded");
+    }
     return st;
   } catch (const Fail& f) {
     cudaGetLastError();
@@ -1430,16 +1448,8 @@ const char* ns_last_error(const ns_handle* h) {
 void ns_destroy(ns_handle* h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
-  dfree(h, h->rowptr, 0);
-  dfree(h, h->col, 0);
-  dfree(h, h->val, 0);
-  dfree(h, h->val32, 0);
-  dfree(h, h->rowptr_t, 0);
-  dfree(h, h->col_t, 0);
-  dfree(h, h->val_t, 0);
-  dfree(h, h->val_t32, 0);
-  dfree(h, h->D64, 0);
-  dfree(h, h->D32, 0);
+  for (auto& pr : h->owned) dfree(h, pr.first, pr.second);
+  h->owned.clear();
   dfree(h, h->basis, h->basis_bytes);
   delete h;
 }
@@ -1483,8 +1493,12 @@ ns_status ns_start_block(const ns_handle* hc, int d, double* Omega) {
   return NS_OK;
 }
 
-ns_status ns_apply_B(ns_handle* h, int d, const double* X, double* Y, double eps, int precision, int on_device) {
+ns_status ns_apply_B(ns_handle* h, int d, const double* X, double* Y, double eps, int precision, int on_device,
+                     int schedule) {
   if (!h || !X || !Y || !(d == 1 || d == 2 || d == 4 || d == 8)) return NS_ERR_INVALID_ARG;
+  if (!(schedule == -1 || schedule == kSchedTma || schedule == 1 || schedule == 2 || schedule == 4 ||
+        schedule == 8 || schedule == 16 || schedule == 32))
+    return set_err(h, NS_ERR_INVALID_ARG, "schedule must be -1, 64 or a power of two up to 32");
   try {
     const size_t cnt = (size_t)h->n * d;
     Buf xb(h, sizeof(double) * cnt), yb(h, sizeof(double) * cnt), rp(h, sizeof(double) * kMaxBlocks * 64 + 256),
@@ -1501,25 +1515,26 @@ ns_status ns_apply_B(ns_handle* h, int d, const double* X, double* Y, double eps
       Buf xf(h, sizeof(float) * cnt), yf(h, sizeof(float) * cnt);
       convert_d2f(xb.as<double>(), xf.as<float>(), (int64_t)cnt, h->stream);
       switch (d) {
-        case 1: apply_B_typed<float, 1>(h, xf.as<float>(), yf.as<float>(), eps, red); break;
-        case 2: apply_B_typed<float, 2>(h, xf.as<float>(), yf.as<float>(), eps, red); break;
-        case 4: apply_B_typed<float, 4>(h, xf.as<float>(), yf.as<float>(), eps, red); break;
-        default: apply_B_typed<float, 8>(h, xf.as<float>(), yf.as<float>(), eps, red); break;
+        case 1: apply_B_typed<float, 1>(h, xf.as<float>(), yf.as<float>(), eps, red, schedule); break;
+        case 2: apply_B_typed<float, 2>(h, xf.as<float>(), yf.as<float>(), eps, red, schedule); break;
+        case 4: apply_B_typed<float, 4>(h, xf.as<float>(), yf.as<float>(), eps, red, schedule); break;
+        default: apply_B_typed<float, 8>(h, xf.as<float>(), yf.as<float>(), eps, red, schedule); break;
       }
       convert_f2d(yf.as<float>(), yb.as<double>(), (int64_t)cnt, h->stream);
       ck(cudaStreamSynchronize(h->stream), "sync");
     } else {
       switch (d) {
-        case 1: apply_B_typed<double, 1>(h, xb.as<double>(), yb.as<double>(), eps, red); break;
-        case 2: apply_B_typed<double, 2>(h, xb.as<double>(), yb.as<double>(), eps, red); break;
-        case 4: apply_B_typed<double, 4>(h, xb.as<double>(), yb.as<double>(), eps, red); break;
-        default: apply_B_typed<double, 8>(h, xb.as<double>(), yb.as<double>(), eps, red); break;
+        case 1: apply_B_typed<double, 1>(h, xb.as<double>(), yb.as<double>(), eps, red, schedule); break;
+        case 2: apply_B_typed<double, 2>(h, xb.as<double>(), yb.as<double>(), eps, red, schedule); break;
+        case 4: apply_B_typed<double, 4>(h, xb.as<double>(), yb.as<double>(), eps, red, schedule); break;
+        default: apply_B_typed<double, 8>(h, xb.as<double>(), yb.as<double>(), eps, red, schedule); break;
       }
     }
     ck(cudaMemcpyAsync(Y, yb.p, sizeof(double) * cnt, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                        h->stream),
        "copy Y");
     ck(cudaStreamSynchronize(h->stream), "sync");
+    if (spmm_wait_timeouts(true)) throw Fail{NS_ERR_TIMEOUT, "a bounded device wait of the SpMM expired"};
   } catch (const Fail& f) {
     return set_err(h, f.st, f.msg);
   }

@@ -13,7 +13,7 @@ struct Csr {
   const int* col = nullptr;
   const T* val = nullptr;
   int64_t nrows = 0, ncols = 0, nnz = 0;
-  int V = 8;
+  int V = 8;  // lanes per row (1..32), or kSchedTma for the TMA-staged schedule
 };
 
 // Reduction workspace: partial sums and an atomic ticket for the last-block protocol
@@ -23,6 +23,10 @@ struct Red {
 };
 
 constexpr int kMaxBlocks = 152 * 8;  // persistent grid cap of reducing kernels
+constexpr int kSchedTma = 64;        // SpMM schedule code of the TMA-staged kernel
+constexpr int kCsrPad = 16;          // padding entries after col/val (16-byte aligned bulk copies)
+// bounded device waits that expired since the last call (clear: reset the count)
+unsigned spmm_wait_timeouts(bool clear);
 
 // Lanczos step epilogue operands (all device pointers)
 template <typename T>

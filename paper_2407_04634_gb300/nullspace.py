@@ -82,7 +82,7 @@ SIGNATURES = {
     "ns_get_transpose": (C.c_int, [_P, _P, _P, _P]),
     "ns_get_perturbation": (C.c_int, [_P, _P]),
     "ns_start_block": (C.c_int, [_P, C.c_int, _P]),
-    "ns_apply_B": (C.c_int, [_P, C.c_int, _P, _P, C.c_double, C.c_int, C.c_int]),
+    "ns_apply_B": (C.c_int, [_P, C.c_int, _P, _P, C.c_double, C.c_int, C.c_int, C.c_int]),
     "ns_syev": (C.c_int, [C.c_int, _P, _P, _P]),
     "ns_project": (C.c_int, [C.c_int64, C.c_int, C.c_int, _P, _P, _P, C.c_int]),
     "ns_project_noalloc": (C.c_int, [C.c_int64, C.c_int, C.c_int, _P, _P, _P, _P]),
@@ -253,12 +253,13 @@ class Handle:
         self._check(self.lib.ns_start_block(self.h, int(d), _ptr(Om)), "ns_start_block")
         return Om
 
-    def apply_B(self, X: np.ndarray, eps: float, precision: str = "fp64") -> np.ndarray:
+    def apply_B(self, X: np.ndarray, eps: float, precision: str = "fp64", schedule: int = -1) -> np.ndarray:
+        """Y = B X; schedule -1 = library default, 64 = TMA-staged, k = k threads per row."""
         X = np.ascontiguousarray(X, dtype=np.float64)
         d = X.shape[1]
         Y = np.zeros_like(X)
-        self._check(self.lib.ns_apply_B(self.h, d, _ptr(X), _ptr(Y), float(eps), PRECISION[precision], 0),
-                    "ns_apply_B")
+        self._check(self.lib.ns_apply_B(self.h, d, _ptr(X), _ptr(Y), float(eps), PRECISION[precision], 0,
+                                        int(schedule)), "ns_apply_B")
         return Y
 
     def close(self):

@@ -93,6 +93,53 @@ def test_apply_B_matches_oracle(ns, mode, d, precision):
     assert np.all(np.abs(Y - ref) <= tol * bound + 1e-300)
 
 
+def _skewed_matrix(seed, m, n):
+    """Sparse m x n matrix with empty rows (one whole 256-row tile among them), short
+    rows, and a few rows of 600-3000 entries (tiles too long to stage in shared
+    memory), m not a multiple of 256."""
+    rng = np.random.default_rng(seed)
+    lens = rng.integers(0, 12, size=m)
+    lens[rng.choice(m, 5, replace=False)] = rng.integers(600, 3000, size=5)
+    lens[rng.choice(m, 40, replace=False)] = 0
+    lens[256:512] = 0
+    rows = np.repeat(np.arange(m), lens)
+    cols = np.concatenate([rng.choice(n, size=k, replace=False) for k in lens])
+    vals = rng.standard_normal(rows.size)
+    return sp.csr_matrix((vals, (rows, cols)), shape=(m, n))
+
+
+@pytest.mark.parametrize("mode", ["spd", "normal"])
+@pytest.mark.parametrize("d,precision", [(1, "fp64"), (1, "mixed"), (2, "fp64"), (4, "mixed"), (8, "fp64")])
+@pytest.mark.parametrize("schedule", [64, 1, 4, 32])
+def test_apply_B_every_schedule(ns, mode, d, precision, schedule):
+    """Every SpMM schedule (TMA-staged and 1/4/32 threads per row) against the oracle's
+    operator, on rows from empty to 3000 entries and a ragged last tile."""
+    from workloads.graphs import CSR, Workload
+    M = _skewed_matrix(100 + d, 4099, 4099 if mode == "spd" else 3001)
+    w = Workload("skewed", CSR.from_scipy(M), mode, 0)
+    h = handle(ns, w, 5)
+    rng = np.random.default_rng(schedule + 7)
+    X = rng.standard_normal((w.A.n, d))
+    if precision == "mixed":
+        X = X.astype(np.float32).astype(np.float64)
+    D = h.perturbation()
+    ref = Operator(w.A.to_scipy(), mode, 1e-3, D).apply(X)
+    Y = h.apply_B(X, 1e-3, precision, schedule)
+    # first-order bound of a recursive sum of k terms: (k + 3) u sum |a x| per stage
+    # (the +3 covers the eps D x term and the rounding of A to FP32); the normal form
+    # adds the row length of its A^T stage
+    k = int(np.diff(M.indptr).max()) + (int(np.diff(M.tocsc().indptr).max()) if mode == "normal" else 0)
+    u = 2.0**-53 if precision == "fp64" else 2.0**-24
+    assert np.all(np.abs(Y - ref) <= (k + 3) * u * abs_bound(w, X, 1e-3, D) + 1e-300)
+
+
+def test_apply_B_rejects_unknown_schedule(ns):
+    w = laplacian_cycle_components(3, 3001, 3, 6, "uniform", 100, 2000)
+    h = handle(ns, w, 1)
+    with pytest.raises(ns.NullspaceError):
+        h.apply_B(np.ones((w.A.n, 1)), 1e-3, "fp64", 3)
+
+
 @pytest.mark.parametrize("k", [3, 17, 64, 120, 160])
 def test_syev_matches_dense_eigensolver(ns, k):
     rng = np.random.default_rng(k)
