@@ -366,19 +366,46 @@ __global__ void __launch_bounds__(kThreads) k_proj_update(VParts<T> V, const dou
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     T w[W];
     load_w<T, W>(Wp, Wp2, ldw, i, w);
-    for (int k = 0; k < V.kx; ++k) {
+    // V streamed in batches: all loads of a batch are issued before its FMAs, so each
+    // thread keeps 8 column loads in flight (the FMA chain on w is serial)
+    int k = 0;
+    for (; k + 8 <= V.kx; k += 8) {
+      T v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = V.X[(int64_t)(k + u) * n + i];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+#pragma unroll
+        for (int c = 0; c < W; ++c) w[c] = fma(-v[u], c_s[(k + u) * W + c], w[c]);
+    }
+    for (; k < V.kx; ++k) {
       const T v = V.X[(int64_t)k * n + i];
 #pragma unroll
       for (int c = 0; c < W; ++c) w[c] = fma(-v, c_s[k * W + c], w[c]);
     }
-    for (int b = 0; b < nzp; ++b) {
+    constexpr int PB = P >= 8 ? 1 : 8 / P;  // Z panels per batch
+    int b = 0;
+    for (; b + PB <= nzp; b += PB) {
+      T zr[PB][P];
+#pragma unroll
+      for (int u = 0; u < PB; ++u) load_row<T, P>(V.Z + (int64_t)(b + u) * n * P + i * P, zr[u]);
+#pragma unroll
+      for (int u = 0; u < PB; ++u)
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+          const int kk = V.kx + (b + u) * P + q;
+#pragma unroll
+          for (int c = 0; c < W; ++c) w[c] = fma(-zr[u][q], c_s[kk * W + c], w[c]);
+        }
+    }
+    for (; b < nzp; ++b) {
       T zr[P];
       load_row<T, P>(V.Z + (int64_t)b * n * P + i * P, zr);
 #pragma unroll
       for (int q = 0; q < P; ++q) {
-        const int k = V.kx + b * P + q;
+        const int kk = V.kx + b * P + q;
 #pragma unroll
-        for (int c = 0; c < W; ++c) w[c] = fma(-zr[q], c_s[k * W + c], w[c]);
+        for (int c = 0; c < W; ++c) w[c] = fma(-zr[q], c_s[kk * W + c], w[c]);
       }
     }
     store_w<T, W>(Wp, Wp2, ldw, i, w);
