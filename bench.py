@@ -559,7 +559,7 @@ def main():
     def traffic(c):
         key = c["name"] if c["name"] != "b_apply" else ("b_apply_fp64" if p["precision"] == "fp64" else "b_apply_mixed")
         if key == "cgs2_project" and p["precision"] != "fp64":
-            key = None  # captured in FP64 only
+            key = "cgs2_project_mixed"
         r = ncu_traffic_ratio(key) if key else None
         return None if r is None else r * c["bytes_per_launch"]
 
