@@ -291,11 +291,12 @@ def kernel_probe(ns, h, w, p):
         for sched in (64, 1, 2, 4, 8):  # every SpMM schedule once (TMA-staged, lanes per row)
             h.apply_B(X, 1e-3, prec, sched)
     V, _ = np.linalg.qr(rng.standard_normal((n, 256)))
-    W = rng.standard_normal((n, 2))
-    for prec in ("fp64", "mixed"):
-        t = time.perf_counter()
-        ns.project(V, W, prec)
-        out[f"project_{prec}_s"] = time.perf_counter() - t
+    for w in (2, 8):  # the merged [Q_j | Q_j+1] panel at d = 1 and d = 4
+        W = rng.standard_normal((n, w))
+        for prec in ("fp64", "mixed"):
+            t = time.perf_counter()
+            ns.project(V, W, prec)
+            out[f"project_w{w}_{prec}_s"] = time.perf_counter() - t
     print(json.dumps({"kernel_probe": p["name"], **out}), flush=True)
 
 

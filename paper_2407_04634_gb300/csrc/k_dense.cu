@@ -256,17 +256,25 @@ __device__ __forceinline__ void store_w(T* Wp, T* Wp2, int64_t ldw, int64_t i, c
 }
 
 // part[chunk][k][c] = sum over the rows of the chunk of V[i,k] W[i,c]
+// V columns per dots tile: wide panels take 4 so the kKT * W accumulators stay in
+// registers at 3+ CTAs per SM
+template <int W>
+constexpr int dots_kt() {
+  return W >= 8 ? 4 : kKT;
+}
+
 template <typename T, int W, int P>
 __global__ void __launch_bounds__(kThreads) k_proj_dots(VParts<T> V, const T* __restrict__ Wp,
                                                         const T* __restrict__ Wp2, int64_t ldw, int64_t n,
                                                         int64_t rows_per_chunk, double* part) {
-  constexpr int NP = kKT * W;
+  constexpr int KT = dots_kt<W>();
+  constexpr int NP = KT * W;
   __shared__ double red_s[(kThreads / 32) * NP];
   __shared__ double tot[NP];
   const int K = V.kx + V.kz;
-  const int tilesX = (V.kx + kKT - 1) / kKT;
+  const int tilesX = (V.kx + KT - 1) / KT;
   const bool isX = (int)blockIdx.y < tilesX;
-  const int k0 = isX ? blockIdx.y * kKT : V.kx + (blockIdx.y - tilesX) * kKT;  // first global column
+  const int k0 = isX ? blockIdx.y * KT : V.kx + (blockIdx.y - tilesX) * KT;  // first global column
   const int kend = isX ? V.kx : K;
   const int64_t r0 = (int64_t)blockIdx.x * rows_per_chunk;
   int64_t r1 = r0 + rows_per_chunk;
@@ -275,10 +283,10 @@ __global__ void __launch_bounds__(kThreads) k_proj_dots(VParts<T> V, const T* __
 #pragma unroll
   for (int k = 0; k < NP; ++k) acc[k] = T(0);
   // column base pointers of this tile (element i of column kk at base[kk] + i * stride)
-  const T* base[kKT];
+  const T* base[KT];
   int64_t stride = 1;
 #pragma unroll
-  for (int kk = 0; kk < kKT; ++kk) {
+  for (int kk = 0; kk < KT; ++kk) {
     const int k = k0 + kk;
     if (isX) {
       base[kk] = V.X + (int64_t)(k < kend ? k : 0) * n;
@@ -292,7 +300,7 @@ __global__ void __launch_bounds__(kThreads) k_proj_dots(VParts<T> V, const T* __
     T w[W];
     load_w<T, W>(Wp, Wp2, ldw, i, w);
 #pragma unroll
-    for (int kk = 0; kk < kKT; ++kk) {
+    for (int kk = 0; kk < KT; ++kk) {
       const T v = (k0 + kk < kend) ? base[kk][i * stride] : T(0);
 #pragma unroll
       for (int c = 0; c < W; ++c) acc[kk * W + c] = fma(v, w[c], acc[kk * W + c]);
@@ -338,7 +346,8 @@ void proj_dots(const VParts<T>& V, const T* Wp, const T* Wp2, int64_t ldw, int64
   if (K == 0) return;
   const int64_t rpc = dots_rows_per_chunk(n);
   const int nchunks = ceil_div(n, rpc);
-  dim3 grid(nchunks, ceil_div(V.kx, kKT) + ceil_div(V.kz, kKT));
+  constexpr int KT = dots_kt<W>();
+  dim3 grid(nchunks, ceil_div(V.kx, KT) + ceil_div(V.kz, KT));
 #define CALL(PP) k_proj_dots<T, W, PP><<<grid, kThreads, 0, s>>>(V, Wp, Wp2, ldw, n, rpc, part)
   NS_P_SWITCH(V.p, CALL)
 #undef CALL
@@ -346,12 +355,12 @@ void proj_dots(const VParts<T>& V, const T* Wp, const T* Wp2, int64_t ldw, int64
 }
 
 // W -= V C (C: K x W row-major FP64, staged in dynamic shared memory) ; optional Gram + Cholesky
-template <typename T, int W, int P>
+template <typename T, int W, int P, bool GRAM>
 __global__ void __launch_bounds__(kThreads) k_proj_update(VParts<T> V, const double* __restrict__ C,
                                                           T* __restrict__ Wp, T* __restrict__ Wp2, int64_t ldw,
                                                           int64_t n, int gram, double* R, double* gdiag,
                                                           unsigned* flags, Red red) {
-  constexpr int NP = W * W;
+  constexpr int NP = GRAM ? W * W : 1;  // Gram accumulators only in the fused-CholQR variant
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* c_s = reinterpret_cast<T*>(smem_raw);
   __shared__ double red_s[(kThreads / 32) * NP];
@@ -409,14 +418,15 @@ __global__ void __launch_bounds__(kThreads) k_proj_update(VParts<T> V, const dou
       }
     }
     store_w<T, W>(Wp, Wp2, ldw, i, w);
-    if (gram) {
+    if constexpr (GRAM) {
 #pragma unroll
       for (int p = 0; p < W; ++p)
 #pragma unroll
         for (int q = 0; q < W; ++q) part[p * W + q] = fma(w[p], w[q], part[p * W + q]);
     }
   }
-  if (!gram) return;
+  (void)gram;
+  if constexpr (!GRAM) return;
   double pd[NP];
 #pragma unroll
   for (int k = 0; k < NP; ++k) pd[k] = (double)part[k];
@@ -431,18 +441,26 @@ void proj_update(const VParts<T>& V, const double* C, T* Wp, T* Wp2, int64_t ldw
                  double* gdiag, unsigned* flags, const Red& red, cudaStream_t s) {
   const int K = V.kx + V.kz;
   const size_t smem = sizeof(T) * (size_t)K * W;
-#define CALL(PP)                                                                                         \
+#define CALL1(PP, GG)                                                                                   \
   do {                                                                                                   \
     static bool attr_set = false;                                                                        \
     if (!attr_set) {                                                                                     \
-      cudaFuncSetAttribute(k_proj_update<T, W, PP>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); \
+      cudaFuncSetAttribute(k_proj_update<T, W, PP, GG>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); \
       attr_set = true;                                                                                   \
     }                                                                                                    \
-    k_proj_update<T, W, PP><<<persistent_rows(n), kThreads, smem, s>>>(V, C, Wp, Wp2, ldw, n, gram, R, gdiag, \
-                                                                        flags, red);                     \
+    k_proj_update<T, W, PP, GG><<<persistent_rows(n), kThreads, smem, s>>>(V, C, Wp, Wp2, ldw, n, gram, R, \
+                                                                            gdiag, flags, red);          \
+  } while (0)
+#define CALL(PP)          \
+  do {                    \
+    if (gram)             \
+      CALL1(PP, true);    \
+    else                  \
+      CALL1(PP, false);   \
   } while (0)
   NS_P_SWITCH(V.p, CALL)
 #undef CALL
+#undef CALL1
 }
 
 #define NS_INST_PROJ(T, W)                                                                                     \

@@ -408,11 +408,12 @@ struct Solver {
   }
 
   void alloc_proj() {
+    // panels up to 2D = 16 wide (the merged [Q_j | Q_j+1] reorthogonalization at d = 8)
     const int K = cap + R + D;
-    cbuf = Buf(h, sizeof(double) * (size_t)K * 8 * 2);
+    cbuf = Buf(h, sizeof(double) * (size_t)K * 16);
     const int64_t rpc = std::min<int64_t>((int64_t)kThreads * 128, std::max<int64_t>(n, 1));
     const int nch = ceil_div(n, rpc);
-    dpart = Buf(h, sizeof(double) * (size_t)nch * K * 8);
+    dpart = Buf(h, sizeof(double) * (size_t)nch * K * 16);
   }
 
   void grow_locked(int need) {

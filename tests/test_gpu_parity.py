@@ -197,7 +197,7 @@ def test_config1_fp64_matches_oracle(ns):
     assert principal_sine(indicator_basis(w.labels), X) <= 1e-6
 
 
-@pytest.mark.parametrize("d", [1, 2, 4])
+@pytest.mark.parametrize("d", [1, 2, 4, 8])
 def test_cycle_laplacian_twin_fp64(ns, d):
     w = laplacian_cycle_components(21, 30000, 15, 8, "powerlaw", 50)
     ref = lanczos_nullspace(w.A.to_scipy(), "spd", d, 120, tol=1e-10, seed=1001)
@@ -240,6 +240,15 @@ def test_mixed_precision_twins(ns, case):
     r = h.solve(d, R, 1e-10, precision="mixed")
     assert r.nullity == w.nullity
     check_solution(w, h.basis(), w.nullity, U, 1e-5)
+
+
+def test_block_size_8_mixed(ns):
+    """d = 8: the merged partial-reorthogonalization panel is 16 columns wide."""
+    w = laplacian_cycle_components(21, 30000, 15, 8, "powerlaw", 50)
+    h = handle(ns, w, 2001)
+    r = h.solve(8, 120, 1e-10, precision="mixed")
+    assert r.nullity == 15
+    check_solution(w, h.basis(), 15, indicator_basis(w.labels), 1e-5)
 
 
 def test_full_rank_matrix_has_empty_null_space(ns):
