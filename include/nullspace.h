@@ -277,7 +277,9 @@ typedef struct {
  *   env    : allocator / stream as for ns_create, may be NULL (the library then
  *            uses its own non-blocking stream)
  * A_i must be symmetric PSD (not checked).  Errors: NS_ERR_INVALID_ARG (bad
- * count, size or CSR structure; nothing allocated), NS_ERR_OOM, NS_ERR_CUDA. */
+ * count, size or row structure, checked on the host before anything is
+ * allocated; a column index outside its instance or a non-finite value, checked
+ * on the device after the copy, everything freed again), NS_ERR_OOM, NS_ERR_CUDA. */
 ns_status ns_batch_create(ns_batch** out, int64_t count, const int64_t* n, const int64_t* rowptr,
                           const int32_t* colind, const double* vals, uint64_t seed, const ns_env* env);
 
@@ -291,7 +293,9 @@ ns_status ns_batch_create(ns_batch** out, int64_t count, const int64_t* n, const
  * >= 0 (default) replays the captured graph {queue reset, persistent launch},
  * re-capturing it only when an argument changed, use_graphs < 0 launches
  * directly.  The first
- * solve autotunes the SpMV lanes on a sample of instances.  Returns NS_OK when
+ * solve of a shape class (device, CTA size, restart_len, mean row length, largest
+ * instance) autotunes the SpMV lanes on a sample of instances; later handles of
+ * the same class in the process reuse that choice (t_tune_ms = 0).  Returns NS_OK when
  * every instance has status 0, else the first non-zero status among
  * NS_ERR_NOT_CONVERGED (max_matvec reached, or more than 32 null vectors) and
  * NS_ERR_REFINE; per-instance results stay readable either way. */
@@ -310,6 +314,12 @@ ns_status ns_batch_results(const ns_batch* hb, int32_t* nullity, int32_t* status
 /* Null-space basis of instance i: n_i x N_i column-major FP64 into out with
  * leading dimension ld >= n_i (host memory, or device memory if out_on_device). */
 ns_status ns_batch_basis(const ns_batch* hb, int64_t i, double* out, int64_t ld, int out_on_device);
+
+/* Every basis of the last solve in one call: instance i's n_i x N_i column-major
+ * block starts at offset sum_{j<i} n_j N_j of out (sum_i n_i N_i doubles; N_i
+ * from ns_batch_results).  out is host memory, or device memory if out_on_device;
+ * a host copy goes through one device staging buffer and one transfer. */
+ns_status ns_batch_basis_packed(const ns_batch* hb, double* out, int out_on_device);
 
 ns_status ns_batch_stats(const ns_batch* hb, ns_batch_stats_t* s);
 const char* ns_batch_last_error(const ns_batch* hb);

@@ -8,6 +8,8 @@
 // stopping rule of Sec. 4.3, and the FP64 CG projection onto null(A) followed by
 // FP64 re-orthonormalization.  Vectors are FP32, every scalar of the projected
 // problem FP64.  No CTA ever waits for another one.
+#include <algorithm>
+
 #include "../../include/nullspace.h"
 #include "ns_common.cuh"
 #include "ns_kernels.cuh"
@@ -956,6 +958,52 @@ void batched_launch(const BatchArgs& a, int lanes, int block, int grid, cudaStre
       default: k_batched<4, 256><<<grid, 256, smem, s>>>(a); break;
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// ingest and output helpers of the batched form (one CTA per instance)
+// ---------------------------------------------------------------------------
+// every entry: column inside the instance, finite value (bit 2: column, bit 4: value)
+__global__ void k_batch_validate(const int64_t* __restrict__ rowptr, const int64_t* __restrict__ rp_off,
+                                 const int64_t* __restrict__ nz_off, const int* __restrict__ nrows,
+                                 const int* __restrict__ col, const double* __restrict__ val, int count,
+                                 unsigned* err) {
+  for (int i = blockIdx.x; i < count; i += gridDim.x) {
+    const int n = nrows[i];
+    const int64_t* rp = rowptr + rp_off[i];
+    const int64_t e0 = rp[0], e1 = rp[n];
+    const int* c = col + nz_off[i];
+    const double* v = val + nz_off[i];
+    unsigned bad = 0;
+    for (int64_t k = e0 + threadIdx.x; k < e1; k += blockDim.x) {
+      const int cc = c[k];
+      if (cc < 0 || cc >= n) bad |= 2u;
+      if (!isfinite(v[k])) bad |= 4u;
+    }
+    if (bad) atomicOr(err, bad);
+  }
+}
+
+// instance i's first N_i basis columns (n_i x N_i, column-major, contiguous at
+// basis + out_off[i]) to packed + poff[i]
+__global__ void k_batch_pack(const double* __restrict__ basis, const int64_t* __restrict__ out_off,
+                             const int64_t* __restrict__ poff, const int64_t* __restrict__ plen, int count,
+                             double* __restrict__ packed) {
+  for (int i = blockIdx.x; i < count; i += gridDim.x) {
+    const double* src = basis + out_off[i];
+    double* dst = packed + poff[i];
+    for (int64_t k = threadIdx.x; k < plen[i]; k += blockDim.x) dst[k] = src[k];
+  }
+}
+
+void batch_validate(const BatchArgs& a, unsigned* err, cudaStream_t s) {
+  k_batch_validate<<<std::min(a.count, 152 * 16), 256, 0, s>>>(a.rowptr, a.rp_off, a.nz_off, a.nrows, a.col,
+                                                               a.val64, a.count, err);
+}
+
+void batch_pack(const double* basis, const int64_t* out_off, const int64_t* poff, const int64_t* plen, int count,
+                double* packed, cudaStream_t s) {
+  k_batch_pack<<<std::min(count, 152 * 16), 256, 0, s>>>(basis, out_off, poff, plen, count, packed);
 }
 
 size_t batched_ws32_per_slot(int nmax, int R) { return (size_t)nmax * (2 * R + 1 + kBMaxLock + 2) + 64; }

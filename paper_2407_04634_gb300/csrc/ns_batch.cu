@@ -9,8 +9,13 @@
 #include <string>
 #include <vector>
 
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "../../include/nullspace.h"
 #include "ns_batch.cuh"
+#include "ns_kernels.cuh"
 
 struct ns_batch {
   ns_env env{};
@@ -116,6 +121,25 @@ void drop_graph(ns_batch* h) {
 
 bool same_args(const ns::BatchArgs& a, const ns::BatchArgs& b) { return std::memcmp(&a, &b, sizeof(a)) == 0; }
 
+// Autotuner results shared by every handle of the process, per shape class: device,
+// CTA size, restart length, mean row length (quarter steps) and the largest
+// instance (powers of two).  A new batch of the same class skips the tuning runs.
+using TuneKey = std::tuple<int, int, int, int64_t, int>;
+std::mutex g_tune_mutex;
+std::map<TuneKey, int> g_tune_cache;
+
+TuneKey tune_key(const ns_batch* h, int dev, int block, int R) {
+  int64_t rows = 0, nz = 0;
+  for (int64_t i = 0; i < h->count; ++i) {
+    rows += h->n_h[i];
+    nz += h->nnz_h[i];
+  }
+  const int64_t len4 = rows ? (4 * nz + rows / 2) / rows : 0;
+  int lg = 0;
+  while ((1 << lg) < h->nmax) ++lg;
+  return TuneKey(dev, block, R, len4, lg);
+}
+
 }  // namespace
 
 extern "C" {
@@ -144,9 +168,8 @@ ns_status ns_batch_create(ns_batch** out, int64_t count, const int64_t* n, const
     nmax = std::max(nmax, n[i]);
   }
   if (nz_tot > 0 && (!colind || !vals)) return NS_ERR_INVALID_ARG;
-  for (int64_t i = 0; i < count; ++i)
-    for (int64_t k = nz_off[i]; k < nz_off[i] + nnz[i]; ++k)
-      if (colind[k] < 0 || colind[k] >= n[i] || !std::isfinite(vals[k])) return NS_ERR_INVALID_ARG;
+  // the row structure is checked above on the host; the entries (columns, values)
+  // are checked on the device right after the copy
   ns_batch* h = new ns_batch();
   if (env && env->alloc) {
     h->env = *env;
@@ -173,12 +196,11 @@ ns_status ns_batch_create(ns_batch** out, int64_t count, const int64_t* n, const
     std::vector<int> order(count);
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return nnz[a] + n[a] > nnz[b] + n[b]; });
-    std::vector<float> v32(nz_tot);
-    for (int64_t k = 0; k < nz_tot; ++k) v32[k] = (float)vals[k];
     h->rowptr = bput(h, rowptr, (size_t)rp_tot);
     h->col = bput(h, reinterpret_cast<const int*>(colind), (size_t)nz_tot);
-    h->val = bput(h, v32.data(), (size_t)nz_tot);
     h->val64 = bput(h, vals, (size_t)nz_tot);
+    h->val = static_cast<float*>(balloc(h, sizeof(float) * (size_t)std::max<int64_t>(nz_tot, 1)));
+    ns::convert_d2f(h->val64, h->val, nz_tot, h->stream);
     h->rp_off = bput(h, rp_off.data(), (size_t)count);
     h->nz_off = bput(h, nz_off.data(), (size_t)count);
     h->out_off = bput(h, out_off.data(), (size_t)count);
@@ -195,7 +217,25 @@ ns_status ns_batch_create(ns_batch** out, int64_t count, const int64_t* n, const
     h->status = static_cast<int*>(balloc(h, sizeof(int) * (size_t)count));
     h->istats = static_cast<long long*>(balloc(h, sizeof(long long) * ns::kBStats * (size_t)count));
     h->queue = static_cast<unsigned*>(balloc(h, 256));
-    bck(cudaStreamSynchronize(h->stream), "ingest");
+    {  // entry checks on the device
+      ns::BatchArgs va;
+      std::memset(&va, 0, sizeof(va));
+      va.rowptr = h->rowptr;
+      va.rp_off = h->rp_off;
+      va.nz_off = h->nz_off;
+      va.nrows = h->nrows;
+      va.col = h->col;
+      va.val64 = h->val64;
+      va.count = (int)count;
+      unsigned* err = h->queue + 32;  // spare word of the queue's 256-byte block
+      bck(cudaMemsetAsync(err, 0, sizeof(unsigned), h->stream), "memset");
+      ns::batch_validate(va, err, h->stream);
+      bck(cudaGetLastError(), "k_batch_validate");
+      unsigned e = 0;
+      bck(cudaMemcpyAsync(&e, err, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream), "d2h");
+      bck(cudaStreamSynchronize(h->stream), "ingest");
+      if (e) throw BFail{NS_ERR_INVALID_ARG, "column index out of range or non-finite value"};
+    }
   } catch (const BFail& f) {
     ns_batch_destroy(h);
     return f.st;
@@ -282,6 +322,15 @@ ns_status ns_batch_solve(ns_batch* h, int d, int restart_len, double tol, const 
     // ---- autotuner: SpMV lanes per row, judged by the SM cycles the sampled
     // instances take while running side by side (first solve only) ----
     if (h->lanes == 0 || h->tuned_block != block) {
+      std::lock_guard<std::mutex> lock(g_tune_mutex);
+      auto it = g_tune_cache.find(tune_key(h, dev, block, R));
+      if (it != g_tune_cache.end()) {
+        h->lanes = it->second;
+        h->tuned_block = block;
+        h->t_tune_ms = 0.0;
+      }
+    }
+    if (h->lanes == 0 || h->tuned_block != block) {
       ns::BatchArgs t = a;
       t.order = h->order_sample;
       t.count = h->sample_count;
@@ -314,6 +363,8 @@ ns_status ns_batch_solve(ns_batch* h, int d, int restart_len, double tol, const 
       h->t_tune_ms = ms;
       h->lanes = best_l;
       h->tuned_block = block;
+      std::lock_guard<std::mutex> lock(g_tune_mutex);
+      g_tune_cache[tune_key(h, dev, block, R)] = best_l;
     }
     h->bps = bps[h->lanes];
     h->grid = (int)std::min<int64_t>(h->count, (int64_t)h->bps * sms);
@@ -433,6 +484,49 @@ ns_status ns_batch_basis(const ns_batch* hc, int64_t i, double* out, int64_t ld,
   } catch (const BFail& f) {
     return bset_err(h, f.st, f.msg);
   }
+  return NS_OK;
+}
+
+ns_status ns_batch_basis_packed(const ns_batch* hc, double* out, int out_on_device) {
+  ns_batch* h = const_cast<ns_batch*>(hc);
+  if (!h || !out) return NS_ERR_INVALID_ARG;
+  if (!h->solved) return bset_err(h, NS_ERR_STATE, "ns_batch_basis_packed before ns_batch_solve");
+  std::vector<int64_t> poff(h->count), plen(h->count);
+  int64_t tot = 0;
+  for (int64_t i = 0; i < h->count; ++i) {
+    poff[i] = tot;
+    plen[i] = h->n_h[i] * (int64_t)h->nullity_h[i];
+    tot += plen[i];
+  }
+  if (tot == 0) return NS_OK;
+  void* dpo = nullptr;
+  void* dpl = nullptr;
+  void* stage = nullptr;
+  try {
+    dpo = balloc(h, sizeof(int64_t) * (size_t)h->count);
+    dpl = balloc(h, sizeof(int64_t) * (size_t)h->count);
+    bck(cudaMemcpyAsync(dpo, poff.data(), sizeof(int64_t) * poff.size(), cudaMemcpyHostToDevice, h->stream), "h2d");
+    bck(cudaMemcpyAsync(dpl, plen.data(), sizeof(int64_t) * plen.size(), cudaMemcpyHostToDevice, h->stream), "h2d");
+    double* dst = out;
+    if (!out_on_device) {
+      stage = balloc(h, sizeof(double) * (size_t)tot);
+      dst = static_cast<double*>(stage);
+    }
+    ns::batch_pack(h->basis, h->out_off, static_cast<int64_t*>(dpo), static_cast<int64_t*>(dpl), (int)h->count, dst,
+                   h->stream);
+    bck(cudaGetLastError(), "k_batch_pack");
+    if (!out_on_device)
+      bck(cudaMemcpyAsync(out, stage, sizeof(double) * (size_t)tot, cudaMemcpyDeviceToHost, h->stream), "d2h");
+    bck(cudaStreamSynchronize(h->stream), "basis pack");
+  } catch (const BFail& f) {
+    bfree(h, stage);
+    bfree(h, dpl);
+    bfree(h, dpo);
+    return bset_err(h, f.st, f.msg);
+  }
+  bfree(h, stage);
+  bfree(h, dpl);
+  bfree(h, dpo);
   return NS_OK;
 }
 

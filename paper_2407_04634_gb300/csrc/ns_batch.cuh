@@ -52,6 +52,12 @@ cudaError_t batched_prepare(int lanes, int block, int R, int* blocks_per_sm);
 // One persistent launch of grid CTAs of `block` threads (128 or 256) over the
 // queue a.queue (which must read 0).
 void batched_launch(const BatchArgs& a, int lanes, int block, int grid, cudaStream_t s);
+// Entry checks of a freshly copied batch (column inside the instance, finite value):
+// ORs 2 (column) / 4 (value) into *err.
+void batch_validate(const BatchArgs& a, unsigned* err, cudaStream_t s);
+// Gather every instance's n_i x N_i basis block (plen[i] = n_i N_i doubles) to packed + poff[i].
+void batch_pack(const double* basis, const int64_t* out_off, const int64_t* poff, const int64_t* plen, int count,
+                double* packed, cudaStream_t s);
 // Workspace per CTA slot, in elements.
 size_t batched_ws32_per_slot(int nmax, int R);
 size_t batched_ws64_per_slot(int nmax);

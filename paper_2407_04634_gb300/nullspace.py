@@ -90,6 +90,7 @@ SIGNATURES = {
     "ns_batch_solve": (C.c_int, [_P, C.c_int, C.c_int, C.c_double, C.POINTER(NsOpts)]),
     "ns_batch_results": (C.c_int, [_P, _P, _P, _P]),
     "ns_batch_basis": (C.c_int, [_P, C.c_int64, _P, C.c_int64, C.c_int]),
+    "ns_batch_basis_packed": (C.c_int, [_P, _P, C.c_int]),
     "ns_batch_stats": (C.c_int, [_P, C.POINTER(NsBatchStats)]),
     "ns_batch_last_error": (C.c_char_p, [_P]),
     "ns_batch_destroy": (None, [_P]),
@@ -373,6 +374,19 @@ class Batch:
         X = np.zeros((int(N[i]), n), dtype=np.float64)
         self._check(self.lib.ns_batch_basis(self.h, int(i), _ptr(X), n, 0), "ns_batch_basis")
         return X.T
+
+    def basis_packed(self, out=None) -> np.ndarray:
+        """Every instance's basis in one transfer: instance i's n_i x N_i block, column-major,
+        at offset sum_{j<i} n_j N_j.  out may be a host array or a CUDA torch tensor."""
+        N, _, _ = self.results()
+        tot = int((self.n * N).sum())
+        if out is not None and hasattr(out, "data_ptr"):
+            self._check(self.lib.ns_batch_basis_packed(self.h, C.c_void_p(out.data_ptr()), 1), "ns_batch_basis_packed")
+            return out
+        if out is None:
+            out = np.zeros(tot, dtype=np.float64)
+        self._check(self.lib.ns_batch_basis_packed(self.h, _ptr(out), 0), "ns_batch_basis_packed")
+        return out
 
     def stats(self) -> dict:
         s = NsBatchStats()

@@ -123,6 +123,26 @@ def test_invalid_arguments(ns):
         ns.Batch([(A.rowptr, bad, A.vals)], 1)
 
 
+def test_packed_basis_and_device_entry_checks(ns):
+    """ns_batch_basis_packed returns every instance's basis back to back, identical to
+    the per-instance calls; a non-finite value is rejected by the device-side checks."""
+    ws = batched_laplacians(config_seed(5) + 17, 5, n_min=150, n_max=700)
+    b = ns.Batch([w.A for w in ws], 321)
+    b.solve(R, TOL, eps=EPS)
+    P = b.basis_packed()
+    ref = np.concatenate([b.basis(i).ravel(order="F") for i in range(len(ws))])
+    np.testing.assert_array_equal(P, ref)
+    import torch
+    Pd = torch.empty(P.size, dtype=torch.float64, device="cuda")
+    b.basis_packed(Pd)
+    np.testing.assert_array_equal(Pd.cpu().numpy(), ref)
+    A = ws[1].A
+    bad = A.vals.copy()
+    bad[7] = np.nan
+    with pytest.raises(ns.NullspaceError):
+        ns.Batch([ws[0].A, (A.rowptr, A.colind, bad)], 1)
+
+
 def test_empty_rows_and_isolated_vertices(ns):
     """Isolated vertices (empty rows) are components of size one: e_k is a null vector."""
     ws = batched_laplacians(config_seed(5) + 16, 1, n_min=300, n_max=300)
