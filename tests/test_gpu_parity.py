@@ -242,6 +242,16 @@ def test_mixed_precision_twins(ns, case):
     check_solution(w, h.basis(), w.nullity, U, 1e-5)
 
 
+def test_long_restart_fp64(ns):
+    """restart_len 448 in FP64: the restart products take the chunked kernel (the row-tile
+    FP64 kernel stages all R basis columns and serves R <= 400)."""
+    w = laplacian_cycle_components(24, 20000, 9, 8, "powerlaw", 50)
+    h = handle(ns, w, 2002)
+    r = h.solve(1, 448, 1e-10)
+    assert r.nullity == 9
+    check_solution(w, h.basis(), 9, indicator_basis(w.labels), 1e-6)
+
+
 def test_block_size_8_mixed(ns):
     """d = 8: the merged partial-reorthogonalization panel is 16 columns wide."""
     w = laplacian_cycle_components(21, 30000, 15, 8, "powerlaw", 50)
