@@ -306,10 +306,7 @@ __global__ void __launch_bounds__(kThreads) k_proj_dots(VParts<T> V, const T* __
       for (int c = 0; c < W; ++c) acc[kk * W + c] = fma(v, w[c], acc[kk * W + c]);
     }
   }
-  double pd[NP];
-#pragma unroll
-  for (int k = 0; k < NP; ++k) pd[k] = (double)acc[k];
-  block_sum<NP>(pd, red_s, tot);
+  block_sum_t<T, NP>(acc, red_s, tot);
   for (int t = threadIdx.x; t < NP; t += blockDim.x) {
     const int k = k0 + t / W;
     if (k < kend) part[((size_t)blockIdx.x * K + k) * W + (t % W)] = tot[t];

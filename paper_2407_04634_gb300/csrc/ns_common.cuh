@@ -92,6 +92,34 @@ __device__ inline void block_sum(const double (&v)[NV], double* red, double* out
   __syncthreads();
 }
 
+// block_sum for partials held in T: the 32-lane step runs in T (FP32 shuffles and
+// adds for float, which are cheap next to FP64 ones), the cross-warp sum in FP64
+template <typename T, int NV>
+__device__ inline void block_sum_t(const T (&v)[NV], double* red, double* out) {
+  if constexpr (sizeof(T) == 8) {
+    double d[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) d[k] = (double)v[k];
+    block_sum<NV>(d, red, out);
+  } else {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      float s = (float)v[k];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) red[warp * NV + k] = (double)s;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < NV; k += blockDim.x) {
+      double s = 0.0;
+      for (int w = 0; w < nw; ++w) s += red[w * NV + k];
+      out[k] = s;
+    }
+    __syncthreads();
+  }
+}
+
 // "Last block" protocol: each block writes NV partial sums to part[block*NV+k];
 // the block that arrives last (atomic ticket) sums all partials in block order
 // and returns true with the totals in tot[0..NV) (shared memory).  The ticket
