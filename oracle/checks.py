@@ -1,4 +1,4 @@
-"""Reference quantities used to judge any computed null-space basis.
+"""Reference quantities for checking any computed null-space basis.
 
 TEST INFRASTRUCTURE ONLY (part of the CPU oracle).
 """

@@ -319,7 +319,7 @@ ns_status ns_batch_solve(ns_batch* h, int d, int restart_len, double tol, const 
     a.istats = h->istats;
     a.queue = h->queue;
     int64_t launches = 0;
-    // ---- autotuner: SpMV lanes per row, judged by the SM cycles the sampled
+    // ---- autotuner: SpMV lanes per row, ranked by the SM cycles the sampled
     // instances take while running side by side (first solve only) ----
     if (h->lanes == 0 || h->tuned_block != block) {
       std::lock_guard<std::mutex> lock(g_tune_mutex);
