@@ -240,24 +240,31 @@ __device__ int cta_jacobi_sweeps(F* A, F* V, int R, bool init_identity, double r
         js.s[k] = (qq < R) ? (double)sn : 0.0;
       }
       __syncthreads();
-      for (int t = tid; t < np * R; t += nt) {  // rows p, q  (A <- J^T A)
-        const int k = t / R, j = t % R;
-        const int pp = js.p[k], qq = js.q[k];
-        if (pp == qq) continue;
-        const F c = (F)js.c[k], sn = (F)js.s[k];
-        const F apj = A[pp * R + j], aqj = A[qq * R + j];
-        A[pp * R + j] = c * apj - sn * aqj;
-        A[qq * R + j] = sn * apj + c * aqj;
+      // the np rotations of a round act on disjoint index pairs, so A <- M A M^T is
+      // applied in one pass: thread -> 2 x 2 block (pairs a, b), new block =
+      // M_a X M_b^T; V <- V M^T on the pairs' columns in the same pass.  A dummy
+      // pair (odd R) has q == p and the identity rotation.
+      for (int t = tid; t < np * np; t += nt) {
+        const int a = t / np, b = t % np;
+        const int pa = js.p[a], qa = js.q[a], pb = js.p[b], qb = js.q[b];
+        const F ca = (F)js.c[a], sa = (F)js.s[a], cb = (F)js.c[b], sb = (F)js.s[b];
+        const bool ra = qa != pa, rb = qb != pb;
+        const F x00 = A[pa * R + pb];
+        const F x01 = rb ? A[pa * R + qb] : F(0);
+        const F x10 = ra ? A[qa * R + pb] : F(0);
+        const F x11 = (ra && rb) ? A[qa * R + qb] : F(0);
+        const F y00 = ca * x00 - sa * x10, y01 = ca * x01 - sa * x11;  // rows: M_a X
+        const F y10 = sa * x00 + ca * x10, y11 = sa * x01 + ca * x11;
+        A[pa * R + pb] = cb * y00 - sb * y01;  // columns: (M_a X) M_b^T
+        if (rb) A[pa * R + qb] = sb * y00 + cb * y01;
+        if (ra) A[qa * R + pb] = cb * y10 - sb * y11;
+        if (ra && rb) A[qa * R + qb] = sb * y10 + cb * y11;
       }
-      __syncthreads();
-      for (int t = tid; t < np * R; t += nt) {  // columns p, q  (A <- A J, V <- V J)
+      for (int t = tid; t < np * R; t += nt) {
         const int k = t / R, i = t % R;
         const int pp = js.p[k], qq = js.q[k];
         if (pp == qq) continue;
         const F c = (F)js.c[k], sn = (F)js.s[k];
-        const F aip = A[i * R + pp], aiq = A[i * R + qq];
-        A[i * R + pp] = c * aip - sn * aiq;
-        A[i * R + qq] = sn * aip + c * aiq;
         const F vip = V[i * R + pp], viq = V[i * R + qq];
         V[i * R + pp] = c * vip - sn * viq;
         V[i * R + qq] = sn * vip + c * viq;
