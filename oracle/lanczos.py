@@ -59,6 +59,10 @@ Readings of points the paper leaves open (each is also listed in the design doc):
   R12 breakdown (sigma_min(Gamma) <= 100 u_d): the block is replaced by a fresh
       Gaussian block (Philox stream 2+k) orthogonalized against [X, Z], and
       Gamma is set to zero.
+
+Parity unpinned: the stopping rule (R11) is a heuristic with no closed form or
+printed example to check it against; it is pinned only through its outcome (the
+nullity is exact on every test matrix, so the run did not stop early).
 """
 
 from __future__ import annotations
