@@ -34,8 +34,33 @@ sys.path.insert(0, ROOT)
 
 METRIC = "converged null vecs/s at rel. residual 1e-8"
 UNIT = "null_vecs/s"
-HBM_GBS = 6783.5          # measured copy bandwidth of the GB300s
-FP64_TFLOPS = 152 * 4 * 2.07e9 / 1e12  # 152 SMs x 4 FP64 flop/clk (1.25 TF nominal) x 2.07 GHz
+HBM_GBS = 6800.0          # fallback copy bandwidth when MEASURED_PEAKS.json is absent
+FP64_TFLOPS_DERIVED = 152 * 4 * 2.07e9 / 1e12  # 152 SMs x 4 FP64 flop/clk x 2.07 GHz (fallback only)
+
+
+def alu_peaks(ns, local):
+    """FP64 and FP32 FMA throughput measured on this device (ns_fma_peak), in TFLOP/s,
+    with the median SM clock sampled while it ran (so a rate can be rescaled to the
+    clock of another timed region: the FMA rate is proportional to the SM clock)."""
+    out = {}
+    for prec in ("fp64", "mixed"):
+        clocks = ClockSampler(local)
+        clocks.start()
+        try:
+            vals = [ns.fma_peak(prec) for _ in range(3)]
+            val, src = max(vals), "measured: ns_fma_peak (8 FMA chains x 256 threads x 8 CTAs per SM), best of 3"
+        except Exception as e:  # reported, not hidden
+            val, src = (FP64_TFLOPS_DERIVED if prec == "fp64" else None), f"derived (measurement failed: {e})"
+        clk = clocks.stop()
+        out[prec] = (val, src, clk.get("sm_mhz"))
+    return out
+
+
+def at_clock(peak, peak_mhz, mhz):
+    """A pipe's peak measured at peak_mhz, rescaled to the SM clock mhz of a timed region."""
+    if peak is None or not peak_mhz or not mhz:
+        return peak
+    return peak * mhz / peak_mhz
 
 
 def peaks():
@@ -301,6 +326,43 @@ def closed_form_sine(w, X):
     return float(torch.linalg.eigvalsh(G)[-1].clamp_min(0).sqrt())
 
 
+def device_csr(A, device="cuda"):
+    """scipy CSR -> torch sparse CSR (FP64) on the device (for the independent checks)."""
+    import numpy as np
+    import torch
+    A = A.tocsr()
+    return torch.sparse_csr_tensor(torch.as_tensor(A.indptr.astype(np.int64), device=device),
+                                   torch.as_tensor(A.indices.astype(np.int64), device=device),
+                                   torch.as_tensor(A.data.astype(np.float64), device=device),
+                                   size=A.shape, dtype=torch.float64)
+
+
+def norm2_power(Ad, AdT, iters=150):
+    """||A||_2 by power iteration on A^T A (a lower bound: residual ratios are over-, never
+    under-estimated).  AdT is None for a symmetric A."""
+    import torch
+    g = torch.Generator(device=Ad.device).manual_seed(0)
+    x = torch.randn((Ad.shape[1], 1), dtype=torch.float64, device=Ad.device, generator=g)
+    x /= torch.linalg.norm(x)
+    lam = 0.0
+    for _ in range(iters):
+        y = Ad @ x
+        y = (AdT @ y) if AdT is not None else (Ad @ y)
+        lam = float(torch.linalg.norm(y))
+        x = y / lam
+    return lam ** 0.5
+
+
+def residual_ratio(Ad, X, normA, chunk=64):
+    """||A X||_F / ||A||_2 for a device basis X (n x N), in column chunks."""
+    import torch
+    tot = 0.0
+    for c0 in range(0, X.shape[1], chunk):
+        R = Ad @ X[:, c0:c0 + chunk].contiguous()
+        tot += float(torch.sum(R * R))
+    return tot ** 0.5 / normA
+
+
 def kernel_probe(ns, h, w, p):
     """A handful of hot-kernel launches on the full-size inputs (for ncu captures):
     three B-applies in each precision and two CGS2 projections against 256 vectors."""
@@ -352,7 +414,7 @@ def bench_batched(args, world, rank, local):
     n = np.array([w.A.n for w in ws], dtype=np.int64)
     rp = np.concatenate([w.A.rowptr for w in ws])
     ci = np.concatenate([w.A.colind for w in ws])
-    va = np.concatenate([w.A.vals for w in ws])
+    va = np.concatenate([w.A.vals for w in ws]).astype(np.float32)  # FP32 CSR, as given (vals_is_fp32)
     nnz = np.array([w.A.nnz for w in ws], dtype=np.int64)
     expect = np.array([w.nullity for w in ws])
     stream = torch.cuda.Stream()
@@ -510,6 +572,7 @@ def main():
     ap.add_argument("--profile-every", type=int, default=16)
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision sub-record")
     ap.add_argument("--scale", type=float, default=1.0, help="workload scale (< 1 is for profiling only)")
     ap.add_argument("--kernel-probe", action="store_true", help="launch a few hot kernels, no bench line")
     ap.add_argument("--loop-sample", type=int, default=32,
@@ -541,93 +604,135 @@ def main():
     p = workload_params(args)
     w = build_workload(p)
     A = w.A
-    h = ns.Handle(A.rowptr, A.colind, A.vals, A.m, A.n, p["solver_seed"], p["mode"])
+    # configuration 4's values are FP32 numbers and go in as FP32 (vals_is_fp32)
+    vals_in = A.vals.astype(np.float32) if p["cfg"] == 4 else A.vals
+    h = ns.Handle(A.rowptr, A.colind, vals_in, A.m, A.n, p["solver_seed"], p["mode"])
     stream = torch.cuda.current_stream()
     if args.kernel_probe:
         kernel_probe(ns, h, w, p)
         return
 
-    def one_step(profile=0):
-        r = h.solve(p["d"], p["restart"], p["tol"], check=False, precision=p["precision"], profile=profile)
-        return r
+    alu = alu_peaks(ns, local)
+    fp64_peak_raw, fp64_src, fp64_mhz = alu["fp64"]
 
     def valid(r):
         return (r.status == ns.NS_OK and r.nullity == w.nullity and r.stats.get("refine_resid_max", 1) <= 1e-8)
 
-    for _ in range(args.warmup):
-        one_step()
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clocks = ClockSampler(local)
-    clocks.start()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    results = [one_step(profile=args.profile_every) for _ in range(args.steps)]
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1)
-    prof = h.profile()  # kernel classes of the last timed step
-    units = sum(r.nullity for r in results if valid(r))
-    all_valid = all(valid(r) for r in results)
-    t_max, units = reduce_over_ranks(ms, float(units), dist, "cuda")
-    value = units / (t_max / 1e3)
-    launches = sum(r.stats.get("kernel_launches", 0) for r in results)
+    def timed_solves(precision):
+        """W untimed warm-up solves, then K solves bracketed by barrier + synchronize
+        and CUDA events on the library stream; returns (ms max over ranks, units, results,
+        profile of the last solve, clocks)."""
+        def one_step(profile=0):
+            return h.solve(p["d"], p["restart"], p["tol"], check=False, precision=precision, profile=profile)
+        for _ in range(args.warmup):
+            one_step()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        clocks = ClockSampler(local)
+        clocks.start()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        results = [one_step(profile=args.profile_every) for _ in range(args.steps)]
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        ms = ev0.elapsed_time(ev1)
+        prof = h.profile()  # kernel classes of the last timed step
+        units = sum(r.nullity for r in results if valid(r))
+        t_max, units = reduce_over_ranks(ms, float(units), dist, "cuda")
+        return t_max, units, results, prof, clk
 
-    # roofline of the dominant kernel class and of the B-apply (SpMM) class
     pk = peaks()
-    dom = max(prof, key=lambda c: (c["ms_total_est"], c["launches"]))
 
-    def traffic(c):
-        key = c["name"] if c["name"] != "b_apply" else ("b_apply_fp64" if p["precision"] == "fp64" else "b_apply_mixed")
-        if key == "cgs2_project" and p["precision"] != "fp64":
-            key = "cgs2_project_mixed"
-        r = ncu_traffic_ratio(key) if key else None
-        return None if r is None else r * c["bytes_per_launch"]
-
-    def roof(c):
+    def roof(c, precision, clk):
         if not c["sampled"] or c["ms_per_launch"] <= 0:
             return {"kernel": c["name"], "bound": None, "achieved": None, "peak": None, "unit": None,
                     "frac": None, "traffic": None, "note": "not sampled (run with --profile-every > 0)"}
-        if c["name"] == "b_apply":
-            ach = c["bytes_per_launch"] / (c["ms_per_launch"] / 1e3) / 1e9
-            return {"kernel": c["name"], "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                    "frac": ach / pk["hbm_gbs"], "traffic": traffic(c), "peak_src": pk["src"],
-                    "bytes_per_launch": c["bytes_per_launch"], "ms_per_launch": c["ms_per_launch"],
-                    "launches": c["launches"], "sampled": c["sampled"]}
-        if p["precision"] == "fp64":
-            ach = c["flops_per_launch"] / (c["ms_per_launch"] / 1e3) / 1e12
-            return {"kernel": c["name"], "bound": "alu", "achieved": ach, "peak": FP64_TFLOPS, "unit": "TFLOP/s",
-                    "frac": ach / FP64_TFLOPS, "traffic": traffic(c),
-                    "peak_src": "derived: 152 SMs x 4 FP64 flop/clk x 2.07 GHz",
-                    "flops_per_launch": c["flops_per_launch"], "ms_per_launch": c["ms_per_launch"],
-                    "launches": c["launches"], "sampled": c["sampled"]}
-        ach = c["bytes_per_launch"] / (c["ms_per_launch"] / 1e3) / 1e9
-        return {"kernel": c["name"], "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": ach / pk["hbm_gbs"], "traffic": traffic(c), "peak_src": pk["src"],
-                "bytes_per_launch": c["bytes_per_launch"], "ms_per_launch": c["ms_per_launch"],
+        key = c["name"] if c["name"] != "b_apply" else ("b_apply_fp64" if precision == "fp64" else "b_apply_mixed")
+        if key == "cgs2_project" and precision != "fp64":
+            key = "cgs2_project_mixed"
+        ratio = ncu_traffic_ratio(key)
+        traffic = None if ratio is None else ratio * c["bytes_per_launch"]
+        base = {"kernel": c["name"], "traffic": traffic, "bytes_per_launch": c["bytes_per_launch"],
+                "flops_per_launch": c["flops_per_launch"], "ms_per_launch": c["ms_per_launch"],
                 "launches": c["launches"], "sampled": c["sampled"]}
+        if c["name"] != "b_apply" and precision == "fp64" and c["flops_per_launch"] > 0:
+            # the FP64 path's dense products have more flops per byte than the FP64 pipe's ridge
+            ach = c["flops_per_launch"] / (c["ms_per_launch"] / 1e3) / 1e12
+            fp64_peak = at_clock(fp64_peak_raw, fp64_mhz, clk.get("sm_mhz"))
+            return {**base, "bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
+                    "frac": ach / fp64_peak,
+                    "peak_src": f"{fp64_src}; {fp64_peak_raw:.4f} TFLOP/s at {fp64_mhz} MHz, rescaled to the "
+                                f"timed region's {clk.get('sm_mhz')} MHz"}
+        ach = c["bytes_per_launch"] / (c["ms_per_launch"] / 1e3) / 1e9
+        return {**base, "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / pk["hbm_gbs"], "peak_src": pk["src"]}
 
-    roofline = roof(dom)
-    spmm = roof(next(c for c in prof if c["name"] == "b_apply"))
+    # independent checks of a basis (outside the timed region): closed-form sine, and the
+    # residual ||A X||_F / ||A||_2 recomputed with PyTorch's sparse product and a
+    # power-iteration ||A||_2 (not the library's own refinement statistics)
+    As = A.to_scipy()
+    Ad = AdT = None
+    normA_ind = None
 
-    # basis of the last timed solve against the closed-form null space (outside the timing)
-    sine = None
-    if results[-1].nullity == w.nullity and w.nullity > 0:
+    def basis_checks(r):
+        nonlocal Ad, AdT, normA_ind
+        if r.nullity != w.nullity or w.nullity == 0:
+            return None, None
+        if Ad is None:
+            Ad = device_csr(As)
+            AdT = device_csr(As.T.tocsr()) if p["mode"] == "normal" else None
+            normA_ind = norm2_power(Ad, AdT)
         Xd = torch.empty((w.nullity, A.n), dtype=torch.float64, device="cuda")
         h.basis(out=Xd)
         sine = closed_form_sine(w, Xd.T)
+        res = residual_ratio(Ad, Xd.T, normA_ind)
         del Xd
         torch.cuda.empty_cache()
+        return sine, res
+
+    t_max, units, results, prof, clk = timed_solves(p["precision"])
+    value = units / (t_max / 1e3)
+    all_valid = all(valid(r) for r in results)
+    launches = sum(r.stats.get("kernel_launches", 0) for r in results)
+    dom = max(prof, key=lambda c: (c["ms_total_est"], c["launches"]))
+    roofline = roof(dom, p["precision"], clk)
+    spmm = roof(next(c for c in prof if c["name"] == "b_apply"), p["precision"], clk)
+    sine, res_ind = basis_checks(results[-1])
+    all_valid = all_valid and res_ind is not None and res_ind <= 1e-8
+
+    # the metric's comparison: the mixed-precision path on the same resident matrix, the
+    # same number of warm-up and timed solves
+    mixed = None
+    if p["precision"] == "fp64" and not args.no_mixed:
+        mt, mu, mres, mprof, mclk = timed_solves("mixed")
+        msine, mres_ind = basis_checks(mres[-1])
+        mvalid = all(valid(r) for r in mres) and mres_ind is not None and mres_ind <= 1e-8
+        mdom = max(mprof, key=lambda c: (c["ms_total_est"], c["launches"]))
+        mlast = mres[-1].stats
+        mixed = {"value": mu / (mt / 1e3), "unit": UNIT, "ms_per_step": mt / args.steps, "steps": args.steps,
+                 "warmup": args.warmup, "valid": bool(mvalid), "dtype": "f32+f64",
+                 "vs_fp64": (mu / (mt / 1e3)) / value if value > 0 else None,
+                 "basis_check": {"sine_vs_closed_form": msine, "residual_independent": mres_ind,
+                                 "residual_library": mlast.get("refine_resid_max")},
+                 "roofline": roof(mdom, "mixed", mclk), "spmm_roofline": roof(
+                     next(c for c in mprof if c["name"] == "b_apply"), "mixed", mclk),
+                 "clocks": mclk, "gpu_launches": int(sum(r.stats.get("kernel_launches", 0) for r in mres)),
+                 "solve": {k: mlast.get(k) for k in ("nullity", "matvecs", "restarts", "reorth_X", "reorth_Z",
+                                                     "lock_events", "refine_iters_max", "t_lanczos_ms",
+                                                     "t_refine_ms")},
+                 "kernel_classes": [{k: c[k] for k in ("name", "launches", "sampled", "ms_per_launch",
+                                                       "ms_total_est")} for c in mprof]}
+        launches += mixed["gpu_launches"]
 
     # end-to-end through the public API: pinned host CSR -> ns_create -> ns_solve -> basis to pinned host
     rp = torch.from_numpy(A.rowptr).pin_memory()
     ci = torch.from_numpy(A.colind).pin_memory()
-    va = torch.from_numpy(A.vals).pin_memory()
+    va = torch.from_numpy(vals_in).pin_memory()
     out = torch.empty((w.nullity, A.n), dtype=torch.float64).pin_memory()
-    h2d = rp.numel() * 8 + ci.numel() * 4 + va.numel() * 8
+    h2d = rp.numel() * 8 + ci.numel() * 4 + va.numel() * va.element_size()
     d2h = out.numel() * 8
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -660,8 +765,10 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if p["precision"] == "fp64" else "f32+f64",
             "data": "synthetic", "config": describe(p, w), "valid": all_valid,
             "gpu_launches": int(launches), "clocks": clk, "roofline": roofline, "spmm_roofline": spmm,
-            "e2e": e2e, "cpu_baseline": cpu,
-            "basis_check": {"sine_vs_closed_form": sine, "residual_max": last.get("refine_resid_max"),
+            "e2e": e2e, "cpu_baseline": cpu, "mixed": mixed,
+            "alu_peaks_tflops": {k: {"value": v[0], "src": v[1], "sm_mhz": v[2]} for k, v in alu.items()},
+            "basis_check": {"sine_vs_closed_form": sine, "residual_independent": res_ind,
+                            "residual_library": last.get("refine_resid_max"), "normA_power_iteration": normA_ind,
                             "bars": "sine <= 1e-6 (FP64) / 1e-5 (mixed), residual <= 1e-8"},
             "solve": {k: last.get(k) for k in ("nullity", "matvecs", "restarts", "reorth_X", "reorth_Z",
                                                "lock_events", "refine_iters_max", "refine_resid_max",

@@ -39,7 +39,9 @@ typedef enum {
   NS_ERR_NOT_CONVERGED = 4, /* max_matvec reached; basis holds what was locked     */
   NS_ERR_TIMEOUT = 5,       /* a bounded device wait gave up (no hang)             */
   NS_ERR_STATE = 6,         /* call out of order (e.g. basis before solve)         */
-  NS_ERR_REFINE = 7         /* some column missed the refinement tolerance          */
+  NS_ERR_REFINE = 7,        /* some column missed the refinement tolerance          */
+  NS_ERR_NUMERICAL = 8      /* a block lost rank during reorthogonalization; a
+                               numerical event of the iteration, not a CUDA failure */
 } ns_status;
 
 typedef enum {
@@ -115,19 +117,25 @@ typedef struct ns_handle ns_handle;
 void ns_default_opts(ns_opts* o);
 
 /* ns_create -- copy A (m x n CSR) to the device, build A^T (normal mode) by a
- * stable counting sort, bound ||B|| and draw D (Alg. 2 line 1, Eq. defB).
+ * stable counting sort, bound ||B|| and draw D (Alg. 2 line 1, Eq. defB).  The
+ * problem statement of Sec. 1.1: a sparse A is given, its null space is sought.
  *   rowptr  : m+1 int64, rowptr[0] = 0, non-decreasing, rowptr[m] = nnz
  *   colind  : nnz int32 in [0, n)
- *   vals    : nnz double, finite
+ *   vals    : nnz values, finite: double when vals_is_fp32 = 0, float when 1
+ *   vals_is_fp32 : 1 = FP32 values; they are kept as given for the mixed path and
+ *             widened exactly to FP64 on the device (FP64 path, refinement); no
+ *             host-side conversion is needed
  *   inputs_on_device : 0 = the three arrays are host memory, 1 = device memory
  *   seed    : Philox-4x32-10 key for D (stream 0) and the start block (stream 1)
  *   mode    : ns_mode; NS_MODE_SPD requires m == n and a symmetric PSD A (not checked)
  *   env     : allocator / stream, may be NULL; copied into the handle
- * Errors: NS_ERR_INVALID_ARG for m < 0, n <= 0, m < n in normal mode is allowed
- * but slow (Remark in Sec. 1.1), broken CSR structure (host inputs are fully
- * checked; device inputs are checked on the device), NaN/Inf values. */
+ * Ownership: the arrays are copied; the caller keeps them.
+ * Errors: NS_ERR_INVALID_ARG for m < 0, n <= 0, vals_is_fp32 not 0 or 1, broken CSR
+ * structure (host inputs are fully checked; device inputs are checked on the
+ * device), NaN/Inf values.  m < n in normal mode is allowed but slow (Remark in
+ * Sec. 1.1). */
 ns_status ns_create(ns_handle** out, int64_t m, int64_t n, const int64_t* rowptr,
-                    const int32_t* colind, const double* vals, int inputs_on_device,
+                    const int32_t* colind, const void* vals, int vals_is_fp32, int inputs_on_device,
                     uint64_t seed, int mode, const ns_env* env);
 
 /* ns_solve -- Alg. 2 with locking and refinement (Sec. 4).
@@ -137,7 +145,8 @@ ns_status ns_create(ns_handle** out, int64_t m, int64_t n, const int64_t* rowptr
  *                 ||Gamma_l V_Z(last block, i)|| <= tol * ||B|| (Remark cormain)
  *   opts        : NULL = defaults
  * Returns NS_OK, NS_ERR_NOT_CONVERGED (max_matvec reached; the basis holds the
- * vectors locked so far), NS_ERR_REFINE (a column missed refine_tol), or an error.
+ * vectors locked so far), NS_ERR_REFINE (a column missed refine_tol),
+ * NS_ERR_NUMERICAL (a reorthogonalized block lost rank), or an error.
  * May be called again on the same handle (new solve, same D and start seed). */
 ns_status ns_solve(ns_handle* h, int d, int restart_len, double tol, const ns_opts* opts);
 
@@ -205,6 +214,28 @@ ns_status ns_start_block(const ns_handle* h, int d, double* Omega);
 ns_status ns_apply_B(ns_handle* h, int d, const double* X, double* Y, double eps,
                      int precision, int on_device, int schedule);
 
+/* ns_fma_peak -- measured FMA throughput of the current device, in TFLOP/s (two
+ * flops per FMA), for precision NS_FP64 (the FP64 pipe) or NS_MIXED (the FP32
+ * pipe).  The paper has no counterpart: it is the roofline denominator of the
+ * FP64 path, whose dense products are bound by the FP64 pipe.  Runs a grid of 8
+ * CTAs of 256 threads per SM, each thread 8 independent FMA chains; the best of
+ * three timed launches after one warm-up (about 50 ms each).  Allocates and frees
+ * a small device buffer; uses the legacy default stream. */
+ns_status ns_fma_peak(int precision, double* tflops);
+
+/* ns_trace_omega -- the W recurrence of Sec. 4.2 (the bounds w_{k,l} on
+ * ||Q_k^T Q_l|| that decide partial reorthogonalization) exactly as ns_solve
+ * computes it, exposed so that it can be checked on its own.  Runs the first
+ * Lanczos cycle of ns_solve on this handle (start block, steps 1 .. nb-1 with the
+ * reorthogonalizations they trigger; no restart, no locking) with the same d,
+ * restart_len and opts (eps, precision, reorth), and records every new W column.
+ *   W : (nb+1) x (nb+1) doubles, column-major, host memory, nb = restart_len / d.
+ *       Entry (b, c), b < c, c >= 2, is w_{b,c} as the recurrence produced it,
+ *       before the reset to u_d that a reorthogonalization makes; columns 0 and 1
+ *       (set to u_d by definition) and entries b >= c are 0.
+ * Does not change the handle's last solve result.  Errors as for ns_solve. */
+ns_status ns_trace_omega(ns_handle* h, int d, int restart_len, const ns_opts* opts, double* W);
+
 /* Eigen-decomposition of a symmetric k x k matrix (k <= 512) on the device with
  * the library's FP64 solver (Householder tridiagonalization in one CTA, Sturm
  * multisection and inverse iteration spread over the SMs),
@@ -222,20 +253,28 @@ ns_status ns_project(int64_t n, int K, int w, const double* V, double* W, double
 
 /* ns_project_noalloc -- the same FP64 CGS2 projection as ns_project, for callers
  * that cannot allocate device memory while they run (code inside a CUDA graph
- * being captured, an allocator's own callback, hosts that only hand over
- * pre-allocated buffers).  The paper has no counterpart; this is a service of
- * the library.  It allocates nothing: its scratch is a fixed 4 MiB device array
- * inside the library (held on every GPU that loads the library until exit).
+ * being captured, where cudaMalloc is refused; an allocator's own callback, which
+ * must not re-enter the allocator; hosts that only hand over pre-allocated
+ * buffers).  The paper has no counterpart; this is a service of the library.  It
+ * allocates nothing: its scratch is a fixed 4 MiB device array inside the library
+ * (held on every GPU that loads the library until exit).
  *   V : n x K column-major FP64, device memory (read)
  *   W : n x w row-major FP64,   device memory (overwritten by W - V V^T W, twice)
  *   C : K x w row-major FP64,   device memory (receives the summed coefficients)
  *   stream : cudaStream_t, NULL = legacy default stream; the call only enqueues work
  * Limits: w in {1, 2, 4, 8}; K*w*(ceil(n/32768)+1) <= 524288 and K*w <= 24320,
- * else NS_ERR_INVALID_ARG (nothing enqueued).  The first call on a device looks
- * up the scratch address (cudaGetSymbolAddress); make that first call before any
- * stream capture.  All calls share the one scratch array and every call fully
- * overwrites what it reads, so calls that overlap on the GPU (different streams,
- * no ordering) race and give wrong results. */
+ * else NS_ERR_INVALID_ARG (nothing enqueued).
+ * Set-up: the first call on a device (and the first after that device's context
+ * was reset) looks up the scratch address and raises the projection kernels'
+ * shared-memory limit; it must be made outside any stream capture.  Made while
+ * `stream` is capturing, it returns NS_ERR_STATE and enqueues nothing.  Later calls
+ * only enqueue kernels.
+ * Errors: an error already pending on the calling thread gives NS_ERR_CUDA, is left
+ * pending for the caller, and nothing is enqueued.  A launch of this call that
+ * fails gives NS_ERR_CUDA; W and C are then undefined (partly projected).
+ * Sharing: all calls share the one scratch array and every call fully overwrites
+ * what it reads, so calls that overlap on the GPU (different streams, no ordering)
+ * race and give wrong results. */
 ns_status ns_project_noalloc(int64_t n, int K, int w, const double* V, double* W, double* C, void* stream);
 
 /* ------------------------------------------------------------------------
@@ -272,7 +311,10 @@ typedef struct {
  *   rowptr : the count local row-pointer arrays back to back (n_i + 1 int64 each,
  *            starting at 0, non-decreasing)
  *   colind : the entries' column indices back to back (int32, local to the instance)
- *   vals   : the entries' values back to back (double, finite; also kept as FP32)
+ *   vals   : the entries' values back to back, finite: double when vals_is_fp32 =
+ *            0 (an FP32 copy is made for the Lanczos phase), float when 1 (kept as
+ *            given; an exact FP64 widening is made on the device for the refinement)
+ *   vals_is_fp32 : 0 or 1, see vals
  *   seed   : Philox key of instance 0 (instance i uses seed + i)
  *   env    : allocator / stream as for ns_create, may be NULL (the library then
  *            uses its own non-blocking stream)
@@ -281,7 +323,8 @@ typedef struct {
  * allocated; a column index outside its instance or a non-finite value, checked
  * on the device after the copy, everything freed again), NS_ERR_OOM, NS_ERR_CUDA. */
 ns_status ns_batch_create(ns_batch** out, int64_t count, const int64_t* n, const int64_t* rowptr,
-                          const int32_t* colind, const double* vals, uint64_t seed, const ns_env* env);
+                          const int32_t* colind, const void* vals, int vals_is_fp32, uint64_t seed,
+                          const ns_env* env);
 
 /* ns_batch_solve -- solve every instance.  d must be 1; restart_len in [8, 64]
  * and every n_i >= restart_len + 34 (the basis, its next vector and up to 32

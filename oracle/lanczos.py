@@ -24,7 +24,7 @@ large-scale null space computations":
     final FP64 projection of every basis vector onto null(A) by CG (CGLS in the
     normal mode) followed by a Rayleigh-Ritz step on (AX)^T (AX).
 
-Readings of points the paper leaves open (each is also listed in the design doc):
+Readings of points the paper leaves open (the CUDA path takes the same readings):
   R1  the recurrence subtracts Q_{l-1} Gamma_{l-1}^T (Eq. laniterfp), not Gamma_{l-1};
   R2  W is strictly upper triangular: w_{i,j} = 0 whenever i >= j, and the three
       cases of Sec. 4.2 fill entries 1..l of column l+1;

@@ -434,17 +434,16 @@ __global__ void __launch_bounds__(kThreads) k_proj_update(VParts<T> V, const dou
 }
 
 template <typename T, int W>
-void proj_update(const VParts<T>& V, const double* C, T* Wp, T* Wp2, int64_t ldw, int64_t n, int gram, double* R,
-                 double* gdiag, unsigned* flags, const Red& red, cudaStream_t s) {
+cudaError_t proj_update(const VParts<T>& V, const double* C, T* Wp, T* Wp2, int64_t ldw, int64_t n, int gram,
+                        double* R, double* gdiag, unsigned* flags, const Red& red, cudaStream_t s) {
   const int K = V.kx + V.kz;
   const size_t smem = sizeof(T) * (size_t)K * W;
-#define CALL1(PP, GG)                                                                                   \
+  cudaError_t e = cudaSuccess;
+#define CALL1(PP, GG)                                                                                    \
   do {                                                                                                   \
-    static bool attr_set = false;                                                                        \
-    if (!attr_set) {                                                                                     \
-      cudaFuncSetAttribute(k_proj_update<T, W, PP, GG>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); \
-      attr_set = true;                                                                                   \
-    }                                                                                                    \
+    const void* fn = reinterpret_cast<const void*>(k_proj_update<T, W, PP, GG>);                         \
+    e = ensure_smem_limit(fn, smem);                                                                     \
+    if (e != cudaSuccess) return e;                                                                      \
     k_proj_update<T, W, PP, GG><<<persistent_rows(n), kThreads, smem, s>>>(V, C, Wp, Wp2, ldw, n, gram, R, \
                                                                             gdiag, flags, red);          \
   } while (0)
@@ -458,13 +457,25 @@ void proj_update(const VParts<T>& V, const double* C, T* Wp, T* Wp2, int64_t ldw
   NS_P_SWITCH(V.p, CALL)
 #undef CALL
 #undef CALL1
+  return e;
+}
+
+// Raises the shared-memory limit of the single-panel update kernels (P = 1, with and
+// without the fused Gram) to `bytes` on the current device ahead of time, so that a
+// later launch needs no attribute change (e.g. while a stream is being captured).
+template <typename T, int W>
+cudaError_t proj_update_reserve_smem(size_t bytes) {
+  cudaError_t e = ensure_smem_limit(reinterpret_cast<const void*>(k_proj_update<T, W, 1, false>), bytes);
+  if (e == cudaSuccess) e = ensure_smem_limit(reinterpret_cast<const void*>(k_proj_update<T, W, 1, true>), bytes);
+  return e;
 }
 
 #define NS_INST_PROJ(T, W)                                                                                     \
   template void proj_dots<T, W>(const VParts<T>&, const T*, const T*, int64_t, int64_t, double*, double*,       \
                                 cudaStream_t);                                                                 \
-  template void proj_update<T, W>(const VParts<T>&, const double*, T*, T*, int64_t, int64_t, int, double*,      \
-                                  double*, unsigned*, const Red&, cudaStream_t);
+  template cudaError_t proj_update<T, W>(const VParts<T>&, const double*, T*, T*, int64_t, int64_t, int,        \
+                                         double*, double*, unsigned*, const Red&, cudaStream_t);              \
+  template cudaError_t proj_update_reserve_smem<T, W>(size_t);
 NS_INST_PROJ(double, 1)
 NS_INST_PROJ(double, 2)
 NS_INST_PROJ(double, 4)
@@ -614,33 +625,28 @@ __global__ void __launch_bounds__(kThreads) k_restart_gemm_fp64(const double* __
 
 
 template <typename T>
-void restart_gemm(const T* Z, int d, int R, const double* VZ, const int* sel, int nsel, int nl, int64_t n, T* Lnew,
-                  T* Znext, cudaStream_t s) {
-  if (nsel == 0 || n == 0) return;
+cudaError_t restart_gemm(const T* Z, int d, int R, const double* VZ, const int* sel, int nsel, int nl, int64_t n,
+                         T* Lnew, T* Znext, cudaStream_t s) {
+  if (nsel == 0 || n == 0) return cudaSuccess;
   const size_t smem64 = sizeof(double) * (size_t)(kGR * R + R * kGC);
   if (sizeof(T) == 8 && smem64 <= 200 * 1024) {  // larger R (> 400) takes the chunked kernel
-    static bool attr64 = false;
-    if (!attr64) {
-      cudaFuncSetAttribute(k_restart_gemm_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      attr64 = true;
-    }
+    const cudaError_t e = ensure_smem_limit(reinterpret_cast<const void*>(k_restart_gemm_fp64), smem64);
+    if (e != cudaSuccess) return e;
     k_restart_gemm_fp64<<<ceil_div(n, kGR), kThreads, smem64, s>>>(reinterpret_cast<const double*>(Z), d, R, VZ, sel,
                                                                    nsel, nl, n, reinterpret_cast<double*>(Lnew),
                                                                    reinterpret_cast<double*>(Znext));
-    return;
+    return cudaSuccess;
   }
   const size_t smem = sizeof(T) * (size_t)kRGJ * (kRGR + kRGC);  // 32 KB
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_restart_gemm<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr_set = true;
-  }
+  const cudaError_t e = ensure_smem_limit(reinterpret_cast<const void*>(k_restart_gemm<T>), smem);
+  if (e != cudaSuccess) return e;
   k_restart_gemm<T><<<ceil_div(n, kRGR), kThreads, smem, s>>>(Z, d, R, VZ, sel, nsel, nl, n, Lnew, Znext);
+  return cudaSuccess;
 }
-template void restart_gemm<double>(const double*, int, int, const double*, const int*, int, int, int64_t, double*,
-                                   double*, cudaStream_t);
-template void restart_gemm<float>(const float*, int, int, const double*, const int*, int, int, int64_t, float*,
-                                  float*, cudaStream_t);
+template cudaError_t restart_gemm<double>(const double*, int, int, const double*, const int*, int, int, int64_t,
+                                          double*, double*, cudaStream_t);
+template cudaError_t restart_gemm<float>(const float*, int, int, const double*, const int*, int, int, int64_t,
+                                         float*, float*, cudaStream_t);
 
 template <typename T>
 __global__ void k_panel_to_cols(const T* P, int64_t ldp, int w, int64_t n, T* X, int c0) {
@@ -733,6 +739,7 @@ __global__ void __launch_bounds__(kThreads) k_step_finalize(OmegaArgs a, int mod
     }
     const double w = g * val;
     cn[b] = w;
+    if (a.trace) a.trace[(size_t)(j + 1) * nbp + b] = w;
     if (!(w <= a.u_ro)) tz = 1;
   }
 #undef WZ

@@ -334,13 +334,8 @@ __global__ void __launch_bounds__(128) k_backtransform(const double* work_c, int
 }
 
 void syev(const double* T, int n, double* theta, double* V, double* work, cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_tridiag, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(sizeof(double) * kEigSmemMaxN * kEigSmemMaxN));
-    attr = true;
-  }
   const size_t smem = (n <= kEigSmemMaxN) ? sizeof(double) * (size_t)n * n : 0;
+  if (ensure_smem_limit(reinterpret_cast<const void*>(k_tridiag), smem) != cudaSuccess) return;  // launch fails; caller checks
   k_tridiag<<<1, kThreads, smem, s>>>(T, n, work);
   k_bisect<<<n, kBisThreads, 0, s>>>(work, n, theta);
   k_inviter<<<n, 32, 0, s>>>(work, n, theta);

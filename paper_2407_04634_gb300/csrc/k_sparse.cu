@@ -389,16 +389,14 @@ __global__ void __launch_bounds__(kThreads) k_spmm_tma(Csr<T> M, const T* __rest
 
 template <typename T, int D, bool LANCZOS>
 static void launch_tma(const Csr<T>& M, const T* v, const StepOps<T>& op, T* y, const Red& red, cudaStream_t s) {
-  static int cap = 0;  // resident CTAs of this instantiation (looked up once)
   const void* fn = reinterpret_cast<const void*>(k_spmm_tma<T, D, LANCZOS>);
-  if (cap == 0) {
-    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma_smem_bytes<T>());
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, tma_smem_bytes<T>());
-    cap = std::max(1, std::min(per_sm, 8)) * std::max(sms, 1);
-  }
+  // the shared-memory limit is a per-device attribute: raised on each device in turn
+  if (ensure_smem_limit(fn, tma_smem_bytes<T>()) != cudaSuccess) return;  // the caller's launch check reports it
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, tma_smem_bytes<T>());
+  const int cap = std::max(1, std::min(per_sm, 8)) * std::max(sms, 1);  // resident CTAs of this instantiation
   const int64_t ntiles = (M.nrows + kTmaRows - 1) / kTmaRows;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, cap));
   k_spmm_tma<T, D, LANCZOS><<<grid, kThreads, tma_smem_bytes<T>(), s>>>(M, v, op, y, red);

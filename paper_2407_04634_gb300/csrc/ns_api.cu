@@ -64,6 +64,11 @@ struct Prof {
   void end(int tok) {
     if (tok >= 0) cudaEventRecord(pend[tok].b, s);
   }
+  // algorithmic work of a launch of class c that is only known after it was enqueued
+  void add(int c, double by, double fl) {
+    bytes[c] += by;
+    flops[c] += fl;
+  }
   void flush() {  // call after the stream was synchronized
     for (auto& p : pend) {
       float t = 0.f;
@@ -223,17 +228,20 @@ struct Prec<float> {
 };
 
 void ensure_fp32(ns_handle* h) {
+  // FP32 copies of A's values (already present when A came in as FP32), A^T's values and D
   if (!h->val32) {
     h->val32 = (float*)dalloc_own(h, sizeof(float) * csr_entries(h->nnz));
     convert_d2f(h->val, h->val32, h->nnz, h->stream);
-    if (h->mode == NS_MODE_NORMAL) {
-      h->val_t32 = (float*)dalloc_own(h, sizeof(float) * csr_entries(h->nnz));
-      convert_d2f(h->val_t, h->val_t32, h->nnz, h->stream);
-    }
+  }
+  if (h->mode == NS_MODE_NORMAL && !h->val_t32) {
+    h->val_t32 = (float*)dalloc_own(h, sizeof(float) * csr_entries(h->nnz));
+    convert_d2f(h->val_t, h->val_t32, h->nnz, h->stream);
+  }
+  if (!h->D32) {
     h->D32 = (float*)dalloc_own(h, sizeof(float) * (size_t)h->n);
     convert_d2f(h->D64, h->D32, h->n, h->stream);
-    ck_launch("fp32 copies");
   }
+  ck_launch("fp32 copies");
 }
 
 template <typename T>
@@ -541,8 +549,9 @@ struct Solver {
     PScope ps(&h->prof, P_PROJ, passes * (2.0 * K * n * sv + 3.0 * n * W * sv), 4.0 * passes * K * n * W);
     for (int pass = 0; pass < passes; ++pass) {
       proj_dots<T, W>(V, Wp, Wp2, ldw, n, cbuf.as<double>(), dpart.as<double>(), s);
-      proj_update<T, W>(V, cbuf.as<double>(), Wp, Wp2, ldw, n, (pass == passes - 1 && gram) ? 1 : 0, Rout, gd,
-                        flags, red, s);
+      ck((proj_update<T, W>(V, cbuf.as<double>(), Wp, Wp2, ldw, n, (pass == passes - 1 && gram) ? 1 : 0, Rout, gd,
+                            flags, red, s)),
+         "proj_update shared-memory limit");
       launches += 3;
     }
   }
@@ -581,6 +590,7 @@ struct Solver {
     a.bd_tol = bd_tol;
     a.flags = flags;
     a.counters = counters;
+    a.trace = trace_dev;
     return a;
   }
 
@@ -672,14 +682,14 @@ struct Solver {
       gram_chol<T, D>(qn, D, D, n, R1, nullptr, flags, red, s);
       cholqr_finish<D>(qn, D, R1, R2);
       launches += 2;
-      if (read_flags() & 1u) throw Fail{NS_ERR_CUDA, "rank loss in reorthogonalization"};
+      if (read_flags() & 1u) throw Fail{NS_ERR_NUMERICAL, "rank loss in reorthogonalization (numerical)"};
     }
   }
 
   void project_parts(T* q, int kx, int nzb) {
     project<D>(q, D, kx, cur, nzb, true, R1, nullptr);
     cholqr_finish<D>(q, D, R1, R2);
-    if (read_flags() & 1u) throw Fail{NS_ERR_CUDA, "rank loss in reorthogonalization"};
+    if (read_flags() & 1u) throw Fail{NS_ERR_NUMERICAL, "rank loss in reorthogonalization (numerical)"};
   }
 
   // lock the new Ritz vectors stored in lnew (row-major, width nl); returns ghosts
@@ -739,6 +749,16 @@ struct Solver {
   }
 
   std::vector<double> pin_theta, pin_res;
+  double* trace_dev = nullptr;  // optional W-column record (ns_trace_omega)
+
+  // first cycle only (start block, then steps 1..nb-1 with their partial
+  // reorthogonalization), for ns_trace_omega
+  void run_first_cycle() {
+    orthonormal_start();
+    first_step(0);
+    for (int j = 1; j < nb; ++j) inner_step(j, 0);
+    sync();
+  }
   bool debug = getenv("NS_DEBUG") != nullptr;
   std::chrono::steady_clock::time_point t_start = std::chrono::steady_clock::now();
 
@@ -775,7 +795,8 @@ struct Solver {
       {
         const double nc = (double)cand.size();
         PScope ps(&h->prof, P_GEMM, (double)n * (R + nc) * sizeof(T), 2.0 * n * R * nc);
-        restart_gemm<T>(Z[cur], D, R, VZ, sel, (int)cand.size(), (int)cand.size(), n, lnew.as<T>(), nullptr, s);
+        ck(restart_gemm<T>(Z[cur], D, R, VZ, sel, (int)cand.size(), (int)cand.size(), n, lnew.as<T>(), nullptr, s),
+           "restart_gemm shared-memory limit");
       }
       launches += 1;
       const int before = nlock;
@@ -817,7 +838,7 @@ struct Solver {
     ck(cudaMemcpyAsync(sel, avail.data(), sizeof(int) * nk, cudaMemcpyHostToDevice, s), "h2d");
     {
       PScope ps(&h->prof, P_GEMM, (double)n * (R + nk) * sizeof(T), 2.0 * n * R * nk);
-      restart_gemm<T>(Z[cur], D, R, VZ, sel, nk, 0, n, nullptr, Z[other], s);
+      ck(restart_gemm<T>(Z[cur], D, R, VZ, sel, nk, 0, n, nullptr, Z[other], s), "restart_gemm shared-memory limit");
     }
     launches += 1;
     // Alg. 2 line 16: Q_{l+1} against [X, Z_new], moved to block nk/D of the new buffer
@@ -905,6 +926,7 @@ struct RefineOut {
   int64_t iters_max = 0;  // largest number of inner iterations over all chunks
   double resid_max = 0.0; // max_j ||A x_j|| / ||A||_2 after refinement (FP64)
   int failed = 0;
+  double bytes = 0.0, flops = 0.0;  // algorithmic work of every kernel enqueued (each operand once)
 };
 
 // Projection of every basis column onto null(A) (Remark after Alg. 1 motivates
@@ -942,6 +964,18 @@ RefineOut refine(ns_handle* h, double* X, int64_t N, double normA, const ns_opts
   ck(cudaMallocHost(&nact_h, 1024), "cudaMallocHost");
   double* rr_h = reinterpret_cast<double*>(nact_h + 8);
   const double tol2 = (o.refine_tol * normA) * (o.refine_tol * normA);
+  // algorithmic bytes / flops of the panel kernels (width W, value size sv)
+  const double nnz = (double)h->nnz;
+  auto spmm_work = [&](double rows, double cols, double sv, bool with_w) {  // y = M v (+ dots)
+    out.bytes += nnz * (4.0 + sv) + (rows + 1.0) * 8.0 + cols * W * sv + rows * W * sv * (with_w ? 2.0 : 1.0);
+    out.flops += 2.0 * nnz * W + 2.0 * rows * W;
+  };
+  auto A_work = [&](double sv, bool with_w) { spmm_work((double)nr, (double)n, sv, with_w); };
+  auto At_work = [&](double sv) { spmm_work((double)n, (double)m, sv, false); };
+  auto stream_work = [&](double rows, double bytes_per, double flops_per) {
+    out.bytes += rows * W * bytes_per;
+    out.flops += rows * W * flops_per;
+  };
   auto read_nact = [&]() {
     ck(cudaMemcpyAsync(nact_h, nact, sizeof(int), cudaMemcpyDeviceToHost, s), "d2h");
     ck(cudaStreamSynchronize(s), "sync");
@@ -950,6 +984,7 @@ RefineOut refine(ns_handle* h, double* X, int64_t N, double normA, const ns_opts
   for (int64_t c0 = 0; c0 < N; c0 += W) {
     const int w = (int)std::min<int64_t>(W, N - c0);
     cols_to_panel_w<W>(X, (int)c0, w, n, bx.as<double>(), s);
+    stream_work((double)n, 16.0, 0.0);
     std::vector<unsigned char> a0(W, 0);
     for (int c = 0; c < w; ++c) a0[c] = 1;
     ck(cudaMemcpyAsync(act_out, a0.data(), W, cudaMemcpyHostToDevice, s), "h2d");
@@ -957,11 +992,13 @@ RefineOut refine(ns_handle* h, double* X, int64_t N, double normA, const ns_opts
     for (int outer = 0; outer < 8; ++outer) {
       // FP64 residual of the current iterate
       spmm_coldot<double, W>(A64, bx.as<double>(), br64.as<double>(), nullptr, 1, rr64, red, s);
+      A_work(8.0, false);
       cg_check(rr64, nullptr, tol2, act_out, nact, W, s);
       h->launches += 2;
       if (read_nact() == 0) break;
       // inner solve in FP32: delta with A delta ~ r (CG) or min ||A delta - r|| (CGLS)
       convert_d2f(br64.as<double>(), br.as<float>(), nr * W, s);
+      stream_work((double)nr, 12.0, 0.0);
       ck(cudaMemsetAsync(bd.p, 0, bd.bytes, s), "memset");
       ck(cudaMemcpyAsync(act, act_out, W, cudaMemcpyDeviceToDevice, s), "copy");
       scale_vec(rr64, kInner * kInner, tin, W, s);
@@ -972,11 +1009,14 @@ RefineOut refine(ns_handle* h, double* X, int64_t N, double normA, const ns_opts
         ck(cudaMemcpyAsync(rr, rr64, sizeof(double) * W, cudaMemcpyDeviceToDevice, s), "copy");
         for (; it < o.refine_maxit; ++it) {
           spmm_coldot<float, W>(A32, bp.as<float>(), bq.as<float>(), nullptr, 0, den, red, s);  // p^T A p
+          A_work(4.0, false);
           cg_scalars(rr, den, act, alpha, W, s);
           cg_update2<float, W>(bd.as<float>(), bp.as<float>(), n, br.as<float>(), bq.as<float>(), n, alpha, red,
                                rrn, s);
+          stream_work(2.0 * n, 12.0, 4.0);
           cg_scalars(rrn, rr, act, beta, W, s);
           cg_direction2<float, W>(bp.as<float>(), br.as<float>(), beta, n, s);
+          stream_work((double)n, 12.0, 2.0);
           ck(cudaMemcpyAsync(rr, rrn, sizeof(double) * W, cudaMemcpyDeviceToDevice, s), "copy");
           cg_check(rr, tin, 0.0, act, nact, W, s);
           h->launches += 6;
@@ -984,16 +1024,21 @@ RefineOut refine(ns_handle* h, double* X, int64_t N, double normA, const ns_opts
         }
       } else {
         spmm_coldot<float, W>(At32, br.as<float>(), bs.as<float>(), nullptr, 1, gam, red, s);  // s = A^T r
+        At_work(4.0);
         ck(cudaMemcpyAsync(bp.p, bs.p, sizeof(float) * n * W, cudaMemcpyDeviceToDevice, s), "copy");
         h->launches += 1;
         for (; it < o.refine_maxit; ++it) {
           spmm_coldot<float, W>(A32, bp.as<float>(), bq.as<float>(), nullptr, 1, den, red, s);  // ||A p||^2
+          A_work(4.0, false);
           cg_scalars(gam, den, act, alpha, W, s);
           cg_update2<float, W>(bd.as<float>(), bp.as<float>(), n, br.as<float>(), bq.as<float>(), m, alpha, red,
                                rr, s);
+          stream_work((double)(n + m), 12.0, 4.0);
           spmm_coldot<float, W>(At32, br.as<float>(), bs.as<float>(), nullptr, 1, rrn, red, s);  // ||A^T r||^2
+          At_work(4.0);
           cg_scalars(rrn, gam, act, beta, W, s);
           cg_direction2<float, W>(bp.as<float>(), bs.as<float>(), beta, n, s);
+          stream_work((double)n, 12.0, 2.0);
           ck(cudaMemcpyAsync(gam, rrn, sizeof(double) * W, cudaMemcpyDeviceToDevice, s), "copy");
           cg_check(rr, tin, 0.0, act, nact, W, s);
           h->launches += 7;
@@ -1002,11 +1047,14 @@ RefineOut refine(ns_handle* h, double* X, int64_t N, double normA, const ns_opts
       }
       out.iters_max = std::max<int64_t>(out.iters_max, it + 1);
       sub_correction<W>(bx.as<double>(), bd.as<float>(), n, s);  // x <- x - delta in FP64
+      stream_work((double)n, 20.0, 1.0);
       h->launches += 1;
     }
     // final FP64 residual for the statistics
     spmm_coldot<double, W>(A64, bx.as<double>(), br64.as<double>(), nullptr, 1, rr64, red, s);
+    A_work(8.0, false);
     panel_to_cols64<W>(bx.as<double>(), X, (int)c0, w, n, s);
+    stream_work((double)n, 16.0, 0.0);
     ck(cudaMemcpyAsync(rr_h, rr64, sizeof(double) * W, cudaMemcpyDeviceToHost, s), "d2h");
     ck(cudaStreamSynchronize(s), "sync");
     ck_launch("refine");
@@ -1057,6 +1105,7 @@ static ns_status solve_typed(ns_handle* h, int R, double tol, const ns_opts& o) 
       PScope ps(&h->prof, P_REFINE, 0.0, 0.0);
       ro = refine(h, h->basis, N, normA, o);
     }
+    h->prof.add(P_REFINE, ro.bytes, ro.flops);  // one "launch" = the whole refinement phase
     ck(cudaStreamSynchronize(s), "sync");
     h->prof.flush();
     if (ro.failed && st == NS_OK) st = NS_ERR_REFINE;
@@ -1135,6 +1184,19 @@ static ns_status solve_typed(ns_handle* h, int R, double tol, const ns_opts& o) 
 }
 
 template <typename T, int D>
+static void trace_omega_typed(ns_handle* h, int R, const ns_opts& o, double* W) {
+  const int nbp = R / D + 1;
+  Buf tr(h, sizeof(double) * (size_t)nbp * nbp);
+  ck(cudaMemsetAsync(tr.p, 0, tr.bytes, h->stream), "memset");
+  h->prof.reset(0, h->stream);
+  Solver<T, D> S(h, R, 1.0, o);
+  S.trace_dev = tr.as<double>();
+  S.run_first_cycle();
+  ck(cudaMemcpyAsync(W, tr.p, tr.bytes, cudaMemcpyDeviceToHost, h->stream), "d2h trace");
+  ck(cudaStreamSynchronize(h->stream), "sync");
+}
+
+template <typename T, int D>
 static void apply_B_typed(ns_handle* h, const T* x, T* y, double eps, Red red, int schedule) {
   StepOps<T> op;
   op.x = x;
@@ -1188,9 +1250,10 @@ static void project_typed(ns_handle* h, int64_t n, int K, const double* V, doubl
   P.kz = 0;
   P.p = 1;
   proj_dots<T, W>(P, wp, nullptr, W, n, cb.as<double>(), part.as<double>(), nullptr);
-  proj_update<T, W>(P, cb.as<double>(), wp, nullptr, W, n, 0, nullptr, nullptr, nullptr, red, nullptr);
+  ck((proj_update<T, W>(P, cb.as<double>(), wp, nullptr, W, n, 0, nullptr, nullptr, nullptr, red, nullptr)), "limit");
   proj_dots<T, W>(P, wp, nullptr, W, n, cb2.as<double>(), part.as<double>(), nullptr);
-  proj_update<T, W>(P, cb2.as<double>(), wp, nullptr, W, n, 0, nullptr, nullptr, nullptr, red, nullptr);
+  ck((proj_update<T, W>(P, cb2.as<double>(), wp, nullptr, W, n, 0, nullptr, nullptr, nullptr, red, nullptr)),
+     "limit");
   ck_launch("project");
   ck(cudaDeviceSynchronize(), "sync");
   if (!std::is_same<T, double>::value) convert_f2d(wb.as<float>(), w64.as<double>(), n * W, nullptr);
@@ -1230,12 +1293,17 @@ static ns_status set_err(ns_handle* h, ns_status st, const std::string& msg) {
 }
 
 ns_status ns_create(ns_handle** out, int64_t m, int64_t n, const int64_t* rowptr, const int32_t* colind,
-                    const double* vals, int inputs_on_device, uint64_t seed, int mode, const ns_env* env) {
+                    const void* vals, int vals_is_fp32, int inputs_on_device, uint64_t seed, int mode,
+                    const ns_env* env) {
   if (!out) return NS_ERR_INVALID_ARG;
   *out = nullptr;
   if (m < 0 || n <= 0 || !rowptr || (mode != NS_MODE_NORMAL && mode != NS_MODE_SPD)) return NS_ERR_INVALID_ARG;
+  if (vals_is_fp32 != 0 && vals_is_fp32 != 1) return NS_ERR_INVALID_ARG;
   if (mode == NS_MODE_SPD && m != n) return NS_ERR_INVALID_ARG;
   if (n > (int64_t)INT32_MAX || m > (int64_t)INT32_MAX) return NS_ERR_INVALID_ARG;
+  const double* vals64 = static_cast<const double*>(vals);
+  const float* vals32 = static_cast<const float*>(vals);
+  auto value_at = [&](int64_t k) { return vals_is_fp32 ? (double)vals32[k] : vals64[k]; };
   if (!inputs_on_device) {  // host inputs are validated before any device work
     if (rowptr[0] != 0) return NS_ERR_INVALID_ARG;
     for (int64_t r = 0; r < m; ++r)
@@ -1243,7 +1311,7 @@ ns_status ns_create(ns_handle** out, int64_t m, int64_t n, const int64_t* rowptr
     const int64_t nz = rowptr[m];
     if (nz > 0 && (!colind || !vals)) return NS_ERR_INVALID_ARG;
     for (int64_t k = 0; k < nz; ++k)
-      if (colind[k] < 0 || (int64_t)colind[k] >= n || !std::isfinite(vals[k])) return NS_ERR_INVALID_ARG;
+      if (colind[k] < 0 || (int64_t)colind[k] >= n || !std::isfinite(value_at(k))) return NS_ERR_INVALID_ARG;
   }
   int dev = 0, ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
@@ -1274,7 +1342,7 @@ ns_status ns_create(ns_handle** out, int64_t m, int64_t n, const int64_t* rowptr
       if (nnz > (int64_t)INT32_MAX * 2) throw Fail{NS_ERR_INVALID_ARG, "nnz too large"};
       for (int64_t k = 0; k < nnz; ++k) {
         if (colind[k] < 0 || (int64_t)colind[k] >= n) throw Fail{NS_ERR_INVALID_ARG, "column index out of range"};
-        if (!std::isfinite(vals[k])) throw Fail{NS_ERR_INVALID_ARG, "non-finite value"};
+        if (!std::isfinite(value_at(k))) throw Fail{NS_ERR_INVALID_ARG, "non-finite value"};
       }
       for (int64_t r = 0; r < m; ++r) h->maxrow_A = std::max(h->maxrow_A, rowptr[r + 1] - rowptr[r]);
     } else {
@@ -1291,9 +1359,22 @@ ns_status ns_create(ns_handle** out, int64_t m, int64_t n, const int64_t* rowptr
     h->col = (int*)dalloc_own(h, sizeof(int) * csr_entries(nnz));
     h->val = (double*)dalloc_own(h, sizeof(double) * csr_entries(nnz));
     ck(cudaMemcpyAsync(h->rowptr, rowptr, sizeof(int64_t) * (m + 1), kind, s), "copy rowptr");
+    if (vals_is_fp32) {
+      // FP32 values are kept as given (the mixed path's copy) and widened exactly on the
+      // device for the FP64 path, the transpose and the refinement
+      h->val32 = (float*)dalloc_own(h, sizeof(float) * csr_entries(nnz));
+      ck(cudaMemsetAsync(h->val32, 0, sizeof(float) * csr_entries(nnz), s), "memset");
+    }
+    ck(cudaMemsetAsync(h->val, 0, sizeof(double) * csr_entries(nnz), s), "memset");
     if (nnz) {
       ck(cudaMemcpyAsync(h->col, colind, sizeof(int) * nnz, kind, s), "copy colind");
-      ck(cudaMemcpyAsync(h->val, vals, sizeof(double) * nnz, kind, s), "copy vals");
+      if (vals_is_fp32) {
+        ck(cudaMemcpyAsync(h->val32, vals, sizeof(float) * nnz, kind, s), "copy vals");
+        convert_f2d(h->val32, h->val, nnz, s);
+        ck_launch("widen vals");
+      } else {
+        ck(cudaMemcpyAsync(h->val, vals, sizeof(double) * nnz, kind, s), "copy vals");
+      }
     }
     Buf small(h, 4096);
     Red red;
@@ -1537,6 +1618,40 @@ ns_status ns_apply_B(ns_handle* h, int d, const double* X, double* Y, double eps
     ck(cudaStreamSynchronize(h->stream), "sync");
     if (spmm_wait_timeouts(true)) throw Fail{NS_ERR_TIMEOUT, "a bounded device wait of the SpMM expired"};
   } catch (const Fail& f) {
+    return set_err(h, f.st, f.msg);
+  }
+  return NS_OK;
+}
+
+ns_status ns_trace_omega(ns_handle* h, int d, int restart_len, const ns_opts* opts, double* W) {
+  if (!h || !W) return NS_ERR_INVALID_ARG;
+  if (!(d == 1 || d == 2 || d == 4 || d == 8)) return set_err(h, NS_ERR_INVALID_ARG, "d must be 1, 2, 4 or 8");
+  if (restart_len % d || restart_len < 3 * d || restart_len > 512)
+    return set_err(h, NS_ERR_INVALID_ARG, "restart_len must be a multiple of d in [3d, 512]");
+  ns_opts o;
+  ns_default_opts(&o);
+  if (opts) o = *opts;
+  if (!(o.eps >= 0.0)) return set_err(h, NS_ERR_INVALID_ARG, "bad opts");
+  try {
+    if (o.precision == NS_MIXED) {
+      ensure_fp32(h);
+      switch (d) {
+        case 1: trace_omega_typed<float, 1>(h, restart_len, o, W); break;
+        case 2: trace_omega_typed<float, 2>(h, restart_len, o, W); break;
+        case 4: trace_omega_typed<float, 4>(h, restart_len, o, W); break;
+        default: trace_omega_typed<float, 8>(h, restart_len, o, W); break;
+      }
+    } else {
+      switch (d) {
+        case 1: trace_omega_typed<double, 1>(h, restart_len, o, W); break;
+        case 2: trace_omega_typed<double, 2>(h, restart_len, o, W); break;
+        case 4: trace_omega_typed<double, 4>(h, restart_len, o, W); break;
+        default: trace_omega_typed<double, 8>(h, restart_len, o, W); break;
+      }
+    }
+    if (spmm_wait_timeouts(true)) throw Fail{NS_ERR_TIMEOUT, "a bounded device wait of the SpMM expired"};
+  } catch (const Fail& f) {
+    cudaGetLastError();
     return set_err(h, f.st, f.msg);
   }
   return NS_OK;

@@ -145,10 +145,12 @@ TuneKey tune_key(const ns_batch* h, int dev, int block, int R) {
 extern "C" {
 
 ns_status ns_batch_create(ns_batch** out, int64_t count, const int64_t* n, const int64_t* rowptr,
-                          const int32_t* colind, const double* vals, uint64_t seed, const ns_env* env) {
+                          const int32_t* colind, const void* vals, int vals_is_fp32, uint64_t seed,
+                          const ns_env* env) {
   if (!out) return NS_ERR_INVALID_ARG;
   *out = nullptr;
   if (count < 1 || count > (int64_t)0x7fffffff || !n || !rowptr) return NS_ERR_INVALID_ARG;
+  if (vals_is_fp32 != 0 && vals_is_fp32 != 1) return NS_ERR_INVALID_ARG;
   // host-side structure checks (nothing is allocated before they pass)
   std::vector<int64_t> nnz(count), rp_off(count), nz_off(count), out_off(count);
   int64_t rp_tot = 0, nz_tot = 0, nmax = 0, basis_tot = 0;
@@ -198,9 +200,15 @@ ns_status ns_batch_create(ns_batch** out, int64_t count, const int64_t* n, const
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return nnz[a] + n[a] > nnz[b] + n[b]; });
     h->rowptr = bput(h, rowptr, (size_t)rp_tot);
     h->col = bput(h, reinterpret_cast<const int*>(colind), (size_t)nz_tot);
-    h->val64 = bput(h, vals, (size_t)nz_tot);
-    h->val = static_cast<float*>(balloc(h, sizeof(float) * (size_t)std::max<int64_t>(nz_tot, 1)));
-    ns::convert_d2f(h->val64, h->val, nz_tot, h->stream);
+    if (vals_is_fp32) {  // FP32 values as given; an exact FP64 widening for the refinement
+      h->val = bput(h, static_cast<const float*>(vals), (size_t)nz_tot);
+      h->val64 = static_cast<double*>(balloc(h, sizeof(double) * (size_t)std::max<int64_t>(nz_tot, 1)));
+      ns::convert_f2d(h->val, h->val64, nz_tot, h->stream);
+    } else {
+      h->val64 = bput(h, static_cast<const double*>(vals), (size_t)nz_tot);
+      h->val = static_cast<float*>(balloc(h, sizeof(float) * (size_t)std::max<int64_t>(nz_tot, 1)));
+      ns::convert_d2f(h->val64, h->val, nz_tot, h->stream);
+    }
     h->rp_off = bput(h, rp_off.data(), (size_t)count);
     h->nz_off = bput(h, nz_off.data(), (size_t)count);
     h->out_off = bput(h, out_off.data(), (size_t)count);

@@ -5,6 +5,9 @@
 #include <stdint.h>
 
 #include <cmath>
+#include <map>
+#include <mutex>
+#include <utility>
 
 namespace ns {
 
@@ -300,5 +303,24 @@ __device__ __forceinline__ void store_row(T* p, const T (&v)[D]) {
 }
 
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// Raises the dynamic shared-memory limit of kernel `fn` to at least `bytes` on the
+// current device.  The attribute belongs to the (function, device) pair, so it is
+// tracked per device; calls from several host threads are serialized.  Returns
+// the status of cudaFuncSetAttribute (cudaSuccess when nothing had to change).
+inline cudaError_t ensure_smem_limit(const void* fn, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, size_t> raised;
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& have = raised[std::make_pair(fn, dev)];
+  if (have >= bytes) return cudaSuccess;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) have = bytes;
+  return e;
+}
 
 }  // namespace ns

@@ -114,14 +114,19 @@ template <typename T, int W>
 void proj_dots(const VParts<T>& V, const T* Wp, const T* Wp2, int64_t ldw, int64_t n, double* C, double* part,
                cudaStream_t s);
 // W -= V C ; if gram: G = W^T W partials, last block chol -> R (+gdiag)
+// (returns the status of raising the kernel's shared-memory limit on this device;
+// the launch itself is checked by the caller)
 template <typename T, int W>
-void proj_update(const VParts<T>& V, const double* C, T* Wp, T* Wp2, int64_t ldw, int64_t n, int gram, double* R,
-                 double* gdiag, unsigned* flags, const Red& red, cudaStream_t s);
+cudaError_t proj_update(const VParts<T>& V, const double* C, T* Wp, T* Wp2, int64_t ldw, int64_t n, int gram,
+                        double* R, double* gdiag, unsigned* flags, const Red& red, cudaStream_t s);
+// raise the shared-memory limit of the P = 1 update kernels to `bytes` ahead of time
+template <typename T, int W>
+cudaError_t proj_update_reserve_smem(size_t bytes);
 
 // restart GEMM: out_c = Z V_Z(:, sel_c), c < nl -> Lnew (row-major, width nl), else Znext panel (width d)
 template <typename T>
-void restart_gemm(const T* Z, int d, int R, const double* VZ, const int* sel, int nsel, int nl, int64_t n,
-                  T* Lnew, T* Znext, cudaStream_t s);
+cudaError_t restart_gemm(const T* Z, int d, int R, const double* VZ, const int* sel, int nsel, int nl, int64_t n,
+                         T* Lnew, T* Znext, cudaStream_t s);
 // copy w columns of a row-major panel (ld) into column-major X (ld n) starting at column c0
 template <typename T>
 void panel_to_cols(const T* P, int64_t ldp, int w, int64_t n, T* X, int c0, cudaStream_t s);
@@ -149,6 +154,8 @@ struct OmegaArgs {
   double bd_tol;
   unsigned* flags;       // bit 1 breakdown, bit 2 reorth Z, bit 4 reorth X
   long long* counters;   // [0] reorth_Z, [1] reorth_X, [2] breakdowns
+  double* trace = nullptr;  // optional record, (nb+1) x (nb+1) column-major: column j+1
+                            // of W as the recurrence produced it, before any reset
 };
 void step_finalize(const OmegaArgs& a, cudaStream_t s);
 // Gamma and its norms only (first step of a cycle)

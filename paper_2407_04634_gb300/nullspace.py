@@ -16,9 +16,9 @@ import numpy as np
 from . import build as _build
 
 NS_OK, NS_ERR_INVALID_ARG, NS_ERR_OOM, NS_ERR_CUDA, NS_ERR_NOT_CONVERGED, NS_ERR_TIMEOUT, NS_ERR_STATE, \
-    NS_ERR_REFINE = range(8)
+    NS_ERR_REFINE, NS_ERR_NUMERICAL = range(9)
 STATUS = {0: "NS_OK", 1: "NS_ERR_INVALID_ARG", 2: "NS_ERR_OOM", 3: "NS_ERR_CUDA", 4: "NS_ERR_NOT_CONVERGED",
-          5: "NS_ERR_TIMEOUT", 6: "NS_ERR_STATE", 7: "NS_ERR_REFINE"}
+          5: "NS_ERR_TIMEOUT", 6: "NS_ERR_STATE", 7: "NS_ERR_REFINE", 8: "NS_ERR_NUMERICAL"}
 MODE = {"normal": 0, "spd": 1}
 PRECISION = {"fp64": 0, "mixed": 1}
 REORTH = {"partial": 0, "full": 1}
@@ -70,8 +70,8 @@ class NsKernelProf(C.Structure):
 _P = C.c_void_p
 SIGNATURES = {
     "ns_default_opts": (None, [C.POINTER(NsOpts)]),
-    "ns_create": (C.c_int, [C.POINTER(_P), C.c_int64, C.c_int64, _P, _P, _P, C.c_int, C.c_uint64, C.c_int,
-                            C.POINTER(NsEnv)]),
+    "ns_create": (C.c_int, [C.POINTER(_P), C.c_int64, C.c_int64, _P, _P, _P, C.c_int, C.c_int, C.c_uint64,
+                            C.c_int, C.POINTER(NsEnv)]),
     "ns_solve": (C.c_int, [_P, C.c_int, C.c_int, C.c_double, C.POINTER(NsOpts)]),
     "ns_nullity": (C.c_int, [_P, C.POINTER(C.c_int64)]),
     "ns_basis": (C.c_int, [_P, _P, C.c_int64, C.c_int]),
@@ -83,10 +83,13 @@ SIGNATURES = {
     "ns_get_perturbation": (C.c_int, [_P, _P]),
     "ns_start_block": (C.c_int, [_P, C.c_int, _P]),
     "ns_apply_B": (C.c_int, [_P, C.c_int, _P, _P, C.c_double, C.c_int, C.c_int, C.c_int]),
+    "ns_trace_omega": (C.c_int, [_P, C.c_int, C.c_int, C.POINTER(NsOpts), _P]),
     "ns_syev": (C.c_int, [C.c_int, _P, _P, _P]),
+    "ns_fma_peak": (C.c_int, [C.c_int, C.POINTER(C.c_double)]),
     "ns_project": (C.c_int, [C.c_int64, C.c_int, C.c_int, _P, _P, _P, C.c_int]),
     "ns_project_noalloc": (C.c_int, [C.c_int64, C.c_int, C.c_int, _P, _P, _P, _P]),
-    "ns_batch_create": (C.c_int, [C.POINTER(_P), C.c_int64, _P, _P, _P, _P, C.c_uint64, C.POINTER(NsEnv)]),
+    "ns_batch_create": (C.c_int, [C.POINTER(_P), C.c_int64, _P, _P, _P, _P, C.c_int, C.c_uint64,
+                                  C.POINTER(NsEnv)]),
     "ns_batch_solve": (C.c_int, [_P, C.c_int, C.c_int, C.c_double, C.POINTER(NsOpts)]),
     "ns_batch_results": (C.c_int, [_P, _P, _P, _P]),
     "ns_batch_basis": (C.c_int, [_P, C.c_int64, _P, C.c_int64, C.c_int]),
@@ -178,14 +181,17 @@ class Handle:
         self._env = torch_env() if env == "torch" else None
         on_dev = 0
         if hasattr(rowptr, "data_ptr"):  # torch tensors on the device
+            import torch
             on_dev = 1
+            fp32 = int(vals.dtype == torch.float32)
             ptrs = [C.c_void_p(t.data_ptr()) for t in (rowptr, colind, vals)]
         else:
+            fp32 = int(np.asarray(vals).dtype == np.float32)  # FP32 values go in as they are
             self._keep = (np.ascontiguousarray(rowptr, dtype=np.int64), np.ascontiguousarray(colind, dtype=np.int32),
-                          np.ascontiguousarray(vals, dtype=np.float64))
+                          np.ascontiguousarray(vals, dtype=np.float32 if fp32 else np.float64))
             ptrs = [_ptr(a) for a in self._keep]
         h = C.c_void_p()
-        st = self.lib.ns_create(C.byref(h), self.m, self.n, *ptrs, on_dev, C.c_uint64(seed), MODE[mode],
+        st = self.lib.ns_create(C.byref(h), self.m, self.n, *ptrs, fp32, on_dev, C.c_uint64(seed), MODE[mode],
                                 C.byref(self._env) if self._env is not None else None)
         if st != NS_OK:
             raise NullspaceError(st, "ns_create failed")
@@ -263,6 +269,15 @@ class Handle:
                                         int(schedule)), "ns_apply_B")
         return Y
 
+    def trace_omega(self, d: int, restart_len: int, **opts) -> np.ndarray:
+        """W columns of the first cycle ((nb+1) x (nb+1), entry [b, c] = w_{b,c} before any reset)."""
+        nbp = restart_len // d + 1
+        W = np.zeros((nbp, nbp), order="F")
+        o = default_opts(**opts)
+        self._check(self.lib.ns_trace_omega(self.h, int(d), int(restart_len), C.byref(o),
+                                            C.c_void_p(W.ctypes.data)), "ns_trace_omega")
+        return W
+
     def close(self):
         if getattr(self, "h", None):
             self.lib.ns_destroy(self.h)
@@ -273,6 +288,16 @@ class Handle:
             self.close()
         except Exception:
             pass
+
+
+def fma_peak(precision: str = "fp64") -> float:
+    """Measured FMA throughput (TFLOP/s) of the current device's FP64 or FP32 pipe."""
+    lib = load()
+    v = C.c_double()
+    st = lib.ns_fma_peak(PRECISION[precision], C.byref(v))
+    if st != NS_OK:
+        raise NullspaceError(st, "ns_fma_peak")
+    return float(v.value)
 
 
 def syev(T: np.ndarray):
@@ -322,8 +347,10 @@ class Batch:
             rp, ci, va = (M.rowptr, M.colind, M.vals) if hasattr(M, "rowptr") else M
             rps.append(np.asarray(rp, dtype=np.int64))
             cis.append(np.asarray(ci, dtype=np.int32))
-            vas.append(np.asarray(va, dtype=np.float64))
+            vas.append(np.asarray(va))
             ns_.append(len(rp) - 1)
+        if not all(v.dtype == np.float32 for v in vas):
+            vas = [v.astype(np.float64) for v in vas]
         self._create(np.asarray(ns_, dtype=np.int64), np.concatenate(rps), np.concatenate(cis),
                      np.concatenate(vas), seed, env)
 
@@ -338,12 +365,14 @@ class Batch:
     def _create(self, n, rowptr, colind, vals, seed, env):
         self.count = len(n)
         self.n = n
+        fp32 = int(np.asarray(vals).dtype == np.float32)  # FP32 values go in as they are
         self._keep = (np.ascontiguousarray(n, dtype=np.int64), np.ascontiguousarray(rowptr, dtype=np.int64),
-                      np.ascontiguousarray(colind, dtype=np.int32), np.ascontiguousarray(vals, dtype=np.float64))
+                      np.ascontiguousarray(colind, dtype=np.int32),
+                      np.ascontiguousarray(vals, dtype=np.float32 if fp32 else np.float64))
         self._env = torch_env() if env == "torch" else None
         h = C.c_void_p()
-        st = self.lib.ns_batch_create(C.byref(h), self.count, *[_ptr(a) for a in self._keep], C.c_uint64(seed),
-                                      C.byref(self._env) if self._env is not None else None)
+        st = self.lib.ns_batch_create(C.byref(h), self.count, *[_ptr(a) for a in self._keep], fp32,
+                                      C.c_uint64(seed), C.byref(self._env) if self._env is not None else None)
         if st != NS_OK:
             raise NullspaceError(st, "ns_batch_create failed")
         self.h = h

@@ -44,21 +44,26 @@ def test_create_rejects_bad_arguments_or_missing_gpu(lib):
     ci = np.array([0, 0, 5], dtype=np.int32)  # 5 is out of range for n = 2
     va = np.ones(3)
     P = lambda a: ctypes.c_void_p(a.ctypes.data)  # noqa: E731
-    st = lib.ns_create(ctypes.byref(h), 2, 2, P(rp), P(ci), P(va), 0, 1, 0, None)
+    st = lib.ns_create(ctypes.byref(h), 2, 2, P(rp), P(ci), P(va), 0, 0, 1, 0, None)
     assert st == ns.NS_ERR_INVALID_ARG
     rp_bad = np.array([0, 2, 1], dtype=np.int64)
-    st = lib.ns_create(ctypes.byref(h), 2, 2, P(rp_bad), P(ci), P(va), 0, 1, 0, None)
+    st = lib.ns_create(ctypes.byref(h), 2, 2, P(rp_bad), P(ci), P(va), 0, 0, 1, 0, None)
     assert st == ns.NS_ERR_INVALID_ARG
     va_nan = np.array([1.0, np.nan, 1.0])
     ci_ok = np.array([0, 0, 1], dtype=np.int32)
-    st = lib.ns_create(ctypes.byref(h), 2, 2, P(rp), P(ci_ok), P(va_nan), 0, 1, 0, None)
+    st = lib.ns_create(ctypes.byref(h), 2, 2, P(rp), P(ci_ok), P(va_nan), 0, 0, 1, 0, None)
     assert st == ns.NS_ERR_INVALID_ARG
-    st = lib.ns_create(ctypes.byref(h), 3, 2, P(np.array([0, 1, 2, 3], dtype=np.int64)), P(ci_ok), P(va), 0, 1,
-                       1, None)
+    st = lib.ns_create(ctypes.byref(h), 3, 2, P(np.array([0, 1, 2, 3], dtype=np.int64)), P(ci_ok), P(va), 0, 0,
+                       1, 1, None)
     assert st == ns.NS_ERR_INVALID_ARG  # spd mode needs a square matrix
+    va32_nan = np.array([1.0, np.inf, 1.0], dtype=np.float32)
+    st = lib.ns_create(ctypes.byref(h), 2, 2, P(rp), P(ci_ok), P(va32_nan), 1, 0, 1, 0, None)
+    assert st == ns.NS_ERR_INVALID_ARG  # FP32 values are checked as FP32
+    st = lib.ns_create(ctypes.byref(h), 2, 2, P(rp), P(ci_ok), P(va), 2, 0, 1, 0, None)
+    assert st == ns.NS_ERR_INVALID_ARG  # the value-type flag is 0 or 1
     import torch
     if not torch.cuda.is_available():
-        st = lib.ns_create(ctypes.byref(h), 2, 2, P(rp), P(ci_ok), P(va), 0, 1, 0, None)
+        st = lib.ns_create(ctypes.byref(h), 2, 2, P(rp), P(ci_ok), P(va), 0, 0, 1, 0, None)
         assert st == ns.NS_ERR_CUDA
 
 

@@ -33,3 +33,21 @@ def test_closed_form_sine_copy_pairs():
     r = lanczos_nullspace(w.A.to_scipy(), "normal", 2, 60, tol=1e-10, seed=3)
     U = copy_pair_basis(3000, w.copy_pairs)
     assert bench.closed_form_sine(w, torch.as_tensor(r.X)) == pytest.approx(principal_sine(U, r.X), rel=1e-6)
+
+
+def test_independent_residual_and_norm_estimate():
+    """The bench's residual check (sparse product + power-iteration ||A||_2), on CPU
+    tensors: ||A||_2 from 150 power steps never exceeds the dense 2-norm and lies
+    within 1e-3 of it (an underestimate only makes the residual ratio larger) for a small Laplacian and a rectangular matrix, and ||A X||_F / ||A||_2
+    matches the dense computation."""
+    import scipy.sparse as sp
+    for w in (laplacian_cycle_components(21, 400, 3, 8, "powerlaw", 50), rectangular_copies(23, 450, 300, 4)):
+        A = w.A.to_scipy()
+        Ad = bench.device_csr(A, device="cpu")
+        AdT = bench.device_csr(A.T.tocsr(), device="cpu") if w.mode == "normal" else None
+        ref = float(np.linalg.norm(A.toarray(), 2))
+        est = bench.norm2_power(Ad, AdT)
+        assert ref * (1 - 1e-3) <= est <= ref * (1 + 1e-12)
+        X = np.random.default_rng(0).standard_normal((A.shape[1], 5))
+        r = bench.residual_ratio(Ad, torch.from_numpy(X), ref, chunk=2)
+        assert abs(r - np.linalg.norm(A @ X) / ref) <= 1e-12 * r

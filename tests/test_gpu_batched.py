@@ -180,3 +180,21 @@ def test_full_size_4096_laplacians(ns):
         w = ws[i]
         X = b.basis(i)
         assert np.linalg.norm(w.A.to_scipy() @ X) / norm2_A(w.A.to_scipy(), "spd") <= 1e-8
+
+
+def test_fp32_values_give_bit_identical_batch(ns):
+    """ns_batch_create with vals_is_fp32 = 1 (the Laplacians' values are FP32 numbers):
+    the same per-instance results and bit-identical bases as the FP64 input, since the
+    batched form's FP32 copy and FP64 widening are both exact."""
+    ws = batched_laplacians(config_seed(5) + 18, 5, n_min=200, n_max=800)
+    b64 = ns.Batch([w.A for w in ws], 606)
+    b32 = ns.Batch([(w.A.rowptr, w.A.colind, w.A.vals.astype(np.float32)) for w in ws], 606)
+    b64.solve(R, TOL, eps=EPS)
+    b32.solve(R, TOL, eps=EPS)
+    N64, S64, _ = b64.results()
+    N32, S32, _ = b32.results()
+    assert list(S32) == [0] * len(ws) and list(N32) == list(N64) == [w.nullity for w in ws]
+    if (b64.stats()["lanes"], b64.stats()["block"]) == (b32.stats()["lanes"], b32.stats()["block"]):
+        np.testing.assert_array_equal(b32.basis_packed(), b64.basis_packed())
+    for i, w in enumerate(ws):
+        check_instance(ns, b32, i, w)

@@ -302,3 +302,71 @@ def test_config2_full_size_closed_form(ns, precision):
     assert principal_sine(U, X) <= (1e-6 if precision == "fp64" else 1e-5)
     A = w.A.to_scipy()
     assert np.linalg.norm(A @ X) / r.stats["normA"] <= 1e-8
+
+
+# ------------------------------------------------ W recurrence (Sec. 4.2) ---
+
+@pytest.mark.parametrize("d", [1, 2])
+def test_omega_columns_match_oracle(ns, d):
+    """Every W column of the first cycle (configuration 1, n = 2000, restart 60), as the
+    CUDA recurrence produced it, against the oracle's recorded columns element by
+    element.  The cycle triggers partial reorthogonalization several times, so the
+    columns after each reset to u_d are covered too."""
+    w, _ = make_config(1)
+    R = 60
+    ref = lanczos_nullspace(w.A.to_scipy(), w.mode, d, R, tol=1e-10, seed=1000, restart=False, record=True)
+    h = handle(ns, w, 1000)
+    Wg = h.trace_omega(d, R)
+    nb = R // d
+    assert Wg.shape == (nb + 1, nb + 1)
+    rec = ref["Wrec"]
+    assert len(rec) == nb - 1
+    triggers = 0
+    for col, newcol, newX in rec:
+        np.testing.assert_allclose(Wg[:col, col], newcol[:col], rtol=1e-9, atol=0)
+        assert np.all(Wg[col:, col] == 0)
+        triggers += bool((newcol[:col] > ref.u_ro).any())
+    assert np.all(Wg[:, :2] == 0)
+    assert triggers >= 3
+
+
+# ------------------------------------------------------ FP32 value input ----
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_fp32_values_give_the_same_solve(ns, precision):
+    """ns_create with vals_is_fp32 = 1 on the configuration-4 twin (whose values are FP32
+    numbers): the device holds the same FP32 and FP64 values as for the FP64 input (the
+    copy and the widening are exact; checked on the transpose), and the solve gives the
+    same nullity and the same null space.  The bases need not be bit-identical: each
+    handle autotunes its SpMM schedule by timing, which may change summation orders."""
+    w = rectangular_copies(23, 4500, 3000, 6)
+    A = w.A
+    h64 = ns.Handle(A.rowptr, A.colind, A.vals, A.m, A.n, 2000, w.mode)
+    h32 = ns.Handle(A.rowptr, A.colind, A.vals.astype(np.float32), A.m, A.n, 2000, w.mode)
+    r64 = h64.solve(2, 60, 1e-10, precision=precision)
+    r32 = h32.solve(2, 60, 1e-10, precision=precision)
+    assert r64.nullity == r32.nullity == w.nullity
+    X64, X32 = h64.basis(), h32.basis()
+    bar = 1e-5 if precision == "mixed" else 1e-6
+    U = copy_pair_basis(3000, w.copy_pairs)
+    assert principal_sine(U, X32) <= bar and principal_sine(U, X64) <= bar
+    assert principal_sine(X64, X32) <= bar
+    check_solution(w, X32, w.nullity, U, bar)
+    rp, ci, va = h32.transpose(A.nnz)
+    At = A.to_scipy().T.tocsr()
+    At.sort_indices()
+    np.testing.assert_array_equal(va, At.data)
+
+
+def test_fp32_values_from_device_memory(ns):
+    """FP32 values handed over in device memory (inputs_on_device = 1)."""
+    import torch
+    w = laplacian_cycle_components(21, 30000, 15, 8, "powerlaw", 50)
+    A = w.A
+    rp = torch.as_tensor(A.rowptr, device="cuda")
+    ci = torch.as_tensor(A.colind, device="cuda")
+    va = torch.as_tensor(A.vals.astype(np.float32), device="cuda")
+    h = ns.Handle(rp, ci, va, A.m, A.n, 1001, w.mode)
+    r = h.solve(1, 120, 1e-10, precision="mixed")
+    assert r.nullity == 15
+    check_solution(w, h.basis(), 15, indicator_basis(w.labels), 1e-5)

@@ -312,3 +312,24 @@ def test_generators_match_planted_structure():
     assert np.abs(w.A.to_scipy() @ copy_pair_basis(2000, w.copy_pairs)).max() == 0.0
     cols = np.bincount(w.A.colind, minlength=2000)
     assert cols.min() >= 8
+
+
+@pytest.mark.parametrize("theta", [1e-9, 1e-6, 1e-3, 0.3, 1.2])
+def test_principal_sine_of_a_known_rotation(theta):
+    """Principal angles (Def. defPA): rotating one basis vector of span(U) by theta
+    towards a vector orthogonal to span(U) gives a largest principal angle of exactly
+    theta, so principal_sine must return sin(theta) (both branches: the residual norm
+    at small angles, the cosine at large ones), independently of the basis chosen for
+    span(X) and of the other, unrotated columns."""
+    from oracle import principal_sine
+    rng = np.random.default_rng(7)
+    n, k = 500, 6
+    Q, _ = np.linalg.qr(rng.standard_normal((n, k + 1)))
+    U, v = Q[:, :k], Q[:, k]
+    X = U.copy()
+    X[:, 2] = np.cos(theta) * U[:, 2] + np.sin(theta) * v
+    M = rng.standard_normal((k, k))  # any other basis of the same span
+    s = principal_sine(U, X @ M)
+    assert abs(s - np.sin(theta)) <= 1e-12 + 1e-9 * np.sin(theta)
+    assert principal_sine(U, U @ M) <= 1e-14
+    assert principal_sine(U, X[:, :k - 1]) == 1.0  # unequal dimensions
