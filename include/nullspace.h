@@ -87,7 +87,21 @@ typedef struct {
   int profile;         /* > 0: time every profile-th launch of each kernel class with
                           CUDA events on the library stream (ns_profile); 0 = off   */
   int batch_block;     /* ns_batch_solve: threads per CTA, 128 or 256; 0 = default (128) */
+  int gemm;            /* thick-restart product Z V_Z (Sec. 4.1): NS_GEMM_* (default 0)  */
 } ns_opts;
+
+/* Kernel of the thick-restart product Z V_Z (ns_opts.gemm, ns_restart_product). */
+typedef enum {
+  NS_GEMM_DEFAULT = 0,   /* the library's choice: NS_GEMM_TC3 on the mixed path, NS_GEMM_TC_EXACT
+                            on the FP64 path when restart_len <= 128, else CUDA cores          */
+  NS_GEMM_CUDA_CORES = 1,/* FP32 / FP64 FMA register-tile kernels                                 */
+  NS_GEMM_TC2 = 2,       /* mixed path: tensor cores, operands split into 2 bf16 slices, 3 products
+                            (3xBF16)                                                          */
+  NS_GEMM_TC3 = 3,       /* mixed path: tensor cores, 3 bf16 slices, 6 products (FP32 accuracy)  */
+  NS_GEMM_TC_EXACT = 4   /* FP64 path: tensor cores, each FP64 operand split exactly into eight
+                            7-bit integer slices (per-row / per-column exponents), exact FP32
+                            slice sums combined in int64: FP64 accuracy; restart_len <= 128  */
+} ns_gemm;
 
 typedef struct {
   int64_t nullity;       /* N = number of locked (null) vectors                      */
@@ -222,6 +236,23 @@ ns_status ns_apply_B(ns_handle* h, int d, const double* X, double* Y, double eps
  * three timed launches after one warm-up (about 50 ms each).  Allocates and frees
  * a small device buffer; uses the legacy default stream. */
 ns_status ns_fma_peak(int precision, double* tflops);
+
+/* ns_restart_product -- the thick-restart product of Alg. 2 (Sec. 4.1: the retained
+ * Ritz vectors Z V_Z(:, keep) and the locked candidates) exactly as ns_solve computes
+ * it, exposed so that each kernel can be checked on its own.
+ *   Z   : n x R column-major FP64, host (the Lanczos basis; blocks of d columns)
+ *   VZ  : R x R column-major FP64, host (eigenvectors of T)
+ *   sel : nsel column indices into VZ, host
+ *   nl  : the first nl outputs go to the locked-candidate panel, the rest to the
+ *         next basis (the two output layouts ns_solve uses); 0 <= nl <= nsel
+ *   precision : NS_FP64 (FP64 Z) or NS_MIXED (Z rounded to FP32, FP32 result)
+ *   gemm      : ns_gemm; NS_GEMM_TC2 / TC3 need precision NS_MIXED and nsel <= 256,
+ *               NS_GEMM_TC_EXACT needs NS_FP64 and R <= 128
+ *   out : n x nsel column-major FP64, host
+ * d in {1, 2, 4, 8}, R a multiple of d, 1 <= R <= 512.  NS_ERR_TIMEOUT when a bounded
+ * device wait gave up.  Allocates its own device buffers. */
+ns_status ns_restart_product(int64_t n, int d, int R, const double* Z, const double* VZ, const int32_t* sel,
+                             int nsel, int nl, int precision, int gemm, double* out);
 
 /* ns_trace_omega -- the W recurrence of Sec. 4.2 (the bounds w_{k,l} on
  * ||Q_k^T Q_l|| that decide partial reorthogonalization) exactly as ns_solve

@@ -283,7 +283,8 @@ struct Solver {
   Csr<T> A, At;
   const T* Dv;
   // buffers
-  Buf zb[2], qp, ybuf, xbuf, lnew, cbuf, dpart, redpart, small, pin;
+  Buf zb[2], qp, ybuf, xbuf, lnew, cbuf, dpart, redpart, small, pin, umma_img;
+  unsigned* umma_err = nullptr;  // set by the tensor-core restart product when a bounded wait gave up
   T* Z[2];
   int cur = 0;
   int cap = 0, nlock = 0;
@@ -373,9 +374,14 @@ struct Solver {
     sel = reinterpret_cast<int*>(b + osel);
     flags = reinterpret_cast<unsigned*>(b + oflags);
     red.ticket = flags + 4;
+    umma_err = flags + 8;
     counters = reinterpret_cast<long long*>(b + ocnt);
     ck(cudaMemsetAsync(small.p, 0, sizeof(double) * off, s), "memset");
     alloc_locked_meta();
+    if (std::is_same<T, float>::value && gemm_kind() != NS_GEMM_CUDA_CORES)
+      umma_img = Buf(h, restart_umma_image_bytes(R, std::min(R, 256), 3));
+    if (std::is_same<T, double>::value && gemm_kind() == NS_GEMM_TC_EXACT)
+      umma_img = Buf(h, restart_ozaki_scratch_bytes(n, R, R));
     ck(cudaMallocHost(&pin_d, sizeof(double) * (2 * (size_t)R + 64)), "cudaMallocHost");
     flags_h = reinterpret_cast<unsigned*>(pin_d + 2 * R + 32);
     // SpMM schedule: lanes per row tuned on this matrix (operands: the basis buffers)
@@ -472,6 +478,38 @@ struct Solver {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return best;
+  }
+
+  // kernel of the thick-restart product (Sec. 4.1): tensor cores on the mixed path
+  int gemm_kind() const {
+    if (!std::is_same<T, float>::value) {
+      if (o.gemm == NS_GEMM_DEFAULT) return restart_ozaki_supported(R, 1) ? NS_GEMM_TC_EXACT : NS_GEMM_CUDA_CORES;
+      return o.gemm;
+    }
+    return o.gemm == NS_GEMM_DEFAULT ? NS_GEMM_TC3 : o.gemm;
+  }
+  // [Lnew | Znext] = Z V_Z(:, sel(0:nsel)), the first nl outputs to Lnew
+  void restart_product(int nsel, int nl, T* Lnew, T* Znext) {
+    const int g = gemm_kind();
+    if constexpr (std::is_same<T, float>::value) {
+      if ((g == NS_GEMM_TC2 || g == NS_GEMM_TC3) && restart_umma_supported(R, nsel)) {
+        ck(restart_gemm_umma(Z[cur], D, R, VZ, sel, nsel, nl, n, Lnew, Znext, umma_img.p, umma_err,
+                             g == NS_GEMM_TC2 ? 2 : 3, s),
+           "restart_gemm_umma");
+        launches += 2;
+        return;
+      }
+    }
+    if constexpr (std::is_same<T, double>::value) {
+      if (g == NS_GEMM_TC_EXACT && restart_ozaki_supported(R, nsel)) {
+        ck(restart_gemm_ozaki(Z[cur], D, R, VZ, sel, nsel, nl, n, Lnew, Znext, umma_img.p, umma_err, s),
+           "restart_gemm_ozaki");
+        launches += 3;
+        return;
+      }
+    }
+    ck(restart_gemm<T>(Z[cur], D, R, VZ, sel, nsel, nl, n, Lnew, Znext, s), "restart_gemm shared-memory limit");
+    launches += 1;
   }
 
   T* X() const { return xbuf.as<T>(); }
@@ -795,10 +833,8 @@ struct Solver {
       {
         const double nc = (double)cand.size();
         PScope ps(&h->prof, P_GEMM, (double)n * (R + nc) * sizeof(T), 2.0 * n * R * nc);
-        ck(restart_gemm<T>(Z[cur], D, R, VZ, sel, (int)cand.size(), (int)cand.size(), n, lnew.as<T>(), nullptr, s),
-           "restart_gemm shared-memory limit");
+        restart_product((int)cand.size(), (int)cand.size(), lnew.as<T>(), nullptr);
       }
-      launches += 1;
       const int before = nlock;
       int ng = 0;
       {
@@ -838,9 +874,8 @@ struct Solver {
     ck(cudaMemcpyAsync(sel, avail.data(), sizeof(int) * nk, cudaMemcpyHostToDevice, s), "h2d");
     {
       PScope ps(&h->prof, P_GEMM, (double)n * (R + nk) * sizeof(T), 2.0 * n * R * nk);
-      ck(restart_gemm<T>(Z[cur], D, R, VZ, sel, nk, 0, n, nullptr, Z[other], s), "restart_gemm shared-memory limit");
+      restart_product(nk, 0, nullptr, Z[other]);
     }
-    launches += 1;
     // Alg. 2 line 16: Q_{l+1} against [X, Z_new], moved to block nk/D of the new buffer
     T* qlast = blk(cur, nb);
     clear_flags();
@@ -1155,6 +1190,9 @@ static ns_status solve_typed(ns_handle* h, int R, double tol, const ns_opts& o) 
   cudaEventElapsedTime(&t2, e1, e2);
   long long cnt[4] = {0, 0, 0, 0};
   ck(cudaMemcpy(cnt, S.counters, sizeof(cnt), cudaMemcpyDeviceToHost), "d2h");
+  unsigned uerr = 0;
+  ck(cudaMemcpy(&uerr, S.umma_err, sizeof(unsigned), cudaMemcpyDeviceToHost), "d2h");
+  if (uerr) st = NS_ERR_TIMEOUT;  // a bounded wait of the tensor-core product gave up
   ns_stats_t& x = h->stats;
   x = ns_stats_t{};
   x.nullity = N;
@@ -1265,6 +1303,69 @@ static void project_typed(ns_handle* h, int64_t n, int K, const double* V, doubl
   for (int t = 0; t < K * W; ++t) C[t] = c1[t] + c2[t];
 }
 
+template <typename T>
+static void restart_product_typed(ns_handle* h, int64_t n, int d, int R, const double* Zh, const double* VZh,
+                                  const int32_t* selh, int nsel, int nl, int gemm, double* outh) {
+  // Z into the solver's panel layout: block b of d columns is an n x d row-major panel
+  std::vector<T> zp((size_t)n * R);
+  for (int j = 0; j < R; ++j) {
+    const int b = j / d, q = j % d;
+    for (int64_t i = 0; i < n; ++i) zp[(size_t)b * n * d + (size_t)i * d + q] = (T)Zh[(size_t)j * n + i];
+  }
+  const int nz = nsel - nl;
+  Buf bz(h, sizeof(T) * zp.size()), bv(h, sizeof(double) * (size_t)R * R), bs(h, sizeof(int) * nsel),
+      bl(h, sizeof(T) * (size_t)n * std::max(nl, 1)), bn(h, sizeof(T) * (size_t)n * std::max(nz, 1)),
+      img(h, std::max(restart_umma_image_bytes(R, std::max(nsel, 1), 3), restart_ozaki_scratch_bytes(n, R, nsel))),
+      fl(h, 256);
+  cudaStream_t s = h->stream;
+  ck(cudaMemcpyAsync(bz.p, zp.data(), bz.bytes, cudaMemcpyHostToDevice, s), "h2d");
+  ck(cudaMemcpyAsync(bv.p, VZh, bv.bytes, cudaMemcpyHostToDevice, s), "h2d");
+  ck(cudaMemcpyAsync(bs.p, selh, sizeof(int) * nsel, cudaMemcpyHostToDevice, s), "h2d");
+  ck(cudaMemsetAsync(fl.p, 0, 256, s), "memset");
+  const bool tc = gemm == NS_GEMM_TC2 || gemm == NS_GEMM_TC3 ||
+                  (gemm == NS_GEMM_DEFAULT && std::is_same<T, float>::value);
+  const bool exact = gemm == NS_GEMM_TC_EXACT ||
+                     (gemm == NS_GEMM_DEFAULT && std::is_same<T, double>::value && restart_ozaki_supported(R, nsel));
+  if constexpr (std::is_same<T, float>::value) {
+    if (tc) {
+      if (!restart_umma_supported(R, nsel)) throw Fail{NS_ERR_INVALID_ARG, "tensor-core product needs nsel <= 256"};
+      ck(restart_gemm_umma(bz.as<float>(), d, R, bv.as<double>(), bs.as<int>(), nsel, nl, n, bl.as<float>(),
+                           bn.as<float>(), img.p, fl.as<unsigned>(), gemm == NS_GEMM_TC2 ? 2 : 3, s),
+         "restart_gemm_umma");
+    }
+  }
+  if constexpr (std::is_same<T, double>::value) {
+    if (exact) {
+      if (!restart_ozaki_supported(R, nsel)) throw Fail{NS_ERR_INVALID_ARG, "exact tensor-core product needs R <= 128"};
+      ck(restart_gemm_ozaki(bz.as<double>(), d, R, bv.as<double>(), bs.as<int>(), nsel, nl, n, bl.as<double>(),
+                            bn.as<double>(), img.p, fl.as<unsigned>(), s),
+         "restart_gemm_ozaki");
+    }
+  }
+  if (!tc && !exact)
+    ck(restart_gemm<T>(bz.as<T>(), d, R, bv.as<double>(), bs.as<int>(), nsel, nl, n, bl.as<T>(), bn.as<T>(), s),
+       "restart_gemm");
+  ck_launch("restart product");
+  std::vector<T> L((size_t)n * std::max(nl, 1)), Zn((size_t)n * std::max(nz, 1));
+  unsigned err = 0;
+  ck(cudaMemcpyAsync(L.data(), bl.p, bl.bytes, cudaMemcpyDeviceToHost, s), "d2h");
+  ck(cudaMemcpyAsync(Zn.data(), bn.p, bn.bytes, cudaMemcpyDeviceToHost, s), "d2h");
+  ck(cudaMemcpyAsync(&err, fl.p, sizeof(unsigned), cudaMemcpyDeviceToHost, s), "d2h");
+  ck(cudaStreamSynchronize(s), "sync");
+  if (err) throw Fail{NS_ERR_TIMEOUT, "a bounded wait of the tensor-core product gave up"};
+  for (int c = 0; c < nsel; ++c)
+    for (int64_t i = 0; i < n; ++i) {
+      double v;
+      if (c < nl) {
+        v = (double)L[(size_t)i * nl + c];
+      } else {
+        const int kz = c - nl;
+        v = (double)Zn[(size_t)(kz / d) * n * d + (size_t)i * d + kz % d];
+      }
+      outh[(size_t)c * n + i] = v;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
@@ -1285,6 +1386,7 @@ void ns_default_opts(ns_opts* o) {
   o->use_graphs = 0;
   o->batch_block = 0;
   o->profile = 0;
+  o->gemm = NS_GEMM_DEFAULT;
 }
 
 static ns_status set_err(ns_handle* h, ns_status st, const std::string& msg) {
@@ -1437,6 +1539,12 @@ ns_status ns_solve(ns_handle* h, int d, int restart_len, double tol, const ns_op
   ns_default_opts(&o);
   if (opts) o = *opts;
   if (!(o.eps >= 0.0) || o.stop_factor <= 0.0) return set_err(h, NS_ERR_INVALID_ARG, "bad opts");
+  if (o.gemm < NS_GEMM_DEFAULT || o.gemm > NS_GEMM_TC_EXACT ||
+      (o.precision != NS_MIXED && (o.gemm == NS_GEMM_TC2 || o.gemm == NS_GEMM_TC3)) ||
+      (o.precision == NS_MIXED && o.gemm == NS_GEMM_TC_EXACT) ||
+      (o.gemm == NS_GEMM_TC_EXACT && !restart_ozaki_supported(restart_len, 1)))
+    return set_err(h, NS_ERR_INVALID_ARG,
+                   "gemm: 0..4; TC2/TC3 on the mixed path, TC_EXACT on the FP64 path with restart_len <= 128");
   h->err.clear();
   h->solved = false;
   h->launches = 0;
@@ -1619,6 +1727,30 @@ ns_status ns_apply_B(ns_handle* h, int d, const double* X, double* Y, double eps
     if (spmm_wait_timeouts(true)) throw Fail{NS_ERR_TIMEOUT, "a bounded device wait of the SpMM expired"};
   } catch (const Fail& f) {
     return set_err(h, f.st, f.msg);
+  }
+  return NS_OK;
+}
+
+ns_status ns_restart_product(int64_t n, int d, int R, const double* Z, const double* VZ, const int32_t* sel, int nsel,
+                             int nl, int precision, int gemm, double* out) {
+  if (n < 1 || !(d == 1 || d == 2 || d == 4 || d == 8) || R < 1 || R > 512 || R % d || nsel < 1 || nl < 0 ||
+      nl > nsel || (nsel - nl) % d || !Z || !VZ || !sel || !out || gemm < 0 || gemm > NS_GEMM_TC_EXACT ||
+      (precision != NS_FP64 && precision != NS_MIXED))
+    return NS_ERR_INVALID_ARG;
+  if (precision == NS_FP64 && (gemm == NS_GEMM_TC2 || gemm == NS_GEMM_TC3)) return NS_ERR_INVALID_ARG;
+  if (precision == NS_MIXED && gemm == NS_GEMM_TC_EXACT) return NS_ERR_INVALID_ARG;
+  for (int c = 0; c < nsel; ++c)
+    if (sel[c] < 0 || sel[c] >= R) return NS_ERR_INVALID_ARG;
+  ns_handle tmp;
+  try {
+    if (precision == NS_MIXED)
+      restart_product_typed<float>(&tmp, n, d, R, Z, VZ, sel, nsel, nl, gemm, out);
+    else
+      restart_product_typed<double>(&tmp, n, d, R, Z, VZ, sel, nsel, nl, gemm, out);
+  } catch (const Fail& f) {
+    cudaGetLastError();
+    fprintf(stderr, "ns_restart_product: %s\n", f.msg.c_str());
+    return f.st;
   }
   return NS_OK;
 }

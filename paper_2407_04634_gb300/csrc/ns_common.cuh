@@ -306,10 +306,13 @@ inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
 // Raises the dynamic shared-memory limit of kernel `fn` to at least `bytes` on the
 // current device.  The attribute belongs to the (function, device) pair, so it is
-// tracked per device; calls from several host threads are serialized.  Returns
-// the status of cudaFuncSetAttribute (cudaSuccess when nothing had to change).
+// tracked per device; calls from several host threads are serialized.  Any nonzero
+// request is raised explicitly: the default 48 KiB covers static plus dynamic shared
+// memory, so a kernel with static arrays can need the opt-in below 48 KiB of
+// dynamic memory.  Returns the status of cudaFuncSetAttribute (cudaSuccess when
+// nothing had to change).
 inline cudaError_t ensure_smem_limit(const void* fn, size_t bytes) {
-  if (bytes <= 48 * 1024) return cudaSuccess;
+  if (bytes == 0) return cudaSuccess;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;

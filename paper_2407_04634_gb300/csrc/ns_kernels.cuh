@@ -127,6 +127,22 @@ cudaError_t proj_update_reserve_smem(size_t bytes);
 template <typename T>
 cudaError_t restart_gemm(const T* Z, int d, int R, const double* VZ, const int* sel, int nsel, int nl, int64_t n,
                          T* Lnew, T* Znext, cudaStream_t s);
+// the same product on the tensor cores (tcgen05, FP32 basis): operands split into
+// `slices` bf16 slices (2: 3 products, 3: 6 products), FP32 accumulation in tensor
+// memory; image = scratch of restart_umma_image_bytes(R, nsel, slices) bytes; err bit 1
+// is set when a bounded mbarrier wait gave up.  Needs restart_umma_supported(R, nsel).
+cudaError_t restart_gemm_umma(const float* Z, int d, int R, const double* VZ, const int* sel, int nsel, int nl,
+                              int64_t n, float* Lnew, float* Znext, void* image, unsigned* err, int slices,
+                              cudaStream_t s);
+size_t restart_umma_image_bytes(int R, int nsel, int slices);
+bool restart_umma_supported(int R, int nsel);
+// the FP64 product on the tensor cores, error-free slicing (eight 7-bit integer slices
+// per operand, exact FP32 group sums, int64 combination); R <= 128; scratch of
+// restart_ozaki_scratch_bytes(n, R, nsel) bytes
+cudaError_t restart_gemm_ozaki(const double* Z, int d, int R, const double* VZ, const int* sel, int nsel, int nl,
+                               int64_t n, double* Lnew, double* Znext, void* scratch, unsigned* err, cudaStream_t s);
+size_t restart_ozaki_scratch_bytes(int64_t n, int R, int nsel);
+bool restart_ozaki_supported(int R, int nsel);
 // copy w columns of a row-major panel (ld) into column-major X (ld n) starting at column c0
 template <typename T>
 void panel_to_cols(const T* P, int64_t ldp, int w, int64_t n, T* X, int c0, cudaStream_t s);

@@ -22,6 +22,7 @@ STATUS = {0: "NS_OK", 1: "NS_ERR_INVALID_ARG", 2: "NS_ERR_OOM", 3: "NS_ERR_CUDA"
 MODE = {"normal": 0, "spd": 1}
 PRECISION = {"fp64": 0, "mixed": 1}
 REORTH = {"partial": 0, "full": 1}
+GEMM = {"default": 0, "cuda_cores": 1, "tc2": 2, "tc3": 3, "tc_exact": 4}
 
 _ALLOC = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 _FREE = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p)
@@ -35,7 +36,7 @@ class NsOpts(C.Structure):
     _fields_ = [("eps", C.c_double), ("precision", C.c_int), ("reorth", C.c_int), ("max_matvec", C.c_int64),
                 ("stop_factor", C.c_double), ("lock_tol_mixed", C.c_double), ("refine", C.c_int),
                 ("refine_tol", C.c_double), ("refine_maxit", C.c_int), ("refine_chunk", C.c_int),
-                ("use_graphs", C.c_int), ("profile", C.c_int), ("batch_block", C.c_int)]
+                ("use_graphs", C.c_int), ("profile", C.c_int), ("batch_block", C.c_int), ("gemm", C.c_int)]
 
 
 class NsStats(C.Structure):
@@ -86,6 +87,8 @@ SIGNATURES = {
     "ns_trace_omega": (C.c_int, [_P, C.c_int, C.c_int, C.POINTER(NsOpts), _P]),
     "ns_syev": (C.c_int, [C.c_int, _P, _P, _P]),
     "ns_fma_peak": (C.c_int, [C.c_int, C.POINTER(C.c_double)]),
+    "ns_restart_product": (C.c_int, [C.c_int64, C.c_int, C.c_int, _P, _P, _P, C.c_int, C.c_int, C.c_int, C.c_int,
+                                     _P]),
     "ns_project": (C.c_int, [C.c_int64, C.c_int, C.c_int, _P, _P, _P, C.c_int]),
     "ns_project_noalloc": (C.c_int, [C.c_int64, C.c_int, C.c_int, _P, _P, _P, _P]),
     "ns_batch_create": (C.c_int, [C.POINTER(_P), C.c_int64, _P, _P, _P, _P, C.c_int, C.c_uint64,
@@ -135,6 +138,8 @@ def default_opts(**kw) -> NsOpts:
             v = PRECISION[v]
         if k == "reorth" and isinstance(v, str):
             v = REORTH[v]
+        if k == "gemm" and isinstance(v, str):
+            v = GEMM[v]
         if not hasattr(o, k):
             raise TypeError(f"unknown option {k}")
         setattr(o, k, v)
@@ -288,6 +293,22 @@ class Handle:
             self.close()
         except Exception:
             pass
+
+
+def restart_product(Z: np.ndarray, VZ: np.ndarray, sel, nl: int, d: int, precision: str = "fp64",
+                    gemm: str = "default") -> np.ndarray:
+    """Z V_Z(:, sel) with the library's restart-product kernel (n x nsel FP64)."""
+    lib = load()
+    n, R = Z.shape
+    Zc = np.asfortranarray(Z, dtype=np.float64)
+    Vc = np.asfortranarray(VZ, dtype=np.float64)
+    sel = np.ascontiguousarray(sel, dtype=np.int32)
+    out = np.zeros((n, sel.size), order="F")
+    st = lib.ns_restart_product(n, int(d), R, C.c_void_p(Zc.ctypes.data), C.c_void_p(Vc.ctypes.data), _ptr(sel),
+                                sel.size, int(nl), PRECISION[precision], GEMM[gemm], C.c_void_p(out.ctypes.data))
+    if st != NS_OK:
+        raise NullspaceError(st, "ns_restart_product")
+    return out
 
 
 def fma_peak(precision: str = "fp64") -> float:
