@@ -51,8 +51,10 @@ typedef enum {
 
 typedef enum {
   NS_FP64 = 0,  /* everything in FP64                                               */
-  NS_MIXED = 1  /* A values, Lanczos basis, SpMM and projections in FP32; projected
+  NS_MIXED = 1, /* A values, Lanczos basis, SpMM and projections in FP32; projected
                    eigenproblem, W recurrence and final refinement in FP64          */
+  NS_FP64_PAIRS = 2 /* ns_project only: FP64 data, products in compensated FP32 pairs
+                   (the FP64 path's default arithmetic for its projections)          */
 } ns_precision;
 
 typedef enum {
@@ -88,6 +90,10 @@ typedef struct {
                           CUDA events on the library stream (ns_profile); 0 = off   */
   int batch_block;     /* ns_batch_solve: threads per CTA, 128 or 256; 0 = default (128) */
   int gemm;            /* thick-restart product Z V_Z (Sec. 4.1): NS_GEMM_* (default 0)  */
+  int fp64_products;   /* FP64 path, Gram-Schmidt products V^T W and W - V C: 0 = compensated
+                          FP32 pairs on the FP32 pipe (default; each FP64 operand split
+                          exactly into two FP32 words, TwoProd / TwoSum accumulation, error
+                          about 2^-47 sum |v w|), 1 = FP64 FMA                            */
 } ns_opts;
 
 /* Kernel of the thick-restart product Z V_Z (ns_opts.gemm, ns_restart_product). */
@@ -277,9 +283,10 @@ ns_status ns_syev(int k, const double* T, double* theta, double* V);
 
 /* Block classical Gram-Schmidt, two passes (CGS2), as used for the partial
  * reorthogonalization (Sec. 4.2): W <- (I - V V^T)^2 W for V (n x K, column-major)
- * and W (n x w, row-major, 1 <= w <= 8).  Host arrays; FP64 (precision NS_FP64)
- * or FP32 arithmetic (NS_MIXED).  C (K x w, row-major) receives the summed
- * coefficients of both passes. */
+ * and W (n x w, row-major, 1 <= w <= 8).  Host arrays; precision NS_FP64 (FP64
+ * FMA), NS_FP64_PAIRS (FP64 data, compensated FP32-pair products, as ns_solve's
+ * FP64 path uses by default) or NS_MIXED (FP32).  C (K x w, row-major) receives the
+ * summed coefficients of both passes. */
 ns_status ns_project(int64_t n, int K, int w, const double* V, double* W, double* C, int precision);
 
 /* ns_project_noalloc -- the same FP64 CGS2 projection as ns_project, for callers

@@ -5,6 +5,7 @@
 #include "ns_kernels.cuh"
 
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 namespace ns {
@@ -60,19 +61,6 @@ template void rng_gauss<float>(uint64_t, uint32_t, float*, int64_t, cudaStream_t
 // ---------------------------------------------------------------------------
 // CholQR passes on n x D panels
 // ---------------------------------------------------------------------------
-// pivot test shared by the last blocks: Cholesky of G; on failure set flag bit 1
-__device__ inline void finish_chol(const double* G, int d, double* R, double* gdiag, unsigned* flags) {
-  double Rl[kMaxD * kMaxD];
-  const bool ok = chol_upper(G, Rl, d);
-  if (gdiag)
-    for (int i = 0; i < d; ++i) gdiag[i] = G[i * d + i];
-  if (!ok) {
-    for (int i = 0; i < d * d; ++i) Rl[i] = (i % (d + 1) == 0) ? 1.0 : 0.0;
-    if (flags) atomicOr(flags, 1u);
-  }
-  for (int i = 0; i < d * d; ++i) R[i] = Rl[i];
-}
-
 template <typename T, int D>
 __global__ void __launch_bounds__(kThreads) k_axpy_gram(T* __restrict__ qp, const T* __restrict__ x,
                                                         const double* __restrict__ Xi, int64_t n, double* R1,
@@ -342,6 +330,12 @@ void proj_dots(const VParts<T>& V, const T* Wp, const T* Wp2, int64_t ldw, int64
   const int K = V.kx + V.kz;
   if (K == 0) return;
   const int64_t rpc = dots_rows_per_chunk(n);
+  if constexpr (std::is_same<T, double>::value) {
+    if (V.df) {
+      proj_dots_df<W>(V, Wp, Wp2, ldw, n, C, part, rpc, s);
+      return;
+    }
+  }
   const int nchunks = ceil_div(n, rpc);
   constexpr int KT = dots_kt<W>();
   dim3 grid(nchunks, ceil_div(V.kx, KT) + ceil_div(V.kz, KT));
@@ -436,6 +430,9 @@ __global__ void __launch_bounds__(kThreads) k_proj_update(VParts<T> V, const dou
 template <typename T, int W>
 cudaError_t proj_update(const VParts<T>& V, const double* C, T* Wp, T* Wp2, int64_t ldw, int64_t n, int gram,
                         double* R, double* gdiag, unsigned* flags, const Red& red, cudaStream_t s) {
+  if constexpr (std::is_same<T, double>::value) {
+    if (V.df) return proj_update_df<W>(V, C, Wp, Wp2, ldw, n, gram, R, gdiag, flags, red, s);
+  }
   const int K = V.kx + V.kz;
   const size_t smem = sizeof(T) * (size_t)K * W;
   cudaError_t e = cudaSuccess;

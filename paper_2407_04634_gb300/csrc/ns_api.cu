@@ -574,6 +574,7 @@ struct Solver {
     V.Z = Z[zw];
     V.kz = nzb * D;
     V.p = D;
+    V.df = (std::is_same<T, double>::value && o.fp64_products == 0) ? 1 : 0;
     if (V.kx + V.kz == 0) {
       if (gram && !Wp2) {
         gram_chol<T, W>(Wp, ldw, W, n, Rout, gd, flags, red, s);
@@ -1260,7 +1261,7 @@ static void apply_B_typed(ns_handle* h, const T* x, T* y, double eps, Red red, i
 }
 
 template <typename T, int W>
-static void project_typed(ns_handle* h, int64_t n, int K, const double* V, double* Wm, double* C) {
+static void project_typed(ns_handle* h, int64_t n, int K, const double* V, double* Wm, double* C, int df) {
   Buf vb(h, sizeof(T) * n * std::max(K, 1)), wb(h, sizeof(T) * n * W), v64(h, sizeof(double) * n * std::max(K, 1)),
       w64(h, sizeof(double) * n * W), cb(h, sizeof(double) * K * W), cb2(h, sizeof(double) * K * W),
       part(h, sizeof(double) * ((size_t)ceil_div(n, std::min<int64_t>(kThreads * 128, n)) * K * W + 8)),
@@ -1287,6 +1288,7 @@ static void project_typed(ns_handle* h, int64_t n, int K, const double* V, doubl
   P.Z = nullptr;
   P.kz = 0;
   P.p = 1;
+  P.df = df;
   proj_dots<T, W>(P, wp, nullptr, W, n, cb.as<double>(), part.as<double>(), nullptr);
   ck((proj_update<T, W>(P, cb.as<double>(), wp, nullptr, W, n, 0, nullptr, nullptr, nullptr, red, nullptr)), "limit");
   proj_dots<T, W>(P, wp, nullptr, W, n, cb2.as<double>(), part.as<double>(), nullptr);
@@ -1387,6 +1389,7 @@ void ns_default_opts(ns_opts* o) {
   o->batch_block = 0;
   o->profile = 0;
   o->gemm = NS_GEMM_DEFAULT;
+  o->fp64_products = 0;
 }
 
 static ns_status set_err(ns_handle* h, ns_status st, const std::string& msg) {
@@ -1539,6 +1542,8 @@ ns_status ns_solve(ns_handle* h, int d, int restart_len, double tol, const ns_op
   ns_default_opts(&o);
   if (opts) o = *opts;
   if (!(o.eps >= 0.0) || o.stop_factor <= 0.0) return set_err(h, NS_ERR_INVALID_ARG, "bad opts");
+  if (!(o.precision == NS_FP64 || o.precision == NS_MIXED) || !(o.fp64_products == 0 || o.fp64_products == 1))
+    return set_err(h, NS_ERR_INVALID_ARG, "precision must be NS_FP64 or NS_MIXED; fp64_products 0 or 1");
   if (o.gemm < NS_GEMM_DEFAULT || o.gemm > NS_GEMM_TC_EXACT ||
       (o.precision != NS_MIXED && (o.gemm == NS_GEMM_TC2 || o.gemm == NS_GEMM_TC3)) ||
       (o.precision == NS_MIXED && o.gemm == NS_GEMM_TC_EXACT) ||
@@ -1809,22 +1814,24 @@ ns_status ns_syev(int k, const double* T, double* theta, double* V) {
 
 ns_status ns_project(int64_t n, int K, int w, const double* V, double* Wm, double* C, int precision) {
   if (n < 1 || K < 1 || !(w == 1 || w == 2 || w == 4 || w == 8) || !V || !Wm || !C) return NS_ERR_INVALID_ARG;
+  if (precision != NS_FP64 && precision != NS_MIXED && precision != NS_FP64_PAIRS) return NS_ERR_INVALID_ARG;
+  const int df = precision == NS_FP64_PAIRS ? 1 : 0;
   ns_handle tmp;
   tmp.n = n;
   try {
     if (precision == NS_MIXED) {
       switch (w) {
-        case 1: project_typed<float, 1>(&tmp, n, K, V, Wm, C); break;
-        case 2: project_typed<float, 2>(&tmp, n, K, V, Wm, C); break;
-        case 4: project_typed<float, 4>(&tmp, n, K, V, Wm, C); break;
-        default: project_typed<float, 8>(&tmp, n, K, V, Wm, C); break;
+        case 1: project_typed<float, 1>(&tmp, n, K, V, Wm, C, 0); break;
+        case 2: project_typed<float, 2>(&tmp, n, K, V, Wm, C, 0); break;
+        case 4: project_typed<float, 4>(&tmp, n, K, V, Wm, C, 0); break;
+        default: project_typed<float, 8>(&tmp, n, K, V, Wm, C, 0); break;
       }
     } else {
       switch (w) {
-        case 1: project_typed<double, 1>(&tmp, n, K, V, Wm, C); break;
-        case 2: project_typed<double, 2>(&tmp, n, K, V, Wm, C); break;
-        case 4: project_typed<double, 4>(&tmp, n, K, V, Wm, C); break;
-        default: project_typed<double, 8>(&tmp, n, K, V, Wm, C); break;
+        case 1: project_typed<double, 1>(&tmp, n, K, V, Wm, C, df); break;
+        case 2: project_typed<double, 2>(&tmp, n, K, V, Wm, C, df); break;
+        case 4: project_typed<double, 4>(&tmp, n, K, V, Wm, C, df); break;
+        default: project_typed<double, 8>(&tmp, n, K, V, Wm, C, df); break;
       }
     }
   } catch (const Fail& f) {

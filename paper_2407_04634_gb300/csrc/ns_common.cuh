@@ -265,6 +265,20 @@ __host__ __device__ inline void sv_minmax(const double* M, int d, double* smax, 
   *smin = sqrt(fmax(mn, 0.0));
 }
 
+// pivot test shared by the last blocks of the CholQR kernels: Cholesky of the d x d
+// Gram matrix G (d <= kMaxD); on failure R = I and flag bit 1 is set
+__device__ inline void finish_chol(const double* G, int d, double* R, double* gdiag, unsigned* flags) {
+  double Rl[kMaxD * kMaxD];
+  const bool ok = chol_upper(G, Rl, d);
+  if (gdiag)
+    for (int i = 0; i < d; ++i) gdiag[i] = G[i * d + i];
+  if (!ok) {
+    for (int i = 0; i < d * d; ++i) Rl[i] = (i % (d + 1) == 0) ? 1.0 : 0.0;
+    if (flags) atomicOr(flags, 1u);
+  }
+  for (int i = 0; i < d * d; ++i) R[i] = Rl[i];
+}
+
 // ---------------------------------------------------------------------------
 // vector loads of one row of a row-major n x D panel
 // ---------------------------------------------------------------------------

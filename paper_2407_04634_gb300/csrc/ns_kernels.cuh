@@ -107,6 +107,7 @@ struct VParts {
   const T* Z = nullptr;
   int kz = 0;
   int p = 1;
+  int df = 0;  // FP64 only: 1 = the products in compensated FP32-pair arithmetic (k_dfproj.cu)
 };
 // C (K x w, FP64, row-major) = V^T W ; W panel with leading dim ldw; when Wp2 is
 // given, columns [W/2, W) of W come from the panel Wp2 (same ldw)
@@ -119,6 +120,14 @@ void proj_dots(const VParts<T>& V, const T* Wp, const T* Wp2, int64_t ldw, int64
 template <typename T, int W>
 cudaError_t proj_update(const VParts<T>& V, const double* C, T* Wp, T* Wp2, int64_t ldw, int64_t n, int gram,
                         double* R, double* gdiag, unsigned* flags, const Red& red, cudaStream_t s);
+// the FP64 products in compensated FP32-pair arithmetic (dispatched from proj_dots /
+// proj_update when V.df is set)
+template <int W>
+void proj_dots_df(const VParts<double>& V, const double* Wp, const double* Wp2, int64_t ldw, int64_t n, double* C,
+                  double* part, int64_t rows_per_chunk, cudaStream_t s);
+template <int W>
+cudaError_t proj_update_df(const VParts<double>& V, const double* C, double* Wp, double* Wp2, int64_t ldw, int64_t n,
+                           int gram, double* R, double* gdiag, unsigned* flags, const Red& red, cudaStream_t s);
 // raise the shared-memory limit of the P = 1 update kernels to `bytes` ahead of time
 template <typename T, int W>
 cudaError_t proj_update_reserve_smem(size_t bytes);

@@ -20,7 +20,7 @@ NS_OK, NS_ERR_INVALID_ARG, NS_ERR_OOM, NS_ERR_CUDA, NS_ERR_NOT_CONVERGED, NS_ERR
 STATUS = {0: "NS_OK", 1: "NS_ERR_INVALID_ARG", 2: "NS_ERR_OOM", 3: "NS_ERR_CUDA", 4: "NS_ERR_NOT_CONVERGED",
           5: "NS_ERR_TIMEOUT", 6: "NS_ERR_STATE", 7: "NS_ERR_REFINE", 8: "NS_ERR_NUMERICAL"}
 MODE = {"normal": 0, "spd": 1}
-PRECISION = {"fp64": 0, "mixed": 1}
+PRECISION = {"fp64": 0, "mixed": 1, "fp64_pairs": 2}
 REORTH = {"partial": 0, "full": 1}
 GEMM = {"default": 0, "cuda_cores": 1, "tc2": 2, "tc3": 3, "tc_exact": 4}
 
@@ -36,7 +36,8 @@ class NsOpts(C.Structure):
     _fields_ = [("eps", C.c_double), ("precision", C.c_int), ("reorth", C.c_int), ("max_matvec", C.c_int64),
                 ("stop_factor", C.c_double), ("lock_tol_mixed", C.c_double), ("refine", C.c_int),
                 ("refine_tol", C.c_double), ("refine_maxit", C.c_int), ("refine_chunk", C.c_int),
-                ("use_graphs", C.c_int), ("profile", C.c_int), ("batch_block", C.c_int), ("gemm", C.c_int)]
+                ("use_graphs", C.c_int), ("profile", C.c_int), ("batch_block", C.c_int), ("gemm", C.c_int),
+                ("fp64_products", C.c_int)]
 
 
 class NsStats(C.Structure):

@@ -160,18 +160,44 @@ def test_syev_matches_dense_eigensolver(ns, k):
 
 
 @pytest.mark.parametrize("w", [1, 2, 4, 8])
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "fp64_pairs", "mixed"])
 def test_cgs2_projection(ns, w, precision):
+    """CGS2 against a dense reference; fp64_pairs (FP64 data, compensated FP32-pair
+    products, the FP64 path's default) meets the same bars as FP64 FMA."""
     rng = np.random.default_rng(w)
     n, K = 70001, 37
     V, _ = np.linalg.qr(rng.standard_normal((n, K)))
     W = rng.standard_normal((n, w)) + V[:, :w] * 3.0
     Wp, Cc = ns.project(V, W, precision)
-    tol = 1e-13 if precision == "fp64" else 2e-6
+    f64 = precision != "mixed"
+    tol = 1e-13 if f64 else 2e-6
     assert np.abs(V.T @ Wp).max() <= tol * np.sqrt(n)
     ref = W - V @ (V.T @ W)
-    assert np.abs(Wp - ref).max() <= (1e-12 if precision == "fp64" else 1e-4)
-    np.testing.assert_allclose(Cc, V.T @ W, atol=1e-11 if precision == "fp64" else 1e-3)
+    assert np.abs(Wp - ref).max() <= (1e-12 if f64 else 1e-4)
+    np.testing.assert_allclose(Cc, V.T @ W, atol=1e-11 if f64 else 1e-3)
+
+
+@pytest.mark.parametrize("w", [2, 8])
+def test_pair_products_are_as_accurate_as_fp64(ns, w):
+    """Nearly orthogonal inputs (the partial-reorthogonalization case: |V^T W| ~ 1e-8
+    from terms of size 1/n): the coefficients from compensated FP32 pairs are at least
+    as close to an exactly rounded reference (computed in extended precision from the
+    FP64 inputs) as those of FP64 FMA, and within 1e-15."""
+    rng = np.random.default_rng(40 + w)
+    n, K = 100003, 16
+    V, _ = np.linalg.qr(rng.standard_normal((n, K)))
+    W = rng.standard_normal((n, w))
+    W -= V @ (V.T @ W)
+    W /= np.linalg.norm(W, axis=0)
+    W += 1e-8 * V[:, :w]
+    Vl, Wl = V.astype(np.longdouble), W.astype(np.longdouble)
+    ref = (Vl.T @ Wl).astype(np.float64)  # first pass of CGS2: C1 = V^T W
+    _, C64 = ns.project(V, W, "fp64")
+    _, Cdf = ns.project(V, W, "fp64_pairs")
+    # C sums both passes; the second pass adds V^T (W - V C1) ~ rounding level
+    e64 = np.abs(C64 - ref).max()
+    edf = np.abs(Cdf - ref).max()
+    assert edf <= 1e-15 and edf <= 4 * e64 + 1e-16
 
 
 # ------------------------------------------------------------------- solves ---

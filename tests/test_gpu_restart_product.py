@@ -133,3 +133,22 @@ def test_fp64_solve_with_each_restart_kernel(ns, gemm):
     As = A.to_scipy()
     assert principal_sine(indicator_basis(w.labels), X) <= 1e-6
     assert np.linalg.norm(As @ X) / norm2_A(As, "spd") <= 1e-8
+
+
+@pytest.mark.parametrize("products", [0, 1])
+def test_fp64_solve_with_each_product_arithmetic(ns, products):
+    """FP64 solves with the Gram-Schmidt products in compensated FP32 pairs (0, the
+    default) and in FP64 FMA (1): exact nullity, sine <= 1e-6, residual <= 1e-8."""
+    from oracle import principal_sine, indicator_basis, norm2_A, lanczos_nullspace
+    from workloads import incidence_cycle_components
+    w = incidence_cycle_components(22, 8000, 8, 8, 100, 3900 // 4)
+    A = w.A
+    h = ns.Handle(A.rowptr, A.colind, A.vals, A.m, A.n, 1002, w.mode)
+    r = h.solve(4, 80, 1e-10, fp64_products=products)
+    assert r.status == ns.NS_OK and r.nullity == 8
+    X = h.basis()
+    As = A.to_scipy()
+    ref = lanczos_nullspace(As, "normal", 4, 80, tol=1e-10, seed=1002)
+    assert principal_sine(ref.X, X) <= 1e-6
+    assert principal_sine(indicator_basis(w.labels), X) <= 1e-6
+    assert np.linalg.norm(As @ X) / norm2_A(As, "normal") <= 1e-8
