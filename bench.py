@@ -364,8 +364,11 @@ def residual_ratio(Ad, X, normA, chunk=64):
 
 
 def kernel_probe(ns, h, w, p):
-    """A handful of hot-kernel launches on the full-size inputs (for ncu captures):
-    three B-applies in each precision and two CGS2 projections against 256 vectors."""
+    """A handful of hot-kernel launches on the workload's inputs (for ncu captures):
+    three B-applies in each precision and every SpMM schedule, the thick-restart
+    product with every kernel (n x min(restart, 128) times half as many Ritz vectors),
+    and CGS2 projections of 2- and 8-wide panels against 256 vectors in FP64 pairs,
+    FP64 and FP32."""
     import numpy as np
     rng = np.random.default_rng(0)
     n = w.A.n
@@ -378,10 +381,22 @@ def kernel_probe(ns, h, w, p):
         out[f"apply_B_{prec}_s"] = (time.perf_counter() - t) / 3
         for sched in (64, 1, 2, 4, 8):  # every SpMM schedule once (TMA-staged, lanes per row)
             h.apply_B(X, 1e-3, prec, sched)
+    # thick-restart product Z V_Z(:, keep) at the workload's restart length, every kernel
+    R = p["restart"] - p["restart"] % 16 if p["restart"] > 128 else p["restart"]
+    R = min(R, 128)
+    Zr = rng.standard_normal((n, R)) / np.sqrt(n)
+    Vr, _ = np.linalg.qr(rng.standard_normal((R, R)))
+    keep = np.arange(R // 2, dtype=np.int32)
+    for prec, gemm in (("fp64", "tc_exact"), ("mixed", "tc3"), ("mixed", "tc2"), ("fp64", "cuda_cores"),
+                       ("mixed", "cuda_cores")):
+        t = time.perf_counter()
+        ns.restart_product(Zr, Vr, keep, 0, 1, prec, gemm)
+        out[f"restart_{prec}_{gemm}_s"] = time.perf_counter() - t
+    del Zr
     V, _ = np.linalg.qr(rng.standard_normal((n, 256)))
     for w in (2, 8):  # the merged [Q_j | Q_j+1] panel at d = 1 and d = 4
         W = rng.standard_normal((n, w))
-        for prec in ("fp64", "mixed"):
+        for prec in ("fp64_pairs", "fp64", "mixed"):
             t = time.perf_counter()
             ns.project(V, W, prec)
             out[f"project_w{w}_{prec}_s"] = time.perf_counter() - t

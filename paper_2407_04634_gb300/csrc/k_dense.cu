@@ -884,34 +884,36 @@ void make_F(const double* Rr, const double* Gam_last, const double* VZ, const in
 // CG / CGLS refinement helpers on row-major panels of width W (T = float for
 // the inner iterations, double for the outer residual correction)
 // ---------------------------------------------------------------------------
-// delta += alpha p (np rows) ; r -= alpha q (nr rows) ; rr_new[c] = sum_i r_i[c]^2
+// delta += alpha p (np rows) ; r -= alpha q (nr rows) ; rr_new[c] = sum_i r_i[c]^2.
+// Element-linear over the row-major panels, so every access is coalesced; W divides
+// the grid stride, so each thread always meets the same column c = threadIdx.x % W
+// and keeps one partial sum (FP32 over its few dozen elements, FP64 beyond).
 template <typename T, int W>
 __global__ void __launch_bounds__(kThreads) k_cg_update(T* delta, const T* p, int64_t np_, T* r, const T* q,
                                                         int64_t nr, const double* alpha, Red red, double* rr_new) {
-  __shared__ double red_s[(kThreads / 32) * W];
+  static_assert(kThreads % W == 0, "the column of an element must not depend on the grid stride");
+  __shared__ double red_s[kThreads];
   __shared__ double tot[W];
-  __shared__ T al[W];
-  if (threadIdx.x < W) al[threadIdx.x] = (T)alpha[threadIdx.x];
-  __syncthreads();
-  const int64_t nmax = np_ > nr ? np_ : nr;
-  double part[W];
-#pragma unroll
-  for (int c = 0; c < W; ++c) part[c] = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nmax; i += (int64_t)gridDim.x * blockDim.x) {
-    if (i < np_) {
-#pragma unroll
-      for (int c = 0; c < W; ++c) delta[i * W + c] = fma(al[c], p[i * W + c], delta[i * W + c]);
-    }
-    if (i < nr) {
-#pragma unroll
-      for (int c = 0; c < W; ++c) {
-        const T v = fma(-al[c], q[i * W + c], r[i * W + c]);
-        r[i * W + c] = v;
-        part[c] += (double)v * (double)v;
-      }
+  const int c = threadIdx.x % W;
+  const T al = (T)alpha[c];
+  const int64_t ep = np_ * W, er = nr * W, emax = ep > er ? ep : er;
+  T part = T(0);
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < emax; t += (int64_t)gridDim.x * blockDim.x) {
+    if (t < ep) delta[t] = fma(al, p[t], delta[t]);
+    if (t < er) {
+      const T v = fma(-al, q[t], r[t]);
+      r[t] = v;
+      part = fma(v, v, part);
     }
   }
-  block_sum<W>(part, red_s, tot);
+  red_s[threadIdx.x] = (double)part;
+  __syncthreads();
+  if (threadIdx.x < W) {
+    double sum = 0.0;
+    for (int j = threadIdx.x; j < kThreads; j += W) sum += red_s[j];
+    tot[threadIdx.x] = sum;
+  }
+  __syncthreads();
   if (threadIdx.x < W) red.part[(size_t)blockIdx.x * W + threadIdx.x] = tot[threadIdx.x];
   if (last_block_reduce(red.part, W, red.ticket, tot, red_s))
     if (threadIdx.x < W) rr_new[threadIdx.x] = tot[threadIdx.x];
@@ -920,8 +922,8 @@ __global__ void __launch_bounds__(kThreads) k_cg_update(T* delta, const T* p, in
 template <typename T, int W>
 void cg_update2(T* delta, const T* p, int64_t np_, T* r, const T* q, int64_t nr, const double* alpha, const Red& red,
                 double* rr_new, cudaStream_t s) {
-  k_cg_update<T, W><<<persistent_rows(np_ > nr ? np_ : nr), kThreads, 0, s>>>(delta, p, np_, r, q, nr, alpha, red,
-                                                                                rr_new);
+  k_cg_update<T, W><<<persistent_rows((np_ > nr ? np_ : nr) * W), kThreads, 0, s>>>(delta, p, np_, r, q, nr, alpha,
+                                                                                      red, rr_new);
 }
 
 // p = s + beta p
@@ -1020,41 +1022,63 @@ namespace ns {
 
 // ---------------------------------------------------------------------------
 // Gram matrix G = X^T X of an FP64 column-major n x N basis (upper-triangular
-// 32 x 32 tiles, split over row chunks; partials reduced in chunk order)
+// 32 x 32 tiles, split over row chunks; partials reduced in chunk order).  The
+// products run in compensated FP32 pairs (df_split / df_fma) on the FP32 pipe:
+// each staged FP64 element is split once into hi + lo words in shared memory, each
+// thread keeps 4 pair accumulators.  A pair add has relative error 2^-48 of its
+// running sum, so the pairs are flushed into FP64 accumulators every 1024 rows:
+// each pair sum stays short, and the FP64 sum of the flushed segments is as
+// accurate as a plain FP64 accumulation.
 // ---------------------------------------------------------------------------
 constexpr int kGT = 32;
 
 __global__ void __launch_bounds__(kThreads) k_gram_tiles(const double* __restrict__ X, int64_t n, int N,
                                                          int64_t rows_per_chunk, const int2* __restrict__ pairs,
                                                          double* part) {
-  __shared__ double xa[kGT][kGT + 1];
-  __shared__ double xb[kGT][kGT + 1];
+  __shared__ float2 xa[kGT][kGT + 1];
+  __shared__ float2 xb[kGT][kGT + 1];
   const int2 pr = pairs[blockIdx.x];
   const int ca = pr.x * kGT, cb = pr.y * kGT;
   const int64_t r0 = (int64_t)blockIdx.y * rows_per_chunk;
   int64_t r1 = r0 + rows_per_chunk;
   if (r1 > n) r1 = n;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  float sh[4] = {0.f, 0.f, 0.f, 0.f}, sl[4] = {0.f, 0.f, 0.f, 0.f};
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  int seg = 0;
   for (int64_t base = r0; base < r1; base += kGT) {
+    if (++seg == 32) {  // 1024 rows into FP64
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        acc[q] += (double)sh[q] + (double)sl[q];
+        sh[q] = sl[q] = 0.f;
+      }
+      seg = 0;
+    }
     __syncthreads();
     for (int t = threadIdx.x; t < kGT * kGT; t += blockDim.x) {
       const int r = t & 31, c = t >> 5;  // 32 consecutive rows of one column per warp
       const int64_t i = base + r;
-      xa[r][c] = (i < r1 && ca + c < N) ? X[(int64_t)(ca + c) * n + i] : 0.0;
-      xb[r][c] = (i < r1 && cb + c < N) ? X[(int64_t)(cb + c) * n + i] : 0.0;
+      float h, l;
+      df_split((i < r1 && ca + c < N) ? X[(int64_t)(ca + c) * n + i] : 0.0, h, l);
+      xa[r][c] = make_float2(h, l);
+      df_split((i < r1 && cb + c < N) ? X[(int64_t)(cb + c) * n + i] : 0.0, h, l);
+      xb[r][c] = make_float2(h, l);
     }
     __syncthreads();
-#pragma unroll 8
+#pragma unroll 4
     for (int r = 0; r < kGT; ++r) {
-      const double b = xb[r][tx];
+      const float2 b = xb[r][tx];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) acc[q] = fma(xa[r][ty + 8 * q], b, acc[q]);
+      for (int q = 0; q < 4; ++q) {
+        const float2 a = xa[r][ty + 8 * q];
+        df_fma(sh[q], sl[q], a.x, a.y, b.x, b.y);
+      }
     }
   }
   double* out = part + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * (kGT * kGT);
 #pragma unroll
-  for (int q = 0; q < 4; ++q) out[(ty + 8 * q) * kGT + tx] = acc[q];
+  for (int q = 0; q < 4; ++q) out[(ty + 8 * q) * kGT + tx] = acc[q] + ((double)sh[q] + (double)sl[q]);
 }
 
 __global__ void k_gram_reduce(const double* part, const int2* pairs, int npairs, int nchunks, int N, double* G) {
@@ -1099,45 +1123,64 @@ void gram64(const double* X, int64_t n, int N, double* G, double* part, cudaStre
 
 // ---------------------------------------------------------------------------
 // first-order symmetric (Loewdin) re-orthonormalization:
-//   Xout = X - 0.5 X E,  E = X^T X - I  (|E| small, so the product runs in FP32)
+//   Xout = X - 0.5 X E,  E = X^T X - I  (|E| small, so the product runs in FP32:
+//   its relative error ~1e-7 is an absolute ~1e-7 |E|, far below FP64 rounding)
+// One CTA: 64 rows x 64 output columns, K = N in chunks of 32, each thread a
+// 4 x 4 register tile.  blockIdx.x walks the column blocks, so the CTAs that read
+// the same 64-row strip of X run together and share it through L2.
 // ---------------------------------------------------------------------------
+constexpr int kLR = 64, kLC = 64, kLK = 32;
+
 __global__ void __launch_bounds__(kThreads) k_lowdin(const double* __restrict__ X, int64_t n, int N,
                                                      const double* __restrict__ G, double* __restrict__ Xout) {
-  __shared__ float xs[kGT][kGT + 1];
-  __shared__ float es[kGT][kGT + 1];
-  const int64_t i0 = (int64_t)blockIdx.x * kGT;
-  const int c0 = blockIdx.y * kGT;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  float acc[4] = {0.f, 0.f, 0.f, 0.f};
-  for (int k0 = 0; k0 < N; k0 += kGT) {
+  __shared__ float xs[kLK][kLR + 4];  // xs[k][row]
+  __shared__ float es[kLK][kLC + 4];  // es[k][col] = E(k0 + k, c0 + col)
+  const int c0 = blockIdx.x * kLC;
+  const int64_t i0 = (int64_t)blockIdx.y * kLR;
+  const int tr = threadIdx.x >> 4, tc = threadIdx.x & 15;  // rows tr*4.., columns tc*4..
+  float acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+  for (int k0 = 0; k0 < N; k0 += kLK) {
     __syncthreads();
-    for (int t = threadIdx.x; t < kGT * kGT; t += blockDim.x) {
-      const int r = t & 31, c = t >> 5;
+    for (int t = threadIdx.x; t < kLK * kLR; t += blockDim.x) {
+      const int r = t % kLR, k = t / kLR;  // consecutive rows of one column: coalesced
       const int64_t i = i0 + r;
-      xs[r][c] = (i < n && k0 + c < N) ? (float)X[(int64_t)(k0 + c) * n + i] : 0.f;
-      const int kk = k0 + r, j = c0 + c;  // es[r][c] = E(k0 + r, c0 + c)
-      es[r][c] = (kk < N && j < N) ? (float)(G[(int64_t)j * N + kk] - (kk == j ? 1.0 : 0.0)) : 0.f;
+      xs[k][r] = (i < n && k0 + k < N) ? (float)X[(int64_t)(k0 + k) * n + i] : 0.f;
+    }
+    for (int t = threadIdx.x; t < kLK * kLC; t += blockDim.x) {
+      const int k = t % kLK, c = t / kLK;  // E is symmetric: E(kk, j) = G[j * N + kk] - delta
+      const int kk = k0 + k, j = c0 + c;
+      es[k][c] = (kk < N && j < N) ? (float)(G[(int64_t)j * N + kk] - (kk == j ? 1.0 : 0.0)) : 0.f;
     }
     __syncthreads();
 #pragma unroll 8
-    for (int k = 0; k < kGT; ++k) {
-      const float e = es[k][tx];
+    for (int k = 0; k < kLK; ++k) {
+      const float4 xv = *reinterpret_cast<const float4*>(&xs[k][tr * 4]);
+      const float4 ev = *reinterpret_cast<const float4*>(&es[k][tc * 4]);
+      const float xa[4] = {xv.x, xv.y, xv.z, xv.w}, eb[4] = {ev.x, ev.y, ev.z, ev.w};
 #pragma unroll
-      for (int q = 0; q < 4; ++q) acc[q] = fmaf(xs[ty + 8 * q][k], e, acc[q]);
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(xa[a], eb[b], acc[a][b]);
     }
   }
-  const int j = c0 + tx;
-  if (j < N) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int64_t i = i0 + ty + 8 * q;
-      if (i < n) Xout[(int64_t)j * n + i] = X[(int64_t)j * n + i] - 0.5 * (double)acc[q];
+  for (int b = 0; b < 4; ++b) {
+    const int j = c0 + tc * 4 + b;
+    if (j >= N) continue;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const int64_t i = i0 + tr * 4 + a;
+      if (i < n) Xout[(int64_t)j * n + i] = X[(int64_t)j * n + i] - 0.5 * (double)acc[a][b];
     }
   }
 }
 
 void lowdin_update(const double* X, int64_t n, int N, const double* G, double* Xout, cudaStream_t s) {
-  dim3 grid(ceil_div(n, kGT), ceil_div(N, kGT));
+  dim3 grid(ceil_div(N, kLC), ceil_div(n, kLR));
   k_lowdin<<<grid, kThreads, 0, s>>>(X, n, N, G, Xout);
 }
 

@@ -26,40 +26,6 @@
 namespace ns {
 namespace {
 
-// exact split x = hi + lo + r, |r| <= 2^-48 |x|; |x| < 2^-126 gives 0 (such entries
-// contribute below 2^-126 to a product of unit vectors)
-__device__ __forceinline__ void df_split(double x, float& hi, float& lo) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const unsigned h32 = (unsigned)(b >> 32), l32 = (unsigned)b;
-  const int E = (int)((h32 >> 20) & 0x7FFu);
-  const unsigned sgn = h32 & 0x80000000u;
-  const int e32 = E - 896;  // FP32 biased exponent of x
-  if (e32 <= 0 || e32 >= 255) {
-    hi = e32 <= 0 ? 0.f : __uint_as_float(sgn | 0x7F800000u);
-    lo = 0.f;
-    return;
-  }
-  hi = __uint_as_float(sgn | ((unsigned)e32 << 23) | ((h32 & 0xFFFFFu) << 3) | (l32 >> 29));
-  const unsigned r = l32 & 0x1FFFFFFFu;  // the remaining 29 significand bits: r 2^(E - 1075)
-  const int el = E - 1075 + 127;
-  const float sc = el >= 1 ? __uint_as_float((unsigned)el << 23) : 0.f;
-  lo = __uint_as_float(__float_as_uint(__fmul_rn(__uint2float_rn(r), sc)) | sgn);
-}
-
-// (sh, sl) += (ah + al)(bh + bl)
-__device__ __forceinline__ void df_fma(float& sh, float& sl, float ah, float al, float bh, float bl) {
-  const float p = __fmul_rn(ah, bh);
-  float e = __fmaf_rn(ah, bh, -p);  // exact: ah bh = p + e
-  e = __fmaf_rn(ah, bl, e);
-  e = __fmaf_rn(al, bh, e);
-  const float s = __fadd_rn(sh, p);  // TwoSum(sh, p) = (s, t)
-  const float v = __fsub_rn(s, sh);
-  float t = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, v)), __fsub_rn(p, v));
-  t = __fadd_rn(t, __fadd_rn(sl, e));
-  sh = __fadd_rn(s, t);  // FastTwoSum(s, t)
-  sl = __fsub_rn(t, __fsub_rn(sh, s));
-}
-
 template <int W>
 __device__ __forceinline__ void load_w2(const double* Wp, const double* Wp2, int64_t ldw, int64_t i, double (&w)[W]) {
   if (Wp2 == nullptr) {

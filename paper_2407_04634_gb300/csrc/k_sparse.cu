@@ -149,6 +149,59 @@ __global__ void __launch_bounds__(kThreads) k_spmm_coldot(Csr<T> M, const T* __r
   }
 }
 
+// The same product for wide panels (the refinement's 16 columns): D lanes per row,
+// lane c owning column c, so a gathered row of the panel is one coalesced D-wide
+// access and no cross-lane reduction is needed.  The nonzeros of a row are walked
+// four at a time (their column indices, then the four gathers, are in flight
+// together).  Each thread keeps its column's dot product (FP32 partials for FP32
+// data, FP64 for FP64), reduced per column in shared memory and across blocks.
+template <typename T, int D>
+__global__ void __launch_bounds__(kThreads) k_spmm_panel(Csr<T> M, const T* __restrict__ v, T* __restrict__ y,
+                                                         const T* __restrict__ w, int sq, Red red, double* dots) {
+  static_assert(kThreads % D == 0 && 32 % D == 0, "D lanes per row within a warp");
+  constexpr int RPB = kThreads / D;
+  __shared__ double red_s[kThreads];
+  __shared__ double tot[D];
+  const int c = threadIdx.x % D, grp = threadIdx.x / D;
+  const T* wv = w ? w : v;
+  T part = T(0);
+  for (int64_t tile = blockIdx.x; tile * RPB < M.nrows; tile += gridDim.x) {
+    const int64_t row = tile * RPB + grp;
+    if (row < M.nrows) {
+      const int64_t s = __ldg(M.rowptr + row), e = __ldg(M.rowptr + row + 1);
+      T acc = T(0);
+      int64_t k = s;
+      for (; k + 4 <= e; k += 4) {
+        int col[4];
+        T a[4], x[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          col[u] = __ldg(M.col + k + u);
+          a[u] = __ldg(M.val + k + u);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) x[u] = __ldg(v + (int64_t)col[u] * D + c);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc = fma(a[u], x[u], acc);
+      }
+      for (; k < e; ++k) acc = fma(__ldg(M.val + k), __ldg(v + (int64_t)__ldg(M.col + k) * D + c), acc);
+      y[row * D + c] = acc;
+      part = sq ? fma(acc, acc, part) : fma(__ldg(wv + row * D + c), acc, part);
+    }
+  }
+  red_s[threadIdx.x] = (double)part;
+  __syncthreads();
+  if (threadIdx.x < D) {
+    double sum = 0.0;
+    for (int j = threadIdx.x; j < kThreads; j += D) sum += red_s[j];
+    tot[threadIdx.x] = sum;
+  }
+  __syncthreads();
+  if (threadIdx.x < D) red.part[(size_t)blockIdx.x * D + threadIdx.x] = tot[threadIdx.x];
+  if (last_block_reduce(red.part, D, red.ticket, tot, red_s))
+    if (threadIdx.x < D) dots[threadIdx.x] = tot[threadIdx.x];
+}
+
 // ---------------------------------------------------------------------------
 // TMA-staged schedule (lanes code kSchedTma): a CTA takes kTmaRows consecutive
 // rows per tile.  One thread copies the tile's col/val segment (the 16-byte
@@ -455,6 +508,10 @@ void spmm_lanczos(const Csr<T>& M, const T* v, const StepOps<T>& op, const Red& 
 template <typename T, int D>
 void spmm_coldot(const Csr<T>& M, const T* v, T* y, const T* w, int sq, double* dots, const Red& red,
                  cudaStream_t s) {
+  if constexpr (D == 16) {  // wide refinement panels: a lane per column
+    k_spmm_panel<T, D><<<persistent_grid(M.nrows, D), kThreads, 0, s>>>(M, v, y, w, sq, red, dots);
+    return;
+  }
   const int V = M.V == kSchedTma ? 1 : M.V;  // the staged schedule serves the step products only
   const int grid = persistent_grid(M.nrows, V);
 #define CALL(VV) k_spmm_coldot<T, D, VV><<<grid, kThreads, 0, s>>>(M, v, y, w, sq, red, dots)

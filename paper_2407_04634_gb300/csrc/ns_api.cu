@@ -1017,8 +1017,11 @@ RefineOut refine(ns_handle* h, double* X, int64_t N, double normA, const ns_opts
     ck(cudaStreamSynchronize(s), "sync");
     return *nact_h;
   };
+  const bool dbg = getenv("NS_DEBUG") != nullptr;
   for (int64_t c0 = 0; c0 < N; c0 += W) {
     const int w = (int)std::min<int64_t>(W, N - c0);
+    const auto tc0 = std::chrono::steady_clock::now();
+    int rounds = 0, inner_total = 0;
     cols_to_panel_w<W>(X, (int)c0, w, n, bx.as<double>(), s);
     stream_work((double)n, 16.0, 0.0);
     std::vector<unsigned char> a0(W, 0);
@@ -1082,6 +1085,8 @@ RefineOut refine(ns_handle* h, double* X, int64_t N, double normA, const ns_opts
         }
       }
       out.iters_max = std::max<int64_t>(out.iters_max, it + 1);
+      rounds += 1;
+      inner_total += it + 1;
       sub_correction<W>(bx.as<double>(), bd.as<float>(), n, s);  // x <- x - delta in FP64
       stream_work((double)n, 20.0, 1.0);
       h->launches += 1;
@@ -1095,6 +1100,9 @@ RefineOut refine(ns_handle* h, double* X, int64_t N, double normA, const ns_opts
     ck(cudaStreamSynchronize(s), "sync");
     ck_launch("refine");
     h->launches += 2;
+    if (dbg)
+      fprintf(stderr, "[ns] refine chunk %lld: %d rounds, %d inner iterations, %.2f ms\n", (long long)c0, rounds,
+              inner_total, std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tc0).count());
     for (int c = 0; c < w; ++c) {
       const double rel = std::sqrt(std::max(rr_h[c], 0.0)) / std::max(normA, 1e-300);
       out.resid_max = std::max(out.resid_max, rel);

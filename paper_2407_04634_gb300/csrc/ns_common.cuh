@@ -126,9 +126,12 @@ __device__ inline void block_sum_t(const T (&v)[NV], double* red, double* out) {
 // "Last block" protocol: each block writes NV partial sums to part[block*NV+k];
 // the block that arrives last (atomic ticket) sums all partials in block order
 // and returns true with the totals in tot[0..NV) (shared memory).  The ticket
-// counter is reset by the last block, so the kernel can be relaunched.
-__device__ inline bool last_block_reduce(double* part, int NV, unsigned* ticket, double* tot,
-                                         double* red) {
+// counter is reset by the last block, so the kernel can be relaunched.  In the last
+// block warp w sums the values k = w, w + nwarps, ...: lane l adds blocks l, l + 32,
+// ... in order, then a fixed butterfly combines the lanes, so the result does not
+// depend on timing; there is one barrier however large NV is.
+__device__ inline bool last_block_reduce(double* part, int NV, unsigned* ticket, double* tot, double* red) {
+  (void)red;
   __shared__ bool am_last;
   __threadfence();
   __syncthreads();
@@ -140,20 +143,14 @@ __device__ inline bool last_block_reduce(double* part, int NV, unsigned* ticket,
   if (!am_last) return false;
   __threadfence();
   const int nw = blockDim.x >> 5, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int k = 0; k < NV; ++k) {
+  for (int k = warp; k < NV; k += nw) {
     double s = 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) s += __ldcg(part + (size_t)b * NV + k);
+    for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(part + (size_t)b * NV + k);
     s = warp_sum(s);
-    if (lane == 0) red[warp] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double t = 0.0;
-      for (int w = 0; w < nw; ++w) t += red[w];
-      tot[k] = t;
-    }
-    __syncthreads();
+    if (lane == 0) tot[k] = s;
   }
   if (threadIdx.x == 0) *ticket = 0u;
+  __syncthreads();
   return true;
 }
 
@@ -263,6 +260,47 @@ __host__ __device__ inline void sv_minmax(const double* M, int d, double* smax, 
   }
   *smax = sqrt(fmax(mx, 0.0));
   *smin = sqrt(fmax(mn, 0.0));
+}
+
+// ---------------------------------------------------------------------------
+// compensated FP32-pair arithmetic for FP64 data (the FP64 path's Gram-Schmidt and
+// Gram products run on the FP32 pipe): an exact split of an FP64 value into two
+// FP32 words, and a multiply-accumulate into an unevaluated pair (TwoProd through
+// the FMA residual, TwoSum of Knuth, FastTwoSum of Dekker).  Explicit
+// round-to-nearest intrinsics keep the compiler from contracting the transformations.
+// ---------------------------------------------------------------------------
+// exact split x = hi + lo + r, |r| <= 2^-48 |x|; |x| < 2^-126 gives 0 (such entries
+// contribute below 2^-126 to a product of unit vectors)
+__device__ __forceinline__ void df_split(double x, float& hi, float& lo) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned h32 = (unsigned)(b >> 32), l32 = (unsigned)b;
+  const int E = (int)((h32 >> 20) & 0x7FFu);
+  const unsigned sgn = h32 & 0x80000000u;
+  const int e32 = E - 896;  // FP32 biased exponent of x
+  if (e32 <= 0 || e32 >= 255) {
+    hi = e32 <= 0 ? 0.f : __uint_as_float(sgn | 0x7F800000u);
+    lo = 0.f;
+    return;
+  }
+  hi = __uint_as_float(sgn | ((unsigned)e32 << 23) | ((h32 & 0xFFFFFu) << 3) | (l32 >> 29));
+  const unsigned r = l32 & 0x1FFFFFFFu;  // the remaining 29 significand bits: r 2^(E - 1075)
+  const int el = E - 1075 + 127;
+  const float sc = el >= 1 ? __uint_as_float((unsigned)el << 23) : 0.f;
+  lo = __uint_as_float(__float_as_uint(__fmul_rn(__uint2float_rn(r), sc)) | sgn);
+}
+
+// (sh, sl) += (ah + al)(bh + bl)
+__device__ __forceinline__ void df_fma(float& sh, float& sl, float ah, float al, float bh, float bl) {
+  const float p = __fmul_rn(ah, bh);
+  float e = __fmaf_rn(ah, bh, -p);  // exact: ah bh = p + e
+  e = __fmaf_rn(ah, bl, e);
+  e = __fmaf_rn(al, bh, e);
+  const float s = __fadd_rn(sh, p);  // TwoSum(sh, p) = (s, t)
+  const float v = __fsub_rn(s, sh);
+  float t = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, v)), __fsub_rn(p, v));
+  t = __fadd_rn(t, __fadd_rn(sl, e));
+  sh = __fadd_rn(s, t);  // FastTwoSum(s, t)
+  sl = __fsub_rn(t, __fsub_rn(sh, s));
 }
 
 // pivot test shared by the last blocks of the CholQR kernels: Cholesky of the d x d
