@@ -588,6 +588,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision sub-record")
+    ap.add_argument("--fp64-products", type=int, default=0, choices=[0, 1],
+                    help="FP64 path's Gram-Schmidt products: 0 compensated FP32 pairs (default), 1 FP64 FMA")
     ap.add_argument("--scale", type=float, default=1.0, help="workload scale (< 1 is for profiling only)")
     ap.add_argument("--kernel-probe", action="store_true", help="launch a few hot kernels, no bench line")
     ap.add_argument("--loop-sample", type=int, default=32,
@@ -638,7 +640,8 @@ def main():
         and CUDA events on the library stream; returns (ms max over ranks, units, results,
         profile of the last solve, clocks)."""
         def one_step(profile=0):
-            return h.solve(p["d"], p["restart"], p["tol"], check=False, precision=precision, profile=profile)
+            return h.solve(p["d"], p["restart"], p["tol"], check=False, precision=precision, profile=profile,
+                           fp64_products=args.fp64_products)
         for _ in range(args.warmup):
             one_step()
         torch.cuda.synchronize()
@@ -673,8 +676,11 @@ def main():
         base = {"kernel": c["name"], "traffic": traffic, "bytes_per_launch": c["bytes_per_launch"],
                 "flops_per_launch": c["flops_per_launch"], "ms_per_launch": c["ms_per_launch"],
                 "launches": c["launches"], "sampled": c["sampled"]}
-        if c["name"] != "b_apply" and precision == "fp64" and c["flops_per_launch"] > 0:
-            # the FP64 path's dense products have more flops per byte than the FP64 pipe's ridge
+        fp64_pipe = {"projected_eig"} | ({"cgs2_project"} if args.fp64_products == 1 else set())
+        if precision == "fp64" and c["name"] in fp64_pipe and c["flops_per_launch"] > 0:
+            # kernel classes that run on the FP64 pipe (above its ridge point): the projected
+            # eigenproblem, and the Gram-Schmidt products when FP64 FMA is selected; the
+            # default FP64 products run in compensated FP32 pairs and are bound by HBM
             ach = c["flops_per_launch"] / (c["ms_per_launch"] / 1e3) / 1e12
             fp64_peak = at_clock(fp64_peak_raw, fp64_mhz, clk.get("sm_mhz"))
             return {**base, "bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",

@@ -227,9 +227,12 @@ ns_status ns_start_block(const ns_handle* h, int d, double* Omega);
  *   precision  : NS_FP64 or NS_MIXED (X rounded to FP32, FP32 arithmetic with
  *                FP32 values of A; Y returned widened to FP64)
  *   schedule   : SpMM schedule: -1 the library's default for this matrix, 1, 2, 4,
- *                8, 16 or 32 threads per CSR row, or 64 the TMA-staged schedule
+ *                8, 16 or 32 threads per CSR row, 64 the TMA-staged schedule
  *                (each CTA bulk-copies a 256-row tile's col/val into shared memory,
- *                a thread per row); anything else gives NS_ERR_INVALID_ARG.
+ *                a thread per row), or 128 the sliced-ELLPACK copy built by ns_create
+ *                (slices of 32 rows, a warp per slice, a lane per row; built when its
+ *                padding stays below 30% of nnz, else NS_ERR_INVALID_ARG); anything
+ *                else gives NS_ERR_INVALID_ARG.
  * A bounded device wait that expires gives NS_ERR_TIMEOUT (no hang). */
 ns_status ns_apply_B(ns_handle* h, int d, const double* X, double* Y, double eps,
                      int precision, int on_device, int schedule);

@@ -326,10 +326,19 @@ static int64_t dots_rows_per_chunk(int64_t n) {
 
 template <typename T, int W>
 void proj_dots(const VParts<T>& V, const T* Wp, const T* Wp2, int64_t ldw, int64_t n, double* C, double* part,
-               cudaStream_t s) {
+               cudaStream_t s, int64_t rows_per_chunk) {
   const int K = V.kx + V.kz;
   if (K == 0) return;
-  const int64_t rpc = dots_rows_per_chunk(n);
+  int64_t rpc = dots_rows_per_chunk(n);
+  if (rows_per_chunk == kDotsAutoChunks) {
+    // enough (chunk, column tile) CTAs for 8 per SM, each chunk >= kDotsMinChunk rows
+    const int kt = (std::is_same<T, double>::value && V.df) ? (W >= 16 ? 2 : W >= 8 ? 4 : 8) : dots_kt<W>();
+    const int64_t tiles = ceil_div(V.kx, kt) + ceil_div(V.kz, kt);
+    const int64_t want = (kMaxBlocks + tiles - 1) / tiles;
+    int64_t r = (n + want - 1) / want;
+    r = (r + kThreads - 1) / kThreads * kThreads;
+    rpc = std::min<int64_t>(rpc, std::max<int64_t>(r, kDotsMinChunk));
+  }
   if constexpr (std::is_same<T, double>::value) {
     if (V.df) {
       proj_dots_df<W>(V, Wp, Wp2, ldw, n, C, part, rpc, s);
@@ -469,7 +478,7 @@ cudaError_t proj_update_reserve_smem(size_t bytes) {
 
 #define NS_INST_PROJ(T, W)                                                                                     \
   template void proj_dots<T, W>(const VParts<T>&, const T*, const T*, int64_t, int64_t, double*, double*,       \
-                                cudaStream_t);                                                                 \
+                                cudaStream_t, int64_t);                                                        \
   template cudaError_t proj_update<T, W>(const VParts<T>&, const double*, T*, T*, int64_t, int64_t, int,        \
                                          double*, double*, unsigned*, const Red&, cudaStream_t);              \
   template cudaError_t proj_update_reserve_smem<T, W>(size_t);

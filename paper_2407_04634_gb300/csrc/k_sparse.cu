@@ -17,6 +17,10 @@ int choose_lanes(int64_t nrows, int64_t nnz) {
 // ---------------------------------------------------------------------------
 // row segment of a CSR product, V lanes per row, D columns of the dense operand
 // ---------------------------------------------------------------------------
+// The row's nonzeros are taken four per lane at a time: the four column indices and
+// values are loaded together, then the four gathered rows of v, so each lane keeps
+// four dependent gathers in flight instead of one (the rows of a Laplacian or an
+// incidence matrix hold 2-12 entries, so most rows finish in one or two rounds).
 template <typename T, int D, int V>
 __device__ __forceinline__ void row_product(const Csr<T>& M, const T* __restrict__ v, int64_t row, int lane,
                                             T (&acc)[D]) {
@@ -24,13 +28,46 @@ __device__ __forceinline__ void row_product(const Csr<T>& M, const T* __restrict
   for (int q = 0; q < D; ++q) acc[q] = T(0);
   if (row < M.nrows) {
     const int64_t s = __ldg(M.rowptr + row), e = __ldg(M.rowptr + row + 1);
-    for (int64_t k = s + lane; k < e; k += V) {
-      const T a = __ldg(M.val + k);
-      const int c = __ldg(M.col + k);
-      T xv[D];
-      load_row<T, D>(v + (int64_t)c * D, xv);
+    int64_t k = s + lane;
+    for (; k + 3 * V < e; k += 4 * V) {
+      int c[4];
+      T a[4];
 #pragma unroll
-      for (int q = 0; q < D; ++q) acc[q] = fma(a, xv[q], acc[q]);
+      for (int u = 0; u < 4; ++u) {
+        c[u] = __ldg(M.col + k + u * V);
+        a[u] = __ldg(M.val + k + u * V);
+      }
+      T xv[4][D];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) load_row<T, D>(v + (int64_t)c[u] * D, xv[u]);
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int q = 0; q < D; ++q) acc[q] = fma(a[u], xv[u][q], acc[q]);
+    }
+    if (k < e) {  // the last one to three entries of this lane, predicated
+      int c[3];
+      T a[3];
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        const bool ok = k + u * V < e;
+        c[u] = ok ? __ldg(M.col + k + u * V) : 0;
+        a[u] = ok ? __ldg(M.val + k + u * V) : T(0);
+      }
+      T xv[3][D];
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        if (k + u * V < e) {
+          load_row<T, D>(v + (int64_t)c[u] * D, xv[u]);
+        } else {
+#pragma unroll
+          for (int q = 0; q < D; ++q) xv[u][q] = T(0);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 3; ++u)
+#pragma unroll
+        for (int q = 0; q < D; ++q) acc[q] = fma(a[u], xv[u][q], acc[q]);
     }
   }
   if constexpr (V > 1) {
@@ -110,6 +147,175 @@ __global__ void __launch_bounds__(kThreads) k_spmm_lanczos(Csr<T> M, const T* __
       *op.xi_norm = sym_norm2(X, D);
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// Sliced ELLPACK schedule (code kSchedSell): a warp takes a slice of kSellC
+// consecutive rows, lane l its row kSellC s + l.  Entry j of all the slice's rows
+// is one contiguous kSellC-wide run of col / val, so every warp load of the
+// structure is a single coalesced access; only the gathers of v are scattered.
+// Four entries per lane are in flight at a time.
+// ---------------------------------------------------------------------------
+template <typename T, int D>
+__device__ __forceinline__ void sell_row(const Csr<T>& M, const T* __restrict__ v, int64_t slice, int lane,
+                                         T (&acc)[D]) {
+#pragma unroll
+  for (int q = 0; q < D; ++q) acc[q] = T(0);
+  const int64_t p0 = __ldg(M.sptr + slice);
+  const int64_t len = (__ldg(M.sptr + slice + 1) - p0) / kSellC;
+  const int* cp = M.scol + p0 + lane;
+  const T* vp = M.sval + p0 + lane;
+  int64_t j = 0;
+  for (; j + 4 <= len; j += 4) {
+    int c[4];
+    T a[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      c[u] = __ldg(cp + (j + u) * kSellC);
+      a[u] = __ldg(vp + (j + u) * kSellC);
+    }
+    T xv[4][D];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) load_row<T, D>(v + (int64_t)c[u] * D, xv[u]);
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int q = 0; q < D; ++q) acc[q] = fma(a[u], xv[u][q], acc[q]);
+  }
+  for (; j < len; ++j) {
+    const int c = __ldg(cp + j * kSellC);
+    const T a = __ldg(vp + j * kSellC);
+    T xv[D];
+    load_row<T, D>(v + (int64_t)c * D, xv);
+#pragma unroll
+    for (int q = 0; q < D; ++q) acc[q] = fma(a, xv[q], acc[q]);
+  }
+}
+
+template <typename T, int D>
+__global__ void __launch_bounds__(kThreads) k_spmm_plain_sell(Csr<T> M, const T* __restrict__ v, T* __restrict__ y) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nslices = (M.nrows + kSellC - 1) / kSellC;
+  const int64_t wid = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5, nw = ((int64_t)gridDim.x * kThreads) >> 5;
+  for (int64_t sl = wid; sl < nslices; sl += nw) {
+    T acc[D];
+    sell_row<T, D>(M, v, sl, lane, acc);
+    const int64_t row = sl * kSellC + lane;
+    if (row < M.nrows) store_row<T, D>(y + row * D, acc);
+  }
+}
+
+// the Lanczos step product of k_spmm_lanczos on the sliced layout (same epilogue)
+template <typename T, int D>
+__global__ void __launch_bounds__(kThreads) k_spmm_lanczos_sell(Csr<T> M, const T* __restrict__ v, StepOps<T> op,
+                                                                Red red) {
+  constexpr int NP = D * D;
+  __shared__ double red_s[(kThreads / 32) * NP];
+  __shared__ double tot[NP];
+  __shared__ T g_s[D * D];
+  if (threadIdx.x < D * D) g_s[threadIdx.x] = op.gprev ? (T)op.gprev[threadIdx.x] : T(0);
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const bool has_prev = op.qprev != nullptr;
+  T part[NP];
+#pragma unroll
+  for (int k = 0; k < NP; ++k) part[k] = T(0);
+  const int64_t nslices = (M.nrows + kSellC - 1) / kSellC;
+  const int64_t wid = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5, nw = ((int64_t)gridDim.x * kThreads) >> 5;
+  for (int64_t sl = wid; sl < nslices; sl += nw) {
+    const int64_t row = sl * kSellC + lane;
+    const bool lead = row < M.nrows;
+    T xi[D], qp[D];
+    T de = T(0);
+    if (lead) {  // epilogue operands first: they do not depend on the gathers
+      load_row<T, D>(op.x + row * D, xi);
+      de = (T)op.eps * __ldg(op.Dv + row);
+      if (has_prev) load_row<T, D>(op.qprev + row * D, qp);
+    }
+    T acc[D];
+    sell_row<T, D>(M, v, sl, lane, acc);
+    if (lead) {
+#pragma unroll
+      for (int q = 0; q < D; ++q) acc[q] = fma(de, xi[q], acc[q]);
+      if (has_prev) {
+#pragma unroll
+        for (int r = 0; r < D; ++r)
+#pragma unroll
+          for (int c = 0; c < D; ++c) acc[r] = fma(-qp[c], g_s[r * D + c], acc[r]);
+      }
+      store_row<T, D>(op.out + row * D, acc);
+#pragma unroll
+      for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int b = 0; b < D; ++b) part[a * D + b] = fma(xi[a], acc[b], part[a * D + b]);
+    }
+  }
+  double pd[NP];
+#pragma unroll
+  for (int k = 0; k < NP; ++k) pd[k] = (double)part[k];
+  block_sum<NP>(pd, red_s, tot);
+  if (threadIdx.x < NP) red.part[(size_t)blockIdx.x * NP + threadIdx.x] = tot[threadIdx.x];
+  if (last_block_reduce(red.part, NP, red.ticket, tot, red_s)) {
+    if (threadIdx.x == 0) {
+      double X[D * D];
+      for (int a = 0; a < D; ++a)
+        for (int b = 0; b < D; ++b) X[a * D + b] = 0.5 * (tot[a * D + b] + tot[b * D + a]);
+      for (int k = 0; k < D * D; ++k) op.xi[k] = X[k];
+      *op.xi_norm = sym_norm2(X, D);
+    }
+  }
+}
+
+// slice lengths: the longest row of each slice
+__global__ void k_sell_len(const int64_t* __restrict__ rowptr, int64_t nrows, int* __restrict__ len) {
+  const int64_t nslices = (nrows + kSellC - 1) / kSellC;
+  for (int64_t sl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; sl < nslices;
+       sl += (int64_t)gridDim.x * blockDim.x) {
+    int64_t mx = 0;
+    for (int l = 0; l < kSellC; ++l) {
+      const int64_t r = sl * kSellC + l;
+      if (r < nrows) mx = max(mx, rowptr[r + 1] - rowptr[r]);
+    }
+    len[sl] = (int)mx;
+  }
+}
+
+// padded column-major copy: lane l of slice s writes entry j of row kSellC s + l
+__global__ void k_sell_fill(const int64_t* __restrict__ rowptr, const int* __restrict__ col,
+                            const double* __restrict__ val, int64_t nrows, const int64_t* __restrict__ sptr,
+                            int* __restrict__ scol, double* __restrict__ sval) {
+  const int64_t nslices = (nrows + kSellC - 1) / kSellC;
+  const int64_t total = nslices * kSellC;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t sl = t / kSellC, r = t;
+    const int l = (int)(t % kSellC);
+    const int64_t p0 = sptr[sl], len = (sptr[sl + 1] - p0) / kSellC;
+    const int64_t s = r < nrows ? rowptr[r] : 0, e = r < nrows ? rowptr[r + 1] : 0;
+    for (int64_t j = 0; j < len; ++j) {
+      const bool real = s + j < e;
+      scol[p0 + j * kSellC + l] = real ? col[s + j] : 0;
+      sval[p0 + j * kSellC + l] = real ? val[s + j] : 0.0;
+    }
+  }
+}
+
+void sell_lengths(const int64_t* rowptr, int64_t nrows, int* slice_len, cudaStream_t s) {
+  const int64_t nslices = (nrows + kSellC - 1) / kSellC;
+  const int g = (int)std::max<int64_t>(1, std::min<int64_t>((nslices + 255) / 256, 152 * 16));
+  k_sell_len<<<g, 256, 0, s>>>(rowptr, nrows, slice_len);
+}
+
+void sell_fill(const int64_t* rowptr, const int* col, const double* val, int64_t nrows, const int64_t* sptr,
+               int* scol, double* sval, cudaStream_t s) {
+  const int64_t total = (nrows + kSellC - 1) / kSellC * kSellC;
+  const int g = (int)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 152 * 16));
+  k_sell_fill<<<g, 256, 0, s>>>(rowptr, col, val, nrows, sptr, scol, sval);
+}
+
+static int sell_grid(int64_t nrows) {
+  const int64_t nslices = (nrows + kSellC - 1) / kSellC;
+  const int64_t blocks = (nslices + (kThreads / 32) - 1) / (kThreads / 32);
+  return (int)std::max<int64_t>(1, std::min<int64_t>(blocks, kMaxBlocks));
 }
 
 // y = M v and per-column dots sum_i w_i[c] y_i[c] (w defaults to the rows of v) or
@@ -478,6 +684,10 @@ unsigned spmm_wait_timeouts(bool clear) {
 template <typename T, int D>
 void spmm_plain(const Csr<T>& M, const T* v, T* y, cudaStream_t s) {
   if (M.nrows == 0) return;
+  if (M.V == kSchedSell && M.sptr) {
+    k_spmm_plain_sell<T, D><<<sell_grid(M.nrows), kThreads, 0, s>>>(M, v, y);
+    return;
+  }
   if (M.V == kSchedTma) {
     launch_tma<T, D, false>(M, v, StepOps<T>{}, y, Red{}, s);
     return;
@@ -495,6 +705,10 @@ static int persistent_grid(int64_t nrows, int V) {
 
 template <typename T, int D>
 void spmm_lanczos(const Csr<T>& M, const T* v, const StepOps<T>& op, const Red& red, cudaStream_t s) {
+  if (M.V == kSchedSell && M.sptr) {
+    k_spmm_lanczos_sell<T, D><<<sell_grid(M.nrows), kThreads, 0, s>>>(M, v, op, red);
+    return;
+  }
   if (M.V == kSchedTma) {
     launch_tma<T, D, true>(M, v, op, nullptr, red, s);
     return;
@@ -512,7 +726,7 @@ void spmm_coldot(const Csr<T>& M, const T* v, T* y, const T* w, int sq, double* 
     k_spmm_panel<T, D><<<persistent_grid(M.nrows, D), kThreads, 0, s>>>(M, v, y, w, sq, red, dots);
     return;
   }
-  const int V = M.V == kSchedTma ? 1 : M.V;  // the staged schedule serves the step products only
+  const int V = (M.V == kSchedTma || M.V == kSchedSell) ? 1 : M.V;  // those serve the step products only
   const int grid = persistent_grid(M.nrows, V);
 #define CALL(VV) k_spmm_coldot<T, D, VV><<<grid, kThreads, 0, s>>>(M, v, y, w, sq, red, dots)
   NS_LANES_SWITCH(V, CALL)
@@ -531,7 +745,8 @@ int tune_lanes(Csr<T> M, const T* v, T* y, cudaStream_t s) {
   cudaEventCreate(&e1);
   int best = M.V;
   float best_ms = 1e30f;
-  for (int V : {kSchedTma, 1, 2, 4, 8, 16}) {
+  for (int V : {kSchedSell, kSchedTma, 1, 2, 4, 8, 16}) {
+    if (V == kSchedSell && !M.sptr) continue;
     M.V = V;
     spmm_plain<T, D>(M, v, y, s);
     cudaEventRecord(e0, s);

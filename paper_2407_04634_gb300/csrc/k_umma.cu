@@ -544,6 +544,10 @@ static cudaError_t launch_umma(const float* Z, int R, int64_t n, const uint4* im
   if (smem > cap_smem) smem = std::max(need, cap_smem);
   cudaError_t e = ensure_smem_limit(fn, smem);
   if (e != cudaSuccess) return e;
+  // the whole unified L1 / shared array as shared memory, so that the occupancy query
+  // (and the launch) see the largest carveout
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  if (e != cudaSuccess) return e;
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

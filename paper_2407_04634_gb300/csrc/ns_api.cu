@@ -118,6 +118,14 @@ struct ns_handle {
   double* D64 = nullptr;
   float* D32 = nullptr;
   double normA1 = 0.0, normAinf = 0.0;
+  // sliced-ELLPACK copies of A and A^T (null when the padding would exceed 30%)
+  struct Sell {
+    int64_t* sptr = nullptr;
+    int* scol = nullptr;
+    double* sval = nullptr;
+    float* sval32 = nullptr;
+    int64_t entries = 0;
+  } sell_A, sell_At;
   // result
   bool solved = false;
   int64_t N = 0;
@@ -219,13 +227,41 @@ struct Prec<double> {
   static const double* D(ns_handle* h) { return h->D64; }
   static const double* val(ns_handle* h) { return h->val; }
   static const double* val_t(ns_handle* h) { return h->val_t; }
+  static const double* sval(const ns_handle::Sell& s) { return s.sval; }
 };
 template <>
 struct Prec<float> {
   static const float* D(ns_handle* h) { return h->D32; }
   static const float* val(ns_handle* h) { return h->val32; }
   static const float* val_t(ns_handle* h) { return h->val_t32; }
+  static const float* sval(const ns_handle::Sell& s) { return s.sval32; }
 };
+
+// sliced-ELLPACK copy of a device CSR (slices of kSellC rows, column-major inside a
+// slice), kept when its padding stays below 30% of nnz
+void build_sell(ns_handle* h, const int64_t* rowptr, const int* col, const double* val, int64_t nrows, int64_t nnz,
+                ns_handle::Sell& out) {
+  const int64_t nslices = (nrows + kSellC - 1) / kSellC;
+  if (nslices == 0) return;
+  Buf len(h, sizeof(int) * (size_t)nslices);
+  sell_lengths(rowptr, nrows, len.as<int>(), h->stream);
+  ck_launch("sell_lengths");
+  std::vector<int> lh((size_t)nslices);
+  ck(cudaMemcpyAsync(lh.data(), len.p, sizeof(int) * nslices, cudaMemcpyDeviceToHost, h->stream), "d2h");
+  ck(cudaStreamSynchronize(h->stream), "sync");
+  std::vector<int64_t> ptr((size_t)nslices + 1, 0);
+  for (int64_t i = 0; i < nslices; ++i) ptr[i + 1] = ptr[i] + (int64_t)kSellC * lh[i];
+  const int64_t entries = ptr[nslices];
+  if ((double)entries > 1.3 * (double)std::max<int64_t>(nnz, 1)) return;
+  out.sptr = (int64_t*)dalloc_own(h, sizeof(int64_t) * (size_t)(nslices + 1));
+  out.scol = (int*)dalloc_own(h, sizeof(int) * (size_t)std::max<int64_t>(entries, 1));
+  out.sval = (double*)dalloc_own(h, sizeof(double) * (size_t)std::max<int64_t>(entries, 1));
+  out.entries = entries;
+  ck(cudaMemcpyAsync(out.sptr, ptr.data(), sizeof(int64_t) * (nslices + 1), cudaMemcpyHostToDevice, h->stream), "h2d");
+  sell_fill(rowptr, col, val, nrows, out.sptr, out.scol, out.sval, h->stream);
+  ck_launch("sell_fill");
+  ck(cudaStreamSynchronize(h->stream), "sync");  // ptr (host) is read by the copy above
+}
 
 void ensure_fp32(ns_handle* h) {
   // FP32 copies of A's values (already present when A came in as FP32), A^T's values and D
@@ -241,6 +277,11 @@ void ensure_fp32(ns_handle* h) {
     h->D32 = (float*)dalloc_own(h, sizeof(float) * (size_t)h->n);
     convert_d2f(h->D64, h->D32, h->n, h->stream);
   }
+  for (ns_handle::Sell* sl : {&h->sell_A, &h->sell_At})
+    if (sl->sval && !sl->sval32) {
+      sl->sval32 = (float*)dalloc_own(h, sizeof(float) * (size_t)sl->entries);
+      convert_d2f(sl->sval, sl->sval32, sl->entries, h->stream);
+    }
   ck_launch("fp32 copies");
 }
 
@@ -254,6 +295,10 @@ Csr<T> csr_A(ns_handle* h) {
   c.ncols = h->n;
   c.nnz = h->nnz;
   c.V = choose_lanes(h->m, h->nnz);
+  c.sptr = h->sell_A.sptr;
+  c.scol = h->sell_A.scol;
+  c.sval = Prec<T>::sval(h->sell_A);
+  if (!c.sval) c.sptr = nullptr;
   return c;
 }
 template <typename T>
@@ -266,6 +311,10 @@ Csr<T> csr_At(ns_handle* h) {
   c.ncols = h->m;
   c.nnz = h->nnz;
   c.V = choose_lanes(h->n, h->nnz);
+  c.sptr = h->sell_At.sptr;
+  c.scol = h->sell_At.scol;
+  c.sval = Prec<T>::sval(h->sell_At);
+  if (!c.sval) c.sptr = nullptr;
   return c;
 }
 
@@ -425,8 +474,7 @@ struct Solver {
     // panels up to 2D = 16 wide (the merged [Q_j | Q_j+1] reorthogonalization at d = 8)
     const int K = cap + R + D;
     cbuf = Buf(h, sizeof(double) * (size_t)K * 16);
-    const int64_t rpc = std::min<int64_t>((int64_t)kThreads * 128, std::max<int64_t>(n, 1));
-    const int nch = ceil_div(n, rpc);
+    const int nch = ceil_div(std::max<int64_t>(n, 1), kDotsMinChunk);  // the auto chunking's smallest chunk
     dpart = Buf(h, sizeof(double) * (size_t)nch * K * 16);
   }
 
@@ -460,7 +508,8 @@ struct Solver {
     cudaEventCreate(&e1);
     int best = M.V;
     float best_ms = 1e30f;
-    for (int V : {kSchedTma, 1, 2, 4, 8}) {  // the TMA-staged schedule and 1..8 lanes per row
+    for (int V : {kSchedSell, kSchedTma, 1, 2, 4, 8}) {  // sliced ELLPACK, TMA-staged, 1..8 lanes per row
+      if (V == kSchedSell && !M.sptr) continue;
       M.V = V;
       spmm_lanczos<T, D>(M, v, op, red, s);
       cudaEventRecord(e0, s);
@@ -587,7 +636,7 @@ struct Solver {
     const double K = V.kx + V.kz, sv = sizeof(T);
     PScope ps(&h->prof, P_PROJ, passes * (2.0 * K * n * sv + 3.0 * n * W * sv), 4.0 * passes * K * n * W);
     for (int pass = 0; pass < passes; ++pass) {
-      proj_dots<T, W>(V, Wp, Wp2, ldw, n, cbuf.as<double>(), dpart.as<double>(), s);
+      proj_dots<T, W>(V, Wp, Wp2, ldw, n, cbuf.as<double>(), dpart.as<double>(), s, kDotsAutoChunks);
       ck((proj_update<T, W>(V, cbuf.as<double>(), Wp, Wp2, ldw, n, (pass == passes - 1 && gram) ? 1 : 0, Rout, gd,
                             flags, red, s)),
          "proj_update shared-memory limit");
@@ -1507,6 +1556,7 @@ ns_status ns_create(ns_handle** out, int64_t m, int64_t n, const int64_t* rowptr
     }
     csr_max_abs_row_sum(h->rowptr, h->val, m, norms, red, s);
     h->launches += 1;
+    build_sell(h, h->rowptr, h->col, h->val, m, nnz, h->sell_A);
     if (mode == NS_MODE_NORMAL) {
       h->rowptr_t = (int64_t*)dalloc_own(h, sizeof(int64_t) * (n + 1));
       h->col_t = (int*)dalloc_own(h, sizeof(int) * csr_entries(nnz));
@@ -1517,6 +1567,7 @@ ns_status ns_create(ns_handle** out, int64_t m, int64_t n, const int64_t* rowptr
       csr_transpose(h->rowptr, h->col, h->val, m, n, nnz, h->rowptr_t, h->col_t, h->val_t, tw, s);
       csr_max_abs_row_sum(h->rowptr_t, h->val_t, n, norms + 1, red, s);
       h->launches += 9;
+      build_sell(h, h->rowptr_t, h->col_t, h->val_t, n, nnz, h->sell_At);
       std::vector<int64_t> rpt(n + 1);
       ck(cudaMemcpyAsync(rpt.data(), h->rowptr_t, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, s), "d2h");
       ck(cudaStreamSynchronize(s), "sync");
@@ -1699,9 +1750,11 @@ ns_status ns_start_block(const ns_handle* hc, int d, double* Omega) {
 ns_status ns_apply_B(ns_handle* h, int d, const double* X, double* Y, double eps, int precision, int on_device,
                      int schedule) {
   if (!h || !X || !Y || !(d == 1 || d == 2 || d == 4 || d == 8)) return NS_ERR_INVALID_ARG;
-  if (!(schedule == -1 || schedule == kSchedTma || schedule == 1 || schedule == 2 || schedule == 4 ||
-        schedule == 8 || schedule == 16 || schedule == 32))
-    return set_err(h, NS_ERR_INVALID_ARG, "schedule must be -1, 64 or a power of two up to 32");
+  if (!(schedule == -1 || schedule == kSchedTma || schedule == kSchedSell || schedule == 1 || schedule == 2 ||
+        schedule == 4 || schedule == 8 || schedule == 16 || schedule == 32))
+    return set_err(h, NS_ERR_INVALID_ARG, "schedule must be -1, 64, 128 or a power of two up to 32");
+  if (schedule == kSchedSell && (!h->sell_A.sptr || (h->mode == NS_MODE_NORMAL && !h->sell_At.sptr)))
+    return set_err(h, NS_ERR_INVALID_ARG, "no sliced-ELLPACK copy for this matrix (padding above 30%)");
   try {
     const size_t cnt = (size_t)h->n * d;
     Buf xb(h, sizeof(double) * cnt), yb(h, sizeof(double) * cnt), rp(h, sizeof(double) * kMaxBlocks * 64 + 256),

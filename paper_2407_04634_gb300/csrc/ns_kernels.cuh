@@ -13,7 +13,13 @@ struct Csr {
   const int* col = nullptr;
   const T* val = nullptr;
   int64_t nrows = 0, ncols = 0, nnz = 0;
-  int V = 8;  // lanes per row (1..32), or kSchedTma for the TMA-staged schedule
+  int V = 8;  // lanes per row (1..32), kSchedTma (TMA-staged) or kSchedSell (sliced ELLPACK)
+  // sliced ELLPACK copy of the same matrix, or null: slices of kSellC consecutive rows,
+  // each padded to its longest row and stored column-major (entry j of row
+  // kSellC s + l at sptr[s] + j kSellC + l); padding has col 0 and value 0
+  const int64_t* sptr = nullptr;
+  const int* scol = nullptr;
+  const T* sval = nullptr;
 };
 
 // Reduction workspace: partial sums and an atomic ticket for the last-block protocol
@@ -24,6 +30,8 @@ struct Red {
 
 constexpr int kMaxBlocks = 152 * 8;  // persistent grid cap of reducing kernels
 constexpr int kSchedTma = 64;        // SpMM schedule code of the TMA-staged kernel
+constexpr int kSchedSell = 128;      // SpMM schedule code of the sliced-ELLPACK kernels
+constexpr int kSellC = 32;           // rows per ELLPACK slice: one warp, a row per lane
 constexpr int kCsrPad = 16;          // padding entries after col/val (16-byte aligned bulk copies)
 // bounded device waits that expired since the last call (clear: reset the count)
 unsigned spmm_wait_timeouts(bool clear);
@@ -69,6 +77,13 @@ struct TransposeWork {
 void csr_transpose(const int64_t* rowptr, const int* col, const double* val, int64_t m, int64_t n,
                    int64_t nnz, int64_t* rowptr_t, int* col_t, double* val_t, const TransposeWork& w,
                    cudaStream_t s);
+// sliced-ELLPACK copy of a device CSR (nrows rows): slice lengths, offsets (scanned on
+// the host), then the padded column-major entries.  Returns the number of entries
+// (kSellC times the sum of the slice lengths) through *entries; sptr must hold
+// ceil(nrows / kSellC) + 1 int64; scol / sval are filled by sell_fill.
+void sell_lengths(const int64_t* rowptr, int64_t nrows, int* slice_len, cudaStream_t s);
+void sell_fill(const int64_t* rowptr, const int* col, const double* val, int64_t nrows, const int64_t* sptr,
+               int* scol, double* sval, cudaStream_t s);
 // validation of a device CSR: err bit 1 rowptr, 2 colind, 4 values
 void csr_validate(const int64_t* rowptr, const int* col, const double* val, int64_t m, int64_t n,
                   int64_t nnz, unsigned* err, cudaStream_t s);
@@ -111,9 +126,14 @@ struct VParts {
 };
 // C (K x w, FP64, row-major) = V^T W ; W panel with leading dim ldw; when Wp2 is
 // given, columns [W/2, W) of W come from the panel Wp2 (same ldw)
+// rows_per_chunk: 0 = 32768 rows per chunk (part needs ceil(n / 32768) K W doubles);
+// kDotsAutoChunks = chosen so that the grid fills the GPU, never below
+// kDotsMinChunk rows (part needs ceil(n / kDotsMinChunk) K W doubles)
+constexpr int64_t kDotsAutoChunks = -1;
+constexpr int64_t kDotsMinChunk = 2048;
 template <typename T, int W>
 void proj_dots(const VParts<T>& V, const T* Wp, const T* Wp2, int64_t ldw, int64_t n, double* C, double* part,
-               cudaStream_t s);
+               cudaStream_t s, int64_t rows_per_chunk = 0);
 // W -= V C ; if gram: G = W^T W partials, last block chol -> R (+gdiag)
 // (returns the status of raising the kernel's shared-memory limit on this device;
 // the launch itself is checked by the caller)

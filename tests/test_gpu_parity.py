@@ -93,6 +93,25 @@ def test_apply_B_matches_oracle(ns, mode, d, precision):
     assert np.all(np.abs(Y - ref) <= tol * bound + 1e-300)
 
 
+def _balanced_matrix(seed, m, n, symmetric):
+    """Sparse m x n matrix whose rows and columns hold nearly the same number of entries
+    (so both A and A^T fit the sliced layout), with empty rows and m not a multiple of
+    the 32-row slice."""
+    rng = np.random.default_rng(seed)
+    rows, cols = [], []
+    for i in range(m):
+        if i % 97 == 5:
+            continue  # an empty row
+        k = 11 + (i % 2)
+        rows.append(np.full(k, i))
+        cols.append((7 * i + 257 * np.arange(k) + 1) % n)
+    M = sp.csr_matrix((rng.standard_normal(sum(len(r) for r in rows)), (np.concatenate(rows), np.concatenate(cols))),
+                      shape=(m, n))
+    if symmetric:
+        M = (M + M.T).tocsr()
+    return M
+
+
 def _skewed_matrix(seed, m, n):
     """Sparse m x n matrix with empty rows (one whole 256-row tile among them), short
     rows, and a few rows of 600-3000 entries (tiles too long to stage in shared
@@ -110,12 +129,17 @@ def _skewed_matrix(seed, m, n):
 
 @pytest.mark.parametrize("mode", ["spd", "normal"])
 @pytest.mark.parametrize("d,precision", [(1, "fp64"), (1, "mixed"), (2, "fp64"), (4, "mixed"), (8, "fp64")])
-@pytest.mark.parametrize("schedule", [64, 1, 4, 32])
+@pytest.mark.parametrize("schedule", [64, 1, 4, 32, 128])
 def test_apply_B_every_schedule(ns, mode, d, precision, schedule):
-    """Every SpMM schedule (TMA-staged and 1/4/32 threads per row) against the oracle's
-    operator, on rows from empty to 3000 entries and a ragged last tile."""
+    """Every SpMM schedule (TMA-staged, 1/4/32 threads per row, sliced ELLPACK) against
+    the oracle's operator, on rows from empty to 3000 entries and a ragged last tile;
+    the sliced layout on a matrix of nearly uniform rows and columns (0-24 entries) with
+    a ragged last slice, since long rows would exceed its padding limit."""
     from workloads.graphs import CSR, Workload
-    M = _skewed_matrix(100 + d, 4099, 4099 if mode == "spd" else 3001)
+    if schedule == 128:
+        M = _balanced_matrix(100 + d, 4099, 4099 if mode == "spd" else 3001, mode == "spd")
+    else:
+        M = _skewed_matrix(100 + d, 4099, 4099 if mode == "spd" else 3001)
     w = Workload("skewed", CSR.from_scipy(M), mode, 0)
     h = handle(ns, w, 5)
     rng = np.random.default_rng(schedule + 7)
