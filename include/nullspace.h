@@ -99,14 +99,14 @@ typedef struct {
 /* Kernel of the thick-restart product Z V_Z (ns_opts.gemm, ns_restart_product). */
 typedef enum {
   NS_GEMM_DEFAULT = 0,   /* the library's choice: NS_GEMM_TC3 on the mixed path, NS_GEMM_TC_EXACT
-                            on the FP64 path when restart_len <= 128, else CUDA cores          */
+                            on the FP64 path when restart_len <= 208, else CUDA cores          */
   NS_GEMM_CUDA_CORES = 1,/* FP32 / FP64 FMA register-tile kernels                                 */
   NS_GEMM_TC2 = 2,       /* mixed path: tensor cores, operands split into 2 bf16 slices, 3 products
                             (3xBF16)                                                          */
   NS_GEMM_TC3 = 3,       /* mixed path: tensor cores, 3 bf16 slices, 6 products (FP32 accuracy)  */
   NS_GEMM_TC_EXACT = 4   /* FP64 path: tensor cores, each FP64 operand split exactly into eight
                             7-bit integer slices (per-row / per-column exponents), exact FP32
-                            slice sums combined in int64: FP64 accuracy; restart_len <= 128  */
+                            slice sums combined in int64: FP64 accuracy; restart_len <= 208  */
 } ns_gemm;
 
 typedef struct {
@@ -162,7 +162,10 @@ ns_status ns_create(ns_handle** out, int64_t m, int64_t n, const int64_t* rowptr
  *   d           : block size, 1 <= d <= 8
  *   restart_len : maximal Krylov dimension dim K, multiple of d, >= 3d
  *   tol         : lock a Ritz pair when its value is < 3 eps and its residual
- *                 ||Gamma_l V_Z(last block, i)|| <= tol * ||B|| (Remark cormain)
+ *                 ||Gamma_l V_Z(last block, i)|| <= tol * ||B|| (Remark cormain), with
+ *                 ||B|| = min(cheap bound ||A||_1 ||A||_inf + eps (normal) or
+ *                 ||A||_inf + eps (SPD), 1.1 x the largest Ritz value seen); the same
+ *                 ||B|| scales u_d of the W recurrence
  *   opts        : NULL = defaults
  * Returns NS_OK, NS_ERR_NOT_CONVERGED (max_matvec reached; the basis holds the
  * vectors locked so far), NS_ERR_REFINE (a column missed refine_tol),
@@ -256,7 +259,7 @@ ns_status ns_fma_peak(int precision, double* tflops);
  *         next basis (the two output layouts ns_solve uses); 0 <= nl <= nsel
  *   precision : NS_FP64 (FP64 Z) or NS_MIXED (Z rounded to FP32, FP32 result)
  *   gemm      : ns_gemm; NS_GEMM_TC2 / TC3 need precision NS_MIXED and nsel <= 256,
- *               NS_GEMM_TC_EXACT needs NS_FP64 and R <= 128
+ *               NS_GEMM_TC_EXACT needs NS_FP64 and R <= 208
  *   out : n x nsel column-major FP64, host
  * d in {1, 2, 4, 8}, R a multiple of d, 1 <= R <= 512.  NS_ERR_TIMEOUT when a bounded
  * device wait gave up.  Allocates its own device buffers. */

@@ -58,7 +58,14 @@ Readings of points the paper leaves open (the CUDA path takes the same readings)
       locked nothing;
   R12 breakdown (sigma_min(Gamma) <= 100 u_d): the block is replaced by a fresh
       Gaussian block (Philox stream 2+k) orthogonalized against [X, Z], and
-      Gamma is set to zero.
+      Gamma is set to zero;
+  M4  ||B|| in u_d and in the lock tolerance, once a cycle has run:
+      min(R9 bound, 1.1 theta_max), theta_max the largest Ritz value seen so far (a
+      Ritz value never exceeds ||B||, and the extreme one converges first; the 10%
+      margin covers its remaining error).  The R9 bound can exceed ||B|| by an order
+      of magnitude for matrices with random values; u_d then reaches u_RO, and the
+      locked residuals rho_k <= tol ||B|| that enter the W rows of the locked set grow
+      with it (ud_rule="ritz", default; "bound" keeps R9 throughout).
 
 Parity unpinned: the stopping rule (R11) is a heuristic with no closed form or
 printed example to check it against; it is pinned only through its outcome (the
@@ -162,7 +169,7 @@ def lanczos_nullspace(A, mode: str, d: int, restart_len: int, tol: float = 1e-10
                       refine_maxit: int = 500, final_rr: bool = True,
                       u: float = U_FP64, D: np.ndarray | None = None,
                       Omega: np.ndarray | None = None, record: bool = False,
-                      probe=None, keep_rule: str = "capped") -> Result:
+                      probe=None, keep_rule: str = "capped", ud_rule: str = "ritz") -> Result:
     """Null space of A by Alg. 2 (restarted, partially reorthogonalized small-block Lanczos).
 
     reorth: "partial" (Sec. 4.2), "full" (every new block projected against the whole
@@ -181,8 +188,8 @@ def lanczos_nullspace(A, mode: str, d: int, restart_len: int, tol: float = 1e-10
     if D is None:
         D = perturbation_diagonal(seed, n)
     op = Operator(A, mode, eps, D)
-    normB = op.norm_bound()
-    u_d = d * np.sqrt(n) * u * normB  # Eq. (defmprd)
+    normB = op.norm_bound()  # reading R9; also the scale of the lock tolerance
+    u_d = d * np.sqrt(n) * u * normB  # Eq. (defmprd), refined after the first cycle (M4)
     u_ro = np.sqrt(u)  # Sec. 4.2
     bd_tol = 100.0 * u_d  # reading R12
     nb = R // d  # blocks of the basis before restart
@@ -318,6 +325,11 @@ def lanczos_nullspace(A, mode: str, d: int, restart_len: int, tol: float = 1e-10
         theta, VZ = np.linalg.eigh(T)  # ascending
         resid = np.linalg.norm(Gam[nb - 1] @ VZ[R - d:R, :], axis=0)
         st["theta_max"] = max(st["theta_max"], float(theta[-1]))
+        normB_est = normB
+        if restart and ud_rule == "ritz":  # reading M4: ||B|| from the Ritz values
+            normB_est = min(normB, 1.1 * st["theta_max"])
+            u_d = d * np.sqrt(n) * u * normB_est
+            bd_tol = 100.0 * u_d
         small = theta < 3 * eps
         if record and restart:
             st.setdefault("cycles", []).append(dict(T=T, Z=Z[:, :R].copy(), Qnext=Z[:, R:R + d].copy(),
@@ -330,7 +342,7 @@ def lanczos_nullspace(A, mode: str, d: int, restart_len: int, tol: float = 1e-10
             break
         st["restarts"] += 1
         # ---- locking (reading R5) ---------------------------------------------
-        cand = np.nonzero(small & (resid <= tol * normB))[0]
+        cand = np.nonzero(small & (resid <= tol * normB_est))[0]
         ghosts = np.zeros(0, dtype=np.int64)
         nlock = 0
         if cand.size:

@@ -264,9 +264,9 @@ __global__ void __launch_bounds__(kUThreads, 1)
 // Oishi and Rump, 2012).  Row i of Z is written as sum_p zq_p 2^(e_i - 7(p+1)) with
 // integer slices |zq_p| <= 127 (e_i: |z_ij| < 2^e_i over the row), column c of V_Z
 // as sum_q vq_q 2^(f_c - 7(q+1)).  A product of two slices is an integer below
-// 2^14, exact in bf16 x bf16 -> FP32, and every partial sum over R <= 128 terms of
-// the (s + 1) slice pairs with p + q = s stays below 2^24, so the FP32 accumulator
-// of group s holds its exact integer value.  The eight groups s = 0..7 (the 36
+// 2^14, exact in bf16 x bf16 -> FP32, and the partial sums of the leading groups
+// (the (s + 1) slice pairs with p + q = s, s <= 4) stay below 2^24 for R <= 208, so
+// their FP32 accumulators hold exact integers (restart_ozaki_supported).  The eight groups s = 0..7 (the 36
 // pairs with p + q <= 7) live in eight TMEM accumulators of 64 columns; the
 // epilogue adds them exactly in int64 and scales by 2^(e_i + f_c - 63) in FP64.
 // Dropped pairs (p + q >= 8) and the truncated tails of the slices leave an error
@@ -565,7 +565,11 @@ size_t restart_ozaki_scratch_bytes(int64_t n, int R, int nsel) {
   return (size_t)nblk * nkc * kOzS * kOzSliceB + sizeof(int) * ((size_t)nblk * kOzN + (size_t)n) + 512;
 }
 
-bool restart_ozaki_supported(int R, int nsel) { return R >= 1 && R <= 128 && nsel >= 1; }
+// Exactness of the slice-pair sums: group s adds (s + 1) pairs over R terms below
+// 2^14 each, so groups s <= 4 stay below 2^24 (exact in FP32) for R <= 208.  Groups
+// s >= 5 may round, but they weigh 2^(-7 s - 14) relative to the leading group, so
+// their FP32 rounding stays below 2^-56 of the result: beyond FP64 precision.
+bool restart_ozaki_supported(int R, int nsel) { return R >= 1 && R <= 208 && nsel >= 1; }
 
 cudaError_t restart_gemm_ozaki(const double* Z, int d, int R, const double* VZ, const int* sel, int nsel, int nl,
                                int64_t n, double* Lnew, double* Znext, void* scratch, unsigned* err, cudaStream_t s) {

@@ -328,6 +328,7 @@ struct Solver {
   int64_t n, m;
   int R, nb;
   double eps, tol_eff, normB, u, u_d, u_ro, bd_tol;
+  double ud_per_normB = 0.0;  // u_d = ud_per_normB * ||B|| (Eq. defmprd with readings M1, M4)
   ns_opts o;
   Csr<T> A, At;
   const T* Dv;
@@ -361,13 +362,18 @@ struct Solver {
     normB = (h->mode == NS_MODE_NORMAL ? h->normA1 * h->normAinf : h->normAinf) + eps;
     u = Unit<T>::u;
     if (!mixed) {
-      u_d = D * std::sqrt((double)n) * u * normB;  // Eq. (defmprd)
+      ud_per_normB = D * std::sqrt((double)n) * u;  // Eq. (defmprd)
     } else {
-      // FP32 reading: the inner-product length of one application of B is the row
-      // length of B, not n (sparse B); sqrt(n) u_32 would exceed sqrt(u_32).
-      const double k = (h->mode == NS_MODE_NORMAL) ? (double)h->maxrow_A * (double)h->maxrow_At : (double)h->maxrow_A;
-      u_d = D * std::sqrt(std::max(k, 1.0)) * u * normB;
+      // FP32 reading M1: the inner-product lengths of one application of B are the row
+      // lengths of its stages, not n (sparse B; sqrt(n) u_32 would exceed sqrt(u_32));
+      // the two stages of A^T (A x) add their errors
+      const double k = (h->mode == NS_MODE_NORMAL)
+                           ? std::sqrt((double)std::max<int64_t>(h->maxrow_A, 1)) +
+                                 std::sqrt((double)std::max<int64_t>(h->maxrow_At, 1))
+                           : std::sqrt((double)std::max<int64_t>(h->maxrow_A, 1));
+      ud_per_normB = D * k * u;
     }
+    u_d = ud_per_normB * normB;
     u_ro = std::sqrt(u);
     bd_tol = 100.0 * u_d;
     A = csr_A<T>(h);
@@ -714,11 +720,19 @@ struct Solver {
     apply_step(q, nullptr, nullptr, Xi + (size_t)r0 * D * D, nXi + r0);
     project<D>(qp.as<T>(), D, nlock, cur, r0 + 1, true, R1, nullptr);
     T* qn = blk(cur, r0 + 1);
-    scale_gram<T, D>(qp.as<T>(), D, qn, D, R1, n, R2, flags, red, s, D);
-    OmegaArgs a = omega_args(r0, r0);
-    gamma_store(a, s);
-    scale_gram<T, D>(qn, D, qn, D, R2, n, nullptr, flags, red, s, D);
-    launches += 3;
+    if constexpr (D == 1) {  // a single vector: one normalization (see inner_step)
+      scale_gram<T, D>(qp.as<T>(), D, qn, D, R1, n, nullptr, flags, red, s, D);
+      OmegaArgs a = omega_args(r0, r0);
+      a.R2 = nullptr;
+      gamma_store(a, s);
+      launches += 2;
+    } else {
+      scale_gram<T, D>(qp.as<T>(), D, qn, D, R1, n, R2, flags, red, s, D);
+      OmegaArgs a = omega_args(r0, r0);
+      gamma_store(a, s);
+      scale_gram<T, D>(qn, D, qn, D, R2, n, nullptr, flags, red, s, D);
+      launches += 3;
+    }
     if (read_flags() & 1u) {
       clear_flags();
       replace_block(cur, r0 + 1);
@@ -739,7 +753,18 @@ struct Solver {
     T* q = blk(cur, j);
     T* qn = blk(cur, j + 1);
     apply_step(q, blk(cur, j - 1), Gam + (size_t)(j - 1) * D * D, Xi + (size_t)j * D * D, nXi + j);
-    {
+    if constexpr (D == 1) {
+      // a single vector: Q_{j+1} = Q' / ||Q'|| in one pass.  The second CholQR pass of a
+      // block (below) would re-normalize an already unit vector, an O(u) correction.
+      PScope ps(&h->prof, P_REC, 5.0 * n * sizeof(T), 6.0 * n);
+      axpy_gram<T, D>(qp.as<T>(), q, Xi + (size_t)j * D * D, n, R1, flags, red, s);
+      scale_gram<T, D>(qp.as<T>(), D, qn, D, R1, n, nullptr, flags, red, s, D);
+      OmegaArgs a = omega_args(j, r0);
+      a.R2 = nullptr;  // Gamma_j = R1 = ||Q'||
+      if (o.reorth == NS_REORTH_FULL) a.u_ro = -1.0;  // every column triggers
+      step_finalize(a, s);
+      launches += 3;
+    } else {
       PScope ps(&h->prof, P_REC, 7.0 * n * D * sizeof(T), 8.0 * n * D * D);
       axpy_gram<T, D>(qp.as<T>(), q, Xi + (size_t)j * D * D, n, R1, flags, red, s);
       scale_gram<T, D>(qp.as<T>(), D, qn, D, R1, n, R2, flags, red, s, D);
@@ -747,8 +772,8 @@ struct Solver {
       if (o.reorth == NS_REORTH_FULL) a.u_ro = -1.0;  // every column triggers
       step_finalize(a, s);
       scale_gram<T, D>(qn, D, qn, D, R2, n, nullptr, flags, red, s, D);
+      launches += 4;
     }
-    launches += 4;
     const unsigned f = read_flags();
     if (f) clear_flags();
     if (f & 1u) {  // breakdown: fresh block, coupling set to zero
@@ -868,12 +893,17 @@ struct Solver {
     pin_res.assign(pin_d + R, pin_d + 2 * R);
     restarts += 1;
     theta_max = std::max(theta_max, pin_theta[R - 1]);
+    // reading M4: once a cycle has run, ||B|| in u_d and in the lock tolerance is
+    // min(R9 bound, 1.1 theta_max)
+    const double normB_est = std::min(normB, 1.1 * theta_max);
+    u_d = ud_per_normB * normB_est;
+    bd_tol = 100.0 * u_d;
     std::vector<int> cand;
     int nsmall = 0;
     for (int i = 0; i < R; ++i) {
       if (pin_theta[i] < 3.0 * eps) {
         ++nsmall;
-        if (pin_res[i] <= tol_eff * normB) cand.push_back(i);
+        if (pin_res[i] <= tol_eff * normB_est) cand.push_back(i);
       }
     }
     std::vector<char> taken(R, 0), is_ghost(cand.size(), 0);
@@ -1395,7 +1425,7 @@ static void restart_product_typed(ns_handle* h, int64_t n, int d, int R, const d
   }
   if constexpr (std::is_same<T, double>::value) {
     if (exact) {
-      if (!restart_ozaki_supported(R, nsel)) throw Fail{NS_ERR_INVALID_ARG, "exact tensor-core product needs R <= 128"};
+      if (!restart_ozaki_supported(R, nsel)) throw Fail{NS_ERR_INVALID_ARG, "exact tensor-core product needs R <= 208"};
       ck(restart_gemm_ozaki(bz.as<double>(), d, R, bv.as<double>(), bs.as<int>(), nsel, nl, n, bl.as<double>(),
                             bn.as<double>(), img.p, fl.as<unsigned>(), s),
          "restart_gemm_ozaki");
@@ -1608,7 +1638,7 @@ ns_status ns_solve(ns_handle* h, int d, int restart_len, double tol, const ns_op
       (o.precision == NS_MIXED && o.gemm == NS_GEMM_TC_EXACT) ||
       (o.gemm == NS_GEMM_TC_EXACT && !restart_ozaki_supported(restart_len, 1)))
     return set_err(h, NS_ERR_INVALID_ARG,
-                   "gemm: 0..4; TC2/TC3 on the mixed path, TC_EXACT on the FP64 path with restart_len <= 128");
+                   "gemm: 0..4; TC2/TC3 on the mixed path, TC_EXACT on the FP64 path with restart_len <= 208");
   h->err.clear();
   h->solved = false;
   h->launches = 0;

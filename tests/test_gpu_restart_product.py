@@ -11,7 +11,7 @@ locked-candidate panel and the next basis blocks):
     dropped slice products are below 3 u32 relative to the operands;
   * tensor cores, 2 bf16 slices (3 products, "3xBF16"): 3 * 2^-16 (|Z32| |V|) plus
     the FP32 accumulation -- each operand is carried to 16 bits;
-  * tensor cores, exact FP64 slicing (8 integer slices, R <= 128): the FP64 bound
+  * tensor cores, exact FP64 slicing (8 integer slices, R <= 208): the FP64 bound
     plus R 2^-49 max_j |z_ij| max_j |v_jc| for the truncated slice tails and the
     dropped slice pairs (p + q >= 8).
 """
@@ -43,6 +43,7 @@ def operands(n, R, nsel, seed):
 
 CASES = [  # n, d, R, nsel, nl
     (1000, 1, 120, 60, 0),
+    (20011, 8, 208, 104, 8),
     (70001, 1, 120, 60, 0),
     (70001, 2, 150, 76, 0),
     (33333, 4, 160, 80, 16),
@@ -55,8 +56,8 @@ CASES = [  # n, d, R, nsel, nl
 @pytest.mark.parametrize("n,d,R,nsel,nl", CASES)
 @pytest.mark.parametrize("kind", ["fp64", "fp32", "tc3", "tc2", "tc_exact"])
 def test_restart_product_matches_fp64(ns, n, d, R, nsel, nl, kind):
-    if kind == "tc_exact" and R > 128:
-        pytest.skip("the exact slicing serves R <= 128")
+    if kind == "tc_exact" and R > 208:
+        pytest.skip("the exact slicing serves R <= 208")
     Z, V, sel = operands(n, R, nsel, seed=n + R + nsel)
     if kind == "tc_exact":  # rows and columns of very different scales
         rng = np.random.default_rng(n)
@@ -89,9 +90,9 @@ def test_restart_product_tensor_cores_need_mixed_and_at_most_256_columns(ns):
         ns.restart_product(Z, V, sel, 0, 1, "fp64", "tc3")
     with pytest.raises(ns.NullspaceError):
         ns.restart_product(Z, V, sel, 0, 1, "mixed", "tc_exact")
-    Z, V, sel = operands(100, 136, 20, 3)
+    Z, V, sel = operands(100, 216, 20, 3)
     with pytest.raises(ns.NullspaceError):
-        ns.restart_product(Z, V, sel, 0, 1, "fp64", "tc_exact")  # R > 128
+        ns.restart_product(Z, V, sel, 0, 1, "fp64", "tc_exact")  # R > 208
     Z, V, sel = operands(300, 300, 272, 2)
     with pytest.raises(ns.NullspaceError):
         ns.restart_product(Z, V, sel, 0, 1, "mixed", "tc3")

@@ -333,3 +333,30 @@ def test_principal_sine_of_a_known_rotation(theta):
     assert abs(s - np.sin(theta)) <= 1e-12 + 1e-9 * np.sin(theta)
     assert principal_sine(U, U @ M) <= 1e-14
     assert principal_sine(U, X[:, :k - 1]) == 1.0  # unequal dimensions
+
+
+@pytest.mark.parametrize("d", [1, 2])
+def test_omega_bounds_with_ritz_norm_estimate(d):
+    """Reading M4 (u_d from 1.1 x the largest Ritz value once a cycle has run) on a
+    matrix whose cheap norm bound R9 is loose (N(0,1) values, normal form): u_d drops
+    well below its R9 value, and every W entry still bounds the true ||Q_k^T Q_{l+1}||
+    of the (partially reorthogonalized) run, locked rows included."""
+    from workloads import rectangular_copies
+    w = rectangular_copies(31, 900, 600, 4)
+    A = w.A.to_scipy()
+    worst = [0.0]
+
+    def probe(j, Z, X, col, colX, dd):
+        Qn = Z[:, (j + 1) * dd:(j + 2) * dd]
+        for b in range(j + 1):
+            true = np.linalg.norm(Z[:, b * dd:(b + 1) * dd].T @ Qn, 2)
+            if col[b] < 1e-3:
+                worst[0] = max(worst[0], true / col[b])
+        if X.shape[1]:
+            worst[0] = max(worst[0], float(np.max(np.abs(X.T @ Qn).max(axis=1) / colX)))
+
+    r = lanczos_nullspace(A, "normal", d, 30 * d, seed=5, probe=probe, refine=False)
+    ref = lanczos_nullspace(A, "normal", d, 30 * d, seed=5, refine=False, ud_rule="bound")
+    assert r.N == ref.N == 4
+    assert r.u_d < 0.5 * ref.u_d  # the Ritz estimate is much tighter than R9 here
+    assert worst[0] <= 1.0, worst[0]
