@@ -279,6 +279,8 @@ constexpr int kOzSliceA = kTM * kOzKC * 2;     // 8 KB
 constexpr int kOzSliceB = kOzN * kOzKC * 2;    // 4 KB
 constexpr int kOzStage = kOzS * (kOzSliceA + kOzSliceB);  // 96 KB
 constexpr uint32_t kOzSBO = (kOzKC / 8) * 128; // 512: 8-row groups of a 32-wide K chunk
+constexpr int kOzThreads = 512;                // 16 warps: one CTA per SM holds all 512 TMEM
+                                               // columns, so the loads in flight come from warps
 
 __host__ __device__ constexpr uint32_t canon32(int r, int k) {
   return (uint32_t)((r >> 3) * kOzSBO + (k >> 3) * kLBO + (r & 7) * 16 + (k & 7) * 2);
@@ -360,7 +362,7 @@ __global__ void k_oz_bimage(const double* __restrict__ VZ, const int* __restrict
 }
 
 template <int D>
-__global__ void __launch_bounds__(kUThreads, 1)
+__global__ void __launch_bounds__(kOzThreads, 1)
     k_restart_ozaki(const double* __restrict__ Z, int R, int64_t n, const int* __restrict__ emax,
                     const uint4* __restrict__ img, const int* __restrict__ fexp, int nsel, int nl,
                     double* __restrict__ Lnew, double* __restrict__ Znext, unsigned* err) {
@@ -393,7 +395,7 @@ __global__ void __launch_bounds__(kUThreads, 1)
   uint32_t ph[2] = {0u, 0u};  // next parity to wait for, per stage buffer
   int pending[2] = {0, 0};    // a commit on this buffer not yet waited for
 
-  const int r = threadIdx.x & (kTM - 1), half = threadIdx.x >> 7;  // A stager: row, which 16 of the 32 K
+  const int r = threadIdx.x & (kTM - 1), kcore = threadIdx.x >> 7;  // A stager: row, which 8 of the 32 K
   const int64_t ntiles = (n + kTM - 1) / kTM;
   for (int64_t tile = blockIdx.x; tile < ntiles && !abort_flag; tile += gridDim.x) {
     const int64_t i0 = tile * kTM, i = i0 + r;
@@ -411,13 +413,12 @@ __global__ void __launch_bounds__(kUThreads, 1)
           ph[sb] ^= 1u;
           pending[sb] = 0;
         }
-        // A: 16 values of row r, split into 8 integer slices each
-#pragma unroll
-        for (int cc = 0; cc < 2; ++cc) {
+        // A: 8 values of row r (one K-core), split into 8 integer slices each
+        {
           double v[8];
 #pragma unroll
           for (int u = 0; u < 8; ++u) {
-            const int k = kc * kOzKC + (half * 2 + cc) * 8 + u;
+            const int k = kc * kOzKC + kcore * 8 + u;
             v[u] = (i < n && k < R) ? __ldg(Z + (int64_t)(k / D) * n * D + i * D + (k % D)) : 0.0;
           }
           __align__(16) uint16_t sl[kOzS][8];
@@ -428,7 +429,7 @@ __global__ void __launch_bounds__(kUThreads, 1)
 #pragma unroll
             for (int p = 0; p < kOzS; ++p) sl[p][u] = o[p];
           }
-          const uint32_t off = canon32(r, (half * 2 + cc) * 8);
+          const uint32_t off = canon32(r, kcore * 8);
 #pragma unroll
           for (int p = 0; p < kOzS; ++p)
             *reinterpret_cast<uint4*>(As + (size_t)p * kOzSliceA + off) = *reinterpret_cast<const uint4*>(sl[p]);
@@ -470,11 +471,11 @@ __global__ void __launch_bounds__(kUThreads, 1)
       __syncthreads();
       if (abort_flag) break;
       fence_after();
-      // epilogue: warp w reads lanes 32 (w % 4) .. +31, 32 of the 64 columns
+      // epilogue: warp w reads lanes 32 (w % 4) .. +31, 16 of the 64 columns
       const int lq = warp & 3, chh = warp >> 2;
       const int64_t row = i0 + 32 * lq + lane;
       const int Er = row < n ? __ldg(emax + row) : 0;
-      for (int c0 = chh * 32; c0 < chh * 32 + 32; c0 += 8) {
+      for (int c0 = chh * 16; c0 < chh * 16 + 16; c0 += 8) {
         float g[kOzS][8];
 #pragma unroll
         for (int sg = 0; sg < kOzS; ++sg)
@@ -548,12 +549,19 @@ static cudaError_t launch_umma(const float* Z, int R, int64_t n, const uint4* im
   // (and the launch) see the largest carveout
   e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (e != cudaSuccess) return e;
-  int dev = 0, sms = 0, per_sm = 0;
+  int dev = 0, sms = 0, smem_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kUThreads, smem);
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  // resident CTAs per SM from the kernel's own registers and shared memory (plus the
+  // 1 KB the driver reserves per CTA), capped by the TMEM columns
+  cudaFuncAttributes fa{};
+  e = cudaFuncGetAttributes(&fa, fn);
   if (e != cudaSuccess) return e;
-  per_sm = std::max(1, std::min(per_sm, max_ctas));
+  const int regs_cta = ((fa.numRegs + 7) / 8) * 8 * kUThreads;
+  const int by_regs = regs_cta > 0 ? 65536 / regs_cta : 1;
+  const int by_smem = (int)((size_t)smem_sm / (smem + fa.sharedSizeBytes + 1024));
+  const int per_sm = std::max(1, std::min({by_regs, by_smem, max_ctas}));
   const int64_t ntiles = (n + kTM - 1) / kTM;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)sms * per_sm));
   k_restart_umma<S, D><<<grid, kUThreads, smem, s>>>(Z, R, n, img, npad, nsel, nl, Lnew, Znext, err);
@@ -605,10 +613,10 @@ cudaError_t restart_gemm_ozaki(const double* Z, int d, int R, const double* VZ, 
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, sms));
   const uint4* im = reinterpret_cast<const uint4*>(img);
   switch (d) {
-    case 1: k_restart_ozaki<1><<<grid, kUThreads, smem, s>>>(Z, R, n, emax, im, fexp, nsel, nl, Lnew, Znext, err); break;
-    case 2: k_restart_ozaki<2><<<grid, kUThreads, smem, s>>>(Z, R, n, emax, im, fexp, nsel, nl, Lnew, Znext, err); break;
-    case 4: k_restart_ozaki<4><<<grid, kUThreads, smem, s>>>(Z, R, n, emax, im, fexp, nsel, nl, Lnew, Znext, err); break;
-    default: k_restart_ozaki<8><<<grid, kUThreads, smem, s>>>(Z, R, n, emax, im, fexp, nsel, nl, Lnew, Znext, err); break;
+    case 1: k_restart_ozaki<1><<<grid, kOzThreads, smem, s>>>(Z, R, n, emax, im, fexp, nsel, nl, Lnew, Znext, err); break;
+    case 2: k_restart_ozaki<2><<<grid, kOzThreads, smem, s>>>(Z, R, n, emax, im, fexp, nsel, nl, Lnew, Znext, err); break;
+    case 4: k_restart_ozaki<4><<<grid, kOzThreads, smem, s>>>(Z, R, n, emax, im, fexp, nsel, nl, Lnew, Znext, err); break;
+    default: k_restart_ozaki<8><<<grid, kOzThreads, smem, s>>>(Z, R, n, emax, im, fexp, nsel, nl, Lnew, Znext, err); break;
   }
   return cudaSuccess;
 }

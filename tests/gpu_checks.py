@@ -56,7 +56,7 @@ def indicator_sine(labels, X) -> float:
     sums = torch.zeros((k, X.shape[1]), dtype=X.dtype, device=X.device).index_add_(0, lab, X)
     cnt = torch.bincount(lab, minlength=k).to(X.dtype)
     Rm = X - (sums / cnt[:, None])[lab]
-    return float(torch.linalg.eigvalsh(Rm.T @ Rm)[-1].clamp_min(0).sqrt())
+    return float(np.sqrt(max(np.linalg.eigvalsh((Rm.T @ Rm).double().cpu().numpy())[-1], 0.0)))
 
 
 def copy_pair_sine(pairs, n: int, X) -> float:
@@ -68,7 +68,7 @@ def copy_pair_sine(pairs, n: int, X) -> float:
     PX[pr[:, 0]] = avg
     PX[pr[:, 1]] = avg
     Rm = X - PX
-    return float(torch.linalg.eigvalsh(Rm.T @ Rm)[-1].clamp_min(0).sqrt())
+    return float(np.sqrt(max(np.linalg.eigvalsh((Rm.T @ Rm).double().cpu().numpy())[-1], 0.0)))
 
 
 def orthonormality(X) -> tuple[float, float]:
