@@ -1094,6 +1094,9 @@ __global__ void k_gram_reduce(const double* part, const int2* pairs, int npairs,
   const int64_t total = (int64_t)npairs * kGT * kGT;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
     const int p = (int)(t / (kGT * kGT)), e = (int)(t % (kGT * kGT));
+    // a diagonal tile holds both (i, j) and (j, i), summed in different orders: only
+    // its upper triangle writes, so every entry of G has exactly one writer
+    if (pairs[p].x == pairs[p].y && e / kGT > e % kGT) continue;
     double s = 0.0;
     for (int c = 0; c < nchunks; ++c) s += part[((size_t)c * npairs + p) * (kGT * kGT) + e];
     const int i = pairs[p].x * kGT + e / kGT, j = pairs[p].y * kGT + e % kGT;
