@@ -363,6 +363,41 @@ def residual_ratio(Ad, X, normA, chunk=64):
     return tot ** 0.5 / normA
 
 
+def d_sweep(ns, h, w, p, args, local):
+    """Block size at a fixed Krylov dimension (Sec. 5.3.1, Table tabCH): for each d in
+    1, 2, 4, 8 one untimed and one timed solve (CUDA events on the current stream) at
+    restart length dim K = the workload's restart length rounded down to a multiple of
+    8; reports B applications (counted per column, as the table does), restarts, the
+    solve time and the nullity, and which d the rule d = dim K / 16 picks."""
+    import torch
+    R = 8 * (p["restart"] // 8)
+    precision = args.precision or p["precision"]
+    stream = torch.cuda.current_stream()
+    rows = []
+    for d in (1, 2, 4, 8):
+        def one():
+            return h.solve(d, R, p["tol"], check=False, precision=precision)
+        one()
+        torch.cuda.synchronize()
+        clocks = ClockSampler(local)
+        clocks.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = one()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        ok = r.status == ns.NS_OK and r.nullity == w.nullity and r.stats.get("refine_resid_max", 1) <= 1e-8
+        rows.append({"d": d, "matvecs": r.stats.get("matvecs"), "restarts": r.stats.get("restarts"),
+                     "ms": e0.elapsed_time(e1), "nullity": r.nullity, "valid": ok,
+                     "t_lanczos_ms": r.stats.get("t_lanczos_ms"), "sm_mhz": clk.get("sm_mhz"),
+                     "reasons": clk.get("reasons")})
+    rule = h.solve(0, R, p["tol"], check=False, precision=precision).stats.get("d")
+    print(json.dumps({"sweep": "block size d at fixed dim K", "dim_K": R, "precision": precision,
+                      "rule_d": rule, "rows": rows,
+                      "config": describe(p, w)}), flush=True)
+
+
 def kernel_probe(ns, h, w, p):
     """A handful of hot-kernel launches on the workload's inputs (for ncu captures):
     three B-applies in each precision and every SpMM schedule, the thick-restart
@@ -595,6 +630,8 @@ def main():
                     help="FP64 path's Gram-Schmidt products: 0 compensated FP32 pairs (default), 1 FP64 FMA")
     ap.add_argument("--scale", type=float, default=1.0, help="workload scale (< 1 is for profiling only)")
     ap.add_argument("--kernel-probe", action="store_true", help="launch a few hot kernels, no bench line")
+    ap.add_argument("--d-sweep", action="store_true",
+                    help="block sizes 1, 2, 4, 8 at a fixed dim K (Sec. 5.3.1), one line, no bench line")
     ap.add_argument("--loop-sample", type=int, default=32,
                     help="batched workload: instances solved one by one with the FP64 path for comparison")
     ap.add_argument("--batch-block", type=int, default=0, choices=[0, 128, 256],
@@ -630,6 +667,9 @@ def main():
     stream = torch.cuda.current_stream()
     if args.kernel_probe:
         kernel_probe(ns, h, w, p)
+        return
+    if args.d_sweep:
+        d_sweep(ns, h, w, p, args, local)
         return
 
     alu = alu_peaks(ns, local)

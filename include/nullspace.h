@@ -40,8 +40,10 @@ typedef enum {
   NS_ERR_TIMEOUT = 5,       /* a bounded device wait gave up (no hang)             */
   NS_ERR_STATE = 6,         /* call out of order (e.g. basis before solve)         */
   NS_ERR_REFINE = 7,        /* some column missed the refinement tolerance          */
-  NS_ERR_NUMERICAL = 8      /* a block lost rank during reorthogonalization; a
+  NS_ERR_NUMERICAL = 8,     /* a block lost rank during reorthogonalization; a
                                numerical event of the iteration, not a CUDA failure */
+  NS_ERR_IO = 9             /* a checkpoint file could not be written, or is missing,
+                               truncated or corrupt (checksum)                     */
 } ns_status;
 
 typedef enum {
@@ -94,6 +96,18 @@ typedef struct {
                           FP32 pairs on the FP32 pipe (default; each FP64 operand split
                           exactly into two FP32 words, TwoProd / TwoSum accumulation, error
                           about 2^-47 sum |v w|), 1 = FP64 FMA                            */
+  int spmm_schedule;   /* SpMM schedule of ns_solve's B applications: 0 = timed on this matrix
+                          at the start of every solve (default); 1, 2, 4 or 8 threads per CSR
+                          row, 64 = TMA-staged rows, 128 = sliced ELLPACK (8 threads per row
+                          when ns_create did not build that layout).  Schedules sum a row in
+                          different orders, and the timed choice can differ between runs:
+                          a fixed schedule makes repeated solves bit-identical.            */
+  int checkpoint_every;/* > 0: ns_solve writes its state to checkpoint_path after every
+                          checkpoint_every-th thick restart, and at the restart where
+                          max_matvec stops it; 0 = never (default)                         */
+  int resume;          /* 1: ns_solve continues from the state in checkpoint_path instead of
+                          drawing a start block; 0 = new solve (default)                  */
+  const char* checkpoint_path; /* file of checkpoint_every / resume (NULL = none)          */
 } ns_opts;
 
 /* Kernel of the thick-restart product Z V_Z (ns_opts.gemm, ns_restart_product). */
@@ -129,6 +143,9 @@ typedef struct {
   double t_lanczos_ms;   /* device time of the Lanczos phase                         */
   double t_refine_ms;    /* device time of the refinement phase                      */
   double t_total_ms;
+  int64_t d;             /* block size of the solve (the d = dim K / 16 choice for d = 0) */
+  int64_t resumed_at;    /* restarts in the checkpoint a resumed solve started from; -1
+                            for a solve that did not resume                          */
 } ns_stats_t;
 
 typedef struct ns_handle ns_handle;
@@ -159,7 +176,9 @@ ns_status ns_create(ns_handle** out, int64_t m, int64_t n, const int64_t* rowptr
                     uint64_t seed, int mode, const ns_env* env);
 
 /* ns_solve -- Alg. 2 with locking and refinement (Sec. 4).
- *   d           : block size, 1 <= d <= 8
+ *   d           : block size 1, 2, 4 or 8; 0 = the block-size rule of Sec. 5.3.1,
+ *                 d = dim K / 16, taken as the largest of 8, 4, 2, 1 that is at most
+ *                 max(1, restart_len / 16) and divides restart_len (ns_stats d)
  *   restart_len : maximal Krylov dimension dim K, multiple of d, >= 3d
  *   tol         : lock a Ritz pair when its value is < 3 eps and its residual
  *                 ||Gamma_l V_Z(last block, i)|| <= tol * ||B|| (Remark cormain), with
@@ -170,8 +189,45 @@ ns_status ns_create(ns_handle** out, int64_t m, int64_t n, const int64_t* rowptr
  * Returns NS_OK, NS_ERR_NOT_CONVERGED (max_matvec reached; the basis holds the
  * vectors locked so far), NS_ERR_REFINE (a column missed refine_tol),
  * NS_ERR_NUMERICAL (a reorthogonalized block lost rank), or an error.
- * May be called again on the same handle (new solve, same D and start seed). */
+ * May be called again on the same handle (new solve, same D and start seed).
+ * Checkpoints (opts checkpoint_every, resume, checkpoint_path): at a thick restart
+ * (Alg. 2 line 17) the whole state of the iteration is the retained Ritz vectors
+ * and the next block, the projected matrix's arrow part, the W rows, the locked
+ * vectors with their Ritz values and residuals, the counters and the SpMM
+ * schedules.  A checkpoint holds exactly that (written to checkpoint_path + ".tmp",
+ * then renamed over checkpoint_path, so an interrupted write leaves the previous
+ * file intact).  A resumed solve restores it and continues as the uninterrupted
+ * solve would: with the same opts (max_matvec, stop_factor and the refinement
+ * options may differ) its basis and counters are bit-identical to those of a solve
+ * that ran straight through with the schedules of the checkpoint.  max_matvec
+ * counts B applications since the start of the solve, including those before the
+ * checkpoint.  A resumed solve needs a handle made from the same matrix and seed
+ * and the same d, restart_len, tol, eps, precision, reorth, gemm and
+ * fp64_products, else NS_ERR_INVALID_ARG; an unreadable or corrupt file gives
+ * NS_ERR_IO.  A checkpoint stores at most (restart_len + d) n + N n values of the
+ * solve's type (N locked vectors) plus O(restart_len^2) doubles. */
 ns_status ns_solve(ns_handle* h, int d, int restart_len, double tol, const ns_opts* opts);
+
+/* What a checkpoint file written by ns_solve holds (all fields 8 bytes). */
+typedef struct {
+  int64_t version;         /* format version, 1                                        */
+  int64_t m, n, nnz, mode; /* the matrix of the solve                                  */
+  int64_t precision, d, restart_len, reorth, gemm, fp64_products; /* the solve's opts  */
+  int64_t spmm_A, spmm_At; /* SpMM schedules in use (A, A^T; A^T is 0 in SPD mode)   */
+  uint64_t seed;
+  double eps, tol_eff;     /* perturbation strength; lock tolerance in use             */
+  double normA1, normAinf; /* ||A||_1, ||A||_inf of the handle (a check of the values) */
+  int64_t matvecs, restarts, nullity; /* progress: B applications, restarts, locked   */
+  int64_t k0;              /* retained Ritz vectors (the next cycle starts at block k0/d) */
+} ns_checkpoint_info;
+
+/* ns_read_checkpoint -- read and verify a checkpoint file on the host (no device
+ * work): its magic, its length and its FNV-1a checksum.  File layout: 8 bytes
+ * "NSCKPT01", the ns_checkpoint_info record, the solver state (host byte order),
+ * then the 64-bit checksum of everything before it, computed over little-endian
+ * 64-bit words (FNV-1a with the word in place of the byte; a tail shorter than
+ * 8 bytes is zero-padded).  NS_ERR_IO for a missing, short or corrupt file. */
+ns_status ns_read_checkpoint(const char* path, ns_checkpoint_info* info);
 
 /* Number of null vectors found by the last ns_solve. NS_ERR_STATE before a solve. */
 ns_status ns_nullity(const ns_handle* h, int64_t* N);

@@ -55,7 +55,9 @@ Readings of points the paper leaves open (the CUDA path takes the same readings)
   R11 stopping: s = (stamp_last - stamp_first) / max(1, (locked - first batch)/d),
       floored at dimK; stop when no Ritz value below 3 eps is left unlocked, no
       lock happened for more than stop_factor * s matvecs and the last cycle
-      locked nothing;
+      locked nothing.  Before the first lock there is no speed estimate; then the
+      smallest Ritz value must also have converged (residual within the lock
+      tolerance) at or above 3 eps, the direct test Sec. 4.3 starts from;
   R12 breakdown (sigma_min(Gamma) <= 100 u_d): the block is replaced by a fresh
       Gaussian block (Philox stream 2+k) orthogonalized against [X, Z], and
       Gamma is set to zero;
@@ -393,7 +395,8 @@ def lanczos_nullspace(A, mode: str, d: int, restart_len: int, tol: float = 1e-10
             s = float(R)
         s = max(s, float(R))
         since = st["matvecs"] - (ev[-1][0] if ev else 0)
-        if n_unl == 0 and nlock == 0 and since > stop_factor * s:
+        settled = bool(ev) or (theta[0] >= 3.0 * eps and resid[0] <= tol * normB_est)
+        if n_unl == 0 and nlock == 0 and since > stop_factor * s and settled:
             converged = True
             break
         if st["matvecs"] >= max_matvec:

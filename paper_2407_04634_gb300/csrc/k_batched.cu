@@ -826,7 +826,10 @@ __device__ void solve_instance(const BatchArgs& a, int inst, float* ws32, double
     sv = fmax(sv, (double)R);
     const long long since = matvecs - (ev_last >= 0 ? ev_last : 0);
     if (status) break;
-    if (n_unl == 0 && locked_now == 0 && (double)since > a.stop_factor * sv) break;
+    // before the first lock: also wait for the smallest Ritz value to converge at or
+    // above 3 eps (the direct test of Sec. 4.3)
+    const bool settled = ev_count > 0 || (S.th[0] >= 3.0 * a.eps && S.res[0] <= tol_eff * normB);
+    if (n_unl == 0 && locked_now == 0 && (double)since > a.stop_factor * sv && settled) break;
     if (matvecs >= max_mv) {
       status = 4;
       break;

@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "../../include/nullspace.h"
+#include "ns_checkpoint.cuh"
 #include "ns_common.cuh"
 #include "ns_kernels.cuh"
 
@@ -354,7 +355,8 @@ struct Solver {
   std::vector<std::pair<int64_t, int>> events;
   long long& launches;
 
-  Solver(ns_handle* hh, int R_, double tol, const ns_opts& oo)
+  // from: the checkpoint a resumed solve continues (its SpMM schedules replace the timing)
+  Solver(ns_handle* hh, int R_, double tol, const ns_opts& oo, const ns_checkpoint_info* from = nullptr)
       : h(hh), s(hh->stream), n(hh->n), m(hh->m), R(R_), nb(R_ / D), o(oo), launches(hh->launches) {
     eps = o.eps;
     const bool mixed = std::is_same<T, float>::value;
@@ -439,18 +441,34 @@ struct Solver {
       umma_img = Buf(h, restart_ozaki_scratch_bytes(n, R, R));
     ck(cudaMallocHost(&pin_d, sizeof(double) * (2 * (size_t)R + 64)), "cudaMallocHost");
     flags_h = reinterpret_cast<unsigned*>(pin_d + 2 * R + 32);
-    // SpMM schedule: lanes per row tuned on this matrix (operands: the basis buffers)
-    ck(cudaMemsetAsync(Z[1], 0, zbytes, s), "memset");
-    if (h->mode == NS_MODE_SPD) {
-      A.V = tune_lanczos(A, Z[1]);
+    if (from) {  // the schedules the checkpointed iteration ran with
+      A.V = checked_schedule(A, from->spmm_A, h->mode == NS_MODE_NORMAL);
+      if (h->mode == NS_MODE_NORMAL) At.V = checked_schedule(At, from->spmm_At, false);
+    } else if (o.spmm_schedule > 0) {
+      A.V = fixed_schedule(A, o.spmm_schedule);
+      if (h->mode == NS_MODE_NORMAL) At.V = fixed_schedule(At, o.spmm_schedule);
     } else {
-      A.V = tune_lanes<T, D>(A, Z[1], ybuf.as<T>(), s);
-      ck(cudaMemsetAsync(ybuf.p, 0, sizeof(T) * (size_t)m * D, s), "memset");
-      At.V = tune_lanczos(At, ybuf.as<T>());
+      // SpMM schedule: lanes per row tuned on this matrix (operands: the basis buffers)
+      ck(cudaMemsetAsync(Z[1], 0, zbytes, s), "memset");
+      if (h->mode == NS_MODE_SPD) {
+        A.V = tune_lanczos(A, Z[1]);
+      } else {
+        A.V = tune_lanes<T, D>(A, Z[1], ybuf.as<T>(), s);
+        ck(cudaMemsetAsync(ybuf.p, 0, sizeof(T) * (size_t)m * D, s), "memset");
+        At.V = tune_lanczos(At, ybuf.as<T>());
+      }
+      launches += (h->mode == NS_MODE_SPD ? 15 : 30);
     }
     if (getenv("NS_DEBUG")) fprintf(stderr, "[ns] lanes per row: A %d, A^T %d\n", A.V, At.V);
-    launches += (h->mode == NS_MODE_SPD ? 15 : 30);
     ck_launch("tune");
+  }
+  static int fixed_schedule(const Csr<T>& M, int sched) { return (sched == kSchedSell && !M.sptr) ? 8 : sched; }
+  // a schedule read from a checkpoint: one the kernels of this operand support
+  static int checked_schedule(const Csr<T>& M, int64_t v, bool plain) {
+    const bool ok = v == 1 || v == 2 || v == 4 || v == 8 || v == kSchedTma || (v == kSchedSell && M.sptr) ||
+                    (plain && v == 16);
+    if (!ok) throw Fail{NS_ERR_INVALID_ARG, "checkpoint SpMM schedule not usable on this handle"};
+    return (int)v;
   }
   ~Solver() {
     if (pin_d) cudaFreeHost(pin_d);
@@ -995,7 +1013,11 @@ struct Solver {
               el, (long long)restarts, (long long)matvecs, nlock, nsmall, n_unl, nk, pin_theta[0], pin_res[0], cnt[0],
               cnt[1]);
     }
-    if (n_unl == 0 && nlocked_now == 0 && (double)since > o.stop_factor * sv) return true;
+    // before the first lock there is no speed estimate: the smallest Ritz value must
+    // also have converged at or above 3 eps (the direct test of Sec. 4.3)
+    const bool settled =
+        !events.empty() || (pin_theta[0] >= 3.0 * eps && pin_res[0] <= tol_eff * normB_est);
+    if (n_unl == 0 && nlocked_now == 0 && (double)since > o.stop_factor * sv && settled) return true;
     return false;
   }
 
@@ -1005,10 +1027,115 @@ struct Solver {
   }
   void mat_small(const double* a, const double* b, double* c);
 
-  // ---- whole Lanczos phase ----
-  ns_status run(bool& converged) {
-    orthonormal_start();
+  // ---- checkpoint / resume at a thick restart (the state at the top of the cycle loop) ----
+  ns_checkpoint_info checkpoint_record(int k0) const {
+    ns_checkpoint_info c{};
+    c.version = kCkptVersion;
+    c.m = m;
+    c.n = n;
+    c.nnz = h->nnz;
+    c.mode = h->mode;
+    c.precision = std::is_same<T, float>::value ? NS_MIXED : NS_FP64;
+    c.d = D;
+    c.restart_len = R;
+    c.reorth = o.reorth;
+    c.gemm = o.gemm;
+    c.fp64_products = o.fp64_products;
+    c.spmm_A = A.V;
+    c.spmm_At = h->mode == NS_MODE_NORMAL ? At.V : 0;
+    c.seed = h->seed;
+    c.eps = eps;
+    c.tol_eff = tol_eff;
+    c.normA1 = h->normA1;
+    c.normAinf = h->normAinf;
+    c.matvecs = matvecs;
+    c.restarts = restarts;
+    c.nullity = nlock;
+    c.k0 = k0;
+    return c;
+  }
+  // host scalars of the iteration, in file order
+  struct HostState {
+    int64_t cur, cap, nlock, breakdowns, lock_events, ghosts, nevents, small_bytes;
+    double theta_max, u_d, bd_tol;
+  };
+  void save_checkpoint(int k0) {
+    sync();
+    CkptWriter w;
+    if (!w.open(o.checkpoint_path)) throw Fail{NS_ERR_IO, "cannot open checkpoint file for writing"};
+    const ns_checkpoint_info c = checkpoint_record(k0);
+    w.put(&c, sizeof c);
+    const HostState hs{cur, cap, nlock, breakdowns, lock_events, ghosts, (int64_t)events.size(), (int64_t)small.bytes,
+                       theta_max, u_d, bd_tol};
+    w.put(&hs, sizeof hs);
+    for (const auto& e : events) {
+      const int64_t ev[2] = {e.first, e.second};
+      w.put(ev, sizeof ev);
+    }
+    w.put(xtheta_h.data(), sizeof(double) * nlock);
+    w.put(xrho_h.data(), sizeof(double) * nlock);
+    ck(w.put_device(small.p, small.bytes, s), "checkpoint d2h");
+    ck(w.put_device(wxbuf.p, wxbuf.bytes, s), "checkpoint d2h");
+    ck(w.put_device(Z[cur], sizeof(T) * (size_t)n * (k0 + D), s), "checkpoint d2h");
+    ck(w.put_device(X(), sizeof(T) * (size_t)n * nlock, s), "checkpoint d2h");
+    if (!w.commit()) throw Fail{NS_ERR_IO, "checkpoint write failed"};
+  }
+  // restores the state written by save_checkpoint; returns k0
+  int restore_checkpoint(CkptReader& r, const ns_checkpoint_info& c) {
+    auto bad = [](const char* what) { return Fail{NS_ERR_IO, std::string("checkpoint: ") + what}; };
+    HostState hs{};
+    if (!r.get(&hs, sizeof hs)) throw bad("short file");
+    const int k0 = (int)c.k0;
+    if (c.k0 < D || c.k0 > R - 2 * D || c.k0 % D || (hs.cur != 0 && hs.cur != 1) || hs.nlock < 0 ||
+        hs.nlock != c.nullity || hs.cap < std::max<int64_t>(hs.nlock, 1) || hs.cap > n || hs.nevents < 0 ||
+        hs.nevents > c.restarts || hs.small_bytes != (int64_t)small.bytes || c.matvecs < 0 || c.restarts < 1)
+      throw bad("inconsistent state");
+    if (hs.cap != cap) {  // the locked store at the checkpoint's capacity (the W rows depend on it)
+      xbuf = Buf(h, sizeof(T) * (size_t)n * hs.cap);
+      cap = (int)hs.cap;
+      alloc_proj();
+      alloc_locked_meta(0);
+    }
+    events.clear();
+    for (int64_t i = 0; i < hs.nevents; ++i) {
+      int64_t ev[2];
+      if (!r.get(ev, sizeof ev)) throw bad("short file");
+      events.emplace_back(ev[0], (int)ev[1]);
+    }
+    nlock = (int)hs.nlock;
+    xtheta_h.assign(nlock, 0.0);
+    xrho_h.assign(nlock, 0.0);
+    if (!r.get(xtheta_h.data(), sizeof(double) * nlock) || !r.get(xrho_h.data(), sizeof(double) * nlock))
+      throw bad("short file");
+    ck(r.get_device(small.p, small.bytes, s), "checkpoint h2d");
+    ck(r.get_device(wxbuf.p, wxbuf.bytes, s), "checkpoint h2d");
+    cur = (int)hs.cur;
+    ck(r.get_device(Z[cur], sizeof(T) * (size_t)n * (k0 + D), s), "checkpoint h2d");
+    ck(r.get_device(X(), sizeof(T) * (size_t)n * nlock, s), "checkpoint h2d");
+    if (!r.ok() || !r.finish()) throw bad("short or corrupt file (checksum)");
+    // flags, reduction tickets and the tensor-core error word are zero between cycles
+    ck(cudaMemsetAsync(flags, 0, 8 * sizeof(double), s), "memset");
+    breakdowns = hs.breakdowns;
+    lock_events = hs.lock_events;
+    ghosts = hs.ghosts;
+    theta_max = hs.theta_max;
+    u_d = hs.u_d;
+    bd_tol = hs.bd_tol;
+    matvecs = c.matvecs;
+    restarts = c.restarts;
+    resumed_at = c.restarts;
+    sync();
+    return k0;
+  }
+  int64_t resumed_at = -1;
+
+  // ---- whole Lanczos phase; `from`: a checkpoint to continue instead of a new start ----
+  ns_status run(bool& converged, CkptReader* from = nullptr, const ns_checkpoint_info* rec = nullptr) {
     int k0 = 0;
+    if (from)
+      k0 = restore_checkpoint(*from, *rec);
+    else
+      orthonormal_start();
     const int64_t maxmv = o.max_matvec > 0 ? o.max_matvec : std::min<int64_t>(100 * n + 50 * R, 1000000);
     converged = false;
     while (true) {
@@ -1019,7 +1146,9 @@ struct Solver {
         converged = true;
         break;
       }
-      if (matvecs >= maxmv) break;
+      const bool stop = matvecs >= maxmv;
+      if (o.checkpoint_every > 0 && (stop || restarts % o.checkpoint_every == 0)) save_checkpoint(k0);
+      if (stop) break;
     }
     return converged ? NS_OK : NS_ERR_NOT_CONVERGED;
   }
@@ -1206,9 +1335,22 @@ static ns_status solve_typed(ns_handle* h, int R, double tol, const ns_opts& o) 
   bool conv = false;
   int64_t N = 0;
   h->prof.reset(o.profile, s);
-  Solver<T, D> S(h, R, tol, o);
+  CkptReader rd;
+  ns_checkpoint_info rec{};
+  if (o.resume) {
+    if (rd.open(o.checkpoint_path, &rec) != NS_OK) throw Fail{NS_ERR_IO, "checkpoint missing or unreadable"};
+    if (rec.m != h->m || rec.n != h->n || rec.nnz != h->nnz || rec.mode != h->mode || rec.seed != h->seed ||
+        rec.normA1 != h->normA1 || rec.normAinf != h->normAinf)
+      throw Fail{NS_ERR_INVALID_ARG, "checkpoint of another matrix or seed"};
+    if (rec.precision != (std::is_same<T, float>::value ? NS_MIXED : NS_FP64) || rec.d != D ||
+        rec.restart_len != R || rec.reorth != o.reorth || rec.gemm != o.gemm ||
+        rec.fp64_products != o.fp64_products || rec.eps != o.eps)
+      throw Fail{NS_ERR_INVALID_ARG, "checkpoint of a solve with other d, restart_len or opts"};
+  }
+  Solver<T, D> S(h, R, tol, o, o.resume ? &rec : nullptr);
+  if (o.resume && rec.tol_eff != S.tol_eff) throw Fail{NS_ERR_INVALID_ARG, "checkpoint of a solve with another tol"};
   cudaEventRecord(e0, s);
-  st = S.run(conv);
+  st = S.run(conv, o.resume ? &rd : nullptr, &rec);
   cudaEventRecord(e1, s);
   N = S.nlock;
   // FP64 basis
@@ -1301,6 +1443,8 @@ static ns_status solve_typed(ns_handle* h, int R, double tol, const ns_opts& o) 
   x.t_lanczos_ms = t1;
   x.t_refine_ms = t2;
   x.t_total_ms = t1 + t2;
+  x.d = D;
+  x.resumed_at = S.resumed_at;
   h->N = N;
   h->solved = true;
   cudaEventDestroy(e0);
@@ -1477,6 +1621,10 @@ void ns_default_opts(ns_opts* o) {
   o->profile = 0;
   o->gemm = NS_GEMM_DEFAULT;
   o->fp64_products = 0;
+  o->spmm_schedule = 0;
+  o->checkpoint_every = 0;
+  o->resume = 0;
+  o->checkpoint_path = nullptr;
 }
 
 static ns_status set_err(ns_handle* h, ns_status st, const std::string& msg) {
@@ -1621,9 +1769,17 @@ ns_status ns_create(ns_handle** out, int64_t m, int64_t n, const int64_t* rowptr
   return NS_OK;
 }
 
+// Sec. 5.3.1: block size dim K / 16, as the largest supported d that divides dim K
+static int block_size_rule(int restart_len) {
+  for (int d : {8, 4, 2})
+    if (d <= std::max(1, restart_len / 16) && restart_len % d == 0 && restart_len >= 3 * d) return d;
+  return 1;
+}
+
 ns_status ns_solve(ns_handle* h, int d, int restart_len, double tol, const ns_opts* opts) {
   if (!h) return NS_ERR_INVALID_ARG;
-  if (!(d == 1 || d == 2 || d == 4 || d == 8)) return set_err(h, NS_ERR_INVALID_ARG, "d must be 1, 2, 4 or 8");
+  if (d == 0) d = block_size_rule(restart_len);
+  if (!(d == 1 || d == 2 || d == 4 || d == 8)) return set_err(h, NS_ERR_INVALID_ARG, "d must be 0, 1, 2, 4 or 8");
   if (restart_len % d || restart_len < 3 * d || restart_len > 512)
     return set_err(h, NS_ERR_INVALID_ARG, "restart_len must be a multiple of d in [3d, 512]");
   if (!(tol > 0.0)) return set_err(h, NS_ERR_INVALID_ARG, "tol must be positive");
@@ -1639,6 +1795,14 @@ ns_status ns_solve(ns_handle* h, int d, int restart_len, double tol, const ns_op
       (o.gemm == NS_GEMM_TC_EXACT && !restart_ozaki_supported(restart_len, 1)))
     return set_err(h, NS_ERR_INVALID_ARG,
                    "gemm: 0..4; TC2/TC3 on the mixed path, TC_EXACT on the FP64 path with restart_len <= 208");
+  {
+    const int sc = o.spmm_schedule;
+    if (!(sc == 0 || sc == 1 || sc == 2 || sc == 4 || sc == 8 || sc == kSchedTma || sc == kSchedSell))
+      return set_err(h, NS_ERR_INVALID_ARG, "spmm_schedule must be 0, 1, 2, 4, 8, 64 or 128");
+    if (o.checkpoint_every < 0 || !(o.resume == 0 || o.resume == 1) ||
+        ((o.checkpoint_every > 0 || o.resume) && (!o.checkpoint_path || !*o.checkpoint_path)))
+      return set_err(h, NS_ERR_INVALID_ARG, "checkpoint_every >= 0, resume 0 or 1, both need checkpoint_path");
+  }
   h->err.clear();
   h->solved = false;
   h->launches = 0;
@@ -1670,6 +1834,17 @@ ns_status ns_solve(ns_handle* h, int d, int restart_len, double tol, const ns_op
     cudaGetLastError();
     return set_err(h, f.st, f.msg);
   }
+}
+
+ns_status ns_read_checkpoint(const char* path, ns_checkpoint_info* info) {
+  if (!path || !info) return NS_ERR_INVALID_ARG;
+  CkptReader r;
+  ns_checkpoint_info c{};
+  const ns_status st = r.open(path, &c);
+  if (st != NS_OK) return st;
+  if (!r.skip_rest() || !r.finish()) return NS_ERR_IO;
+  *info = c;
+  return NS_OK;
 }
 
 ns_status ns_nullity(const ns_handle* h, int64_t* N) {

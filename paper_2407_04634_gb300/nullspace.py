@@ -9,6 +9,7 @@ library cannot be built or loaded.
 from __future__ import annotations
 
 import ctypes as C
+import os
 from dataclasses import dataclass
 
 import numpy as np
@@ -16,9 +17,9 @@ import numpy as np
 from . import build as _build
 
 NS_OK, NS_ERR_INVALID_ARG, NS_ERR_OOM, NS_ERR_CUDA, NS_ERR_NOT_CONVERGED, NS_ERR_TIMEOUT, NS_ERR_STATE, \
-    NS_ERR_REFINE, NS_ERR_NUMERICAL = range(9)
+    NS_ERR_REFINE, NS_ERR_NUMERICAL, NS_ERR_IO = range(10)
 STATUS = {0: "NS_OK", 1: "NS_ERR_INVALID_ARG", 2: "NS_ERR_OOM", 3: "NS_ERR_CUDA", 4: "NS_ERR_NOT_CONVERGED",
-          5: "NS_ERR_TIMEOUT", 6: "NS_ERR_STATE", 7: "NS_ERR_REFINE", 8: "NS_ERR_NUMERICAL"}
+          5: "NS_ERR_TIMEOUT", 6: "NS_ERR_STATE", 7: "NS_ERR_REFINE", 8: "NS_ERR_NUMERICAL", 9: "NS_ERR_IO"}
 MODE = {"normal": 0, "spd": 1}
 PRECISION = {"fp64": 0, "mixed": 1, "fp64_pairs": 2}
 REORTH = {"partial": 0, "full": 1}
@@ -37,7 +38,8 @@ class NsOpts(C.Structure):
                 ("stop_factor", C.c_double), ("lock_tol_mixed", C.c_double), ("refine", C.c_int),
                 ("refine_tol", C.c_double), ("refine_maxit", C.c_int), ("refine_chunk", C.c_int),
                 ("use_graphs", C.c_int), ("profile", C.c_int), ("batch_block", C.c_int), ("gemm", C.c_int),
-                ("fp64_products", C.c_int)]
+                ("fp64_products", C.c_int), ("spmm_schedule", C.c_int), ("checkpoint_every", C.c_int),
+                ("resume", C.c_int), ("checkpoint_path", C.c_char_p)]
 
 
 class NsStats(C.Structure):
@@ -45,7 +47,18 @@ class NsStats(C.Structure):
                 ("reorth_Z", C.c_int64), ("breakdowns", C.c_int64), ("lock_events", C.c_int64),
                 ("ghosts", C.c_int64), ("refine_iters_max", C.c_int64), ("kernel_launches", C.c_int64),
                 ("normB", C.c_double), ("normA", C.c_double), ("u_d", C.c_double), ("refine_resid_max", C.c_double), ("orth_before", C.c_double), ("orth_after", C.c_double),
-                ("t_lanczos_ms", C.c_double), ("t_refine_ms", C.c_double), ("t_total_ms", C.c_double)]
+                ("t_lanczos_ms", C.c_double), ("t_refine_ms", C.c_double), ("t_total_ms", C.c_double),
+                ("d", C.c_int64), ("resumed_at", C.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class NsCheckpointInfo(C.Structure):
+    _fields_ = [(f, C.c_int64) for f in ("version", "m", "n", "nnz", "mode", "precision", "d", "restart_len",
+                                         "reorth", "gemm", "fp64_products", "spmm_A", "spmm_At")] + \
+               [("seed", C.c_uint64)] + [(f, C.c_double) for f in ("eps", "tol_eff", "normA1", "normAinf")] + \
+               [(f, C.c_int64) for f in ("matvecs", "restarts", "nullity", "k0")]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -75,6 +88,7 @@ SIGNATURES = {
     "ns_create": (C.c_int, [C.POINTER(_P), C.c_int64, C.c_int64, _P, _P, _P, C.c_int, C.c_int, C.c_uint64,
                             C.c_int, C.POINTER(NsEnv)]),
     "ns_solve": (C.c_int, [_P, C.c_int, C.c_int, C.c_double, C.POINTER(NsOpts)]),
+    "ns_read_checkpoint": (C.c_int, [C.c_char_p, C.POINTER(NsCheckpointInfo)]),
     "ns_nullity": (C.c_int, [_P, C.POINTER(C.c_int64)]),
     "ns_basis": (C.c_int, [_P, _P, C.c_int64, C.c_int]),
     "ns_stats": (C.c_int, [_P, C.POINTER(NsStats)]),
@@ -141,10 +155,21 @@ def default_opts(**kw) -> NsOpts:
             v = REORTH[v]
         if k == "gemm" and isinstance(v, str):
             v = GEMM[v]
+        if k == "checkpoint_path" and v is not None:
+            v = os.fsencode(v)
         if not hasattr(o, k):
             raise TypeError(f"unknown option {k}")
         setattr(o, k, v)
     return o
+
+
+def read_checkpoint(path) -> dict:
+    """The record of a checkpoint file written by a solve (checked: magic, length, checksum)."""
+    info = NsCheckpointInfo()
+    st = load().ns_read_checkpoint(os.fsencode(path), C.byref(info))
+    if st != NS_OK:
+        raise NullspaceError(st, f"ns_read_checkpoint({path!r})")
+    return info.as_dict()
 
 
 def torch_env():

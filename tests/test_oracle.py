@@ -360,3 +360,18 @@ def test_omega_bounds_with_ritz_norm_estimate(d):
     assert r.N == ref.N == 4
     assert r.u_d < 0.5 * ref.u_d  # the Ritz estimate is much tighter than R9 here
     assert worst[0] <= 1.0, worst[0]
+
+
+def test_slow_start_waits_for_the_first_lock():
+    """d = dim K / 8 (d = 8, dim K = 64): the first cycles converge nothing, so there is
+    no speed estimate yet; the termination test of Sec. 4.3 must not stop the iteration
+    before the smallest Ritz value has settled, and the planted nullity is found for
+    every block size of the sweep (Sec. 5.3.1), with more B applications for larger d."""
+    w = rectangular_copies(35, 6000, 4000, 10)
+    mv = {}
+    for d in (8, 2):
+        r = lanczos_nullspace(w.A.to_scipy(), "normal", d, 64, tol=1e-10, seed=11)
+        assert r.N == 10, d
+        assert principal_sine(r.X, copy_pair_basis(4000, w.copy_pairs)) <= 1e-8
+        mv[d] = r.stats["matvecs"]
+    assert mv[8] > mv[2]
