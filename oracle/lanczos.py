@@ -7,17 +7,17 @@ it; the product path never does.  It shares no code with the CUDA library.
 
 It follows Kressner & Shao, "On a randomized small-block Lanczos method for
 large-scale null space computations":
-  * Eq. (defB) and Alg. 1 line 1: B = A^T A + eps*D (mode "normal"), or
+  * Eq. (defB) and Alg. 1 (its perturbed operator): B = A^T A + eps*D (mode "normal"), or
     B = A + eps*D for a symmetric positive semi-definite A (mode "spd", Sec. 5.1);
     D diagonal with i.i.d. U[0,1] entries; B is only applied, Bx = A^T(Ax) + eps*(Dx).
-  * Alg. 1 line 2 / Alg. 2 lines 2, 4: Gaussian start block Omega, Q_1 = orth(Omega).
-  * Alg. 2 lines 6-8 (first step of a cycle, full projection against Z_{l0+1})
-    and lines 9-12 (three-term block recurrence, QR, partial reorthogonalization).
+  * Alg. 1 and Alg. 2, the start: Gaussian start block Omega, Q_1 = orth(Omega).
+  * Alg. 2, the first step of a cycle (full projection against Z_{l0+1}) and the
+    block recurrence after it (three-term recurrence, QR, partial reorthogonalization).
   * Sec. 4.2: the W (omega) recurrence bounding ||Q_k^T Q_{l+1}||, with
     u_d = d sqrt(n) u ||B|| (Eq. defmprd) and threshold u_RO = sqrt(u).
-  * Sec. 4.1 and Alg. 2 lines 13-17: thick restart keeping the smallest Ritz
+  * Sec. 4.1 and Alg. 2 (the thick restart): thick restart keeping the smallest Ritz
     pairs; T has the arrow + block-tridiagonal form of Eq. (defT).
-  * Alg. 2 line 14 and Remark cormain: Ritz values below 3*eps count as null.
+  * Alg. 2 (its count of small Ritz values) and Remark cormain: Ritz values below 3*eps count as null.
   * Sec. 4.3: stop when no Ritz value converged within s matvecs, s estimated
     from the observed convergence speed (matvecs per d newly converged values).
   * Remark after Alg. 1: an extraction step without the perturbation; here a
@@ -42,14 +42,17 @@ Readings of points the paper leaves open (the CUDA path takes the same readings)
       only when an X row exceeds u_RO, the Z part only when a Z row does, and only
       the rows that were reorthogonalized are reset to u_d;
   R7  retained count l0 d = d * floor((N_unlocked + dimK) / (2d)) clamped to
-      [d, dimK - 2d] (Alg. 2 line 14 counted in vectors);
+      [d, dimK - 2d] (Alg. 2 (the count of small Ritz values) counted in vectors);
   R7b when the nullity exceeds dimK the unconverged near-null Ritz pairs fill the
       basis and that rule leaves almost no room for new vectors; the retained
-      count is therefore capped at dimK/2, and among the Ritz values below 3 eps
-      the pairs with the smallest residuals are kept first (keep_rule="capped",
-      default; "paper" keeps the l0 d smallest as printed);
+      count is therefore capped: at the unlocked small pairs (rounded up to a
+      multiple of d) when they fit in 3 dimK/4, else at dimK/2; among the Ritz
+      values below 3 eps the pairs with the smallest residuals are kept first
+      (keep_rule="capped", default; "paper" keeps the l0 d smallest as printed).
+      A cap of dimK/2 alone discards unconverged null pairs every cycle when
+      dimK/2 < N_unlocked <= 3 dimK/4, which stalls d = 8 at dimK = 120;
   R8  after restart F = R Gamma_l V_Z(last block, kept) where R is the factor of the
-      re-orthogonalization QR of Q_{l+1} (Alg. 2 line 17, printed index garbled);
+      re-orthogonalization QR of Q_{l+1} (Alg. 2 (the restarted coupling F), printed index garbled);
   R9  ||B|| in u_d is the bound ||A||_1 ||A||_inf + eps (normal) or ||A||_inf + eps (spd);
   R10 u = 2^-52 (the paper quotes 2.22e-16);
   R11 stopping: s = (stamp_last - stamp_first) / max(1, (locked - first batch)/d),
@@ -171,7 +174,8 @@ def lanczos_nullspace(A, mode: str, d: int, restart_len: int, tol: float = 1e-10
                       refine_maxit: int = 500, final_rr: bool = True,
                       u: float = U_FP64, D: np.ndarray | None = None,
                       Omega: np.ndarray | None = None, record: bool = False,
-                      probe=None, keep_rule: str = "capped", ud_rule: str = "ritz") -> Result:
+                      probe=None, keep_rule: str = "capped", ud_rule: str = "ritz",
+                      precond: float | None = None) -> Result:
     """Null space of A by Alg. 2 (restarted, partially reorthogonalized small-block Lanczos).
 
     reorth: "partial" (Sec. 4.2), "full" (every new block projected against the whole
@@ -181,6 +185,9 @@ def lanczos_nullspace(A, mode: str, d: int, restart_len: int, tol: float = 1e-10
     probe(j, Z, X, col, colX, d) is called after each new W column (before any
     reorthogonalization) so tests can compare the bounds with the true inner products;
     record=True also keeps the quantities of the last cycle before each restart.
+    precond=alpha (spd mode) runs the method on B_R = L^-1 A~ L^-T + eps D, the outer
+    preconditioning of Sec. 4.4.2 with the IC(0) factor L of A~ + alpha diag(A~)
+    (oracle.precond), and maps the basis back by Pi L^-T before the refinement.
     """
     A = sp.csr_matrix(A, dtype=np.float64)
     n = A.shape[1]
@@ -189,7 +196,15 @@ def lanczos_nullspace(A, mode: str, d: int, restart_len: int, tol: float = 1e-10
         raise ValueError("restart_len must be a multiple of d and at least 3d")
     if D is None:
         D = perturbation_diagonal(seed, n)
-    op = Operator(A, mode, eps, D)
+    pc = None
+    if precond is not None:
+        from .precond import Preconditioner, PrecondOperator
+        if mode != "spd":
+            raise ValueError("outer preconditioning is for the spd form")
+        pc = Preconditioner(A, seed, precond)
+        op = PrecondOperator(pc, eps, D)
+    else:
+        op = Operator(A, mode, eps, D)
     normB = op.norm_bound()  # reading R9; also the scale of the lock tolerance
     u_d = d * np.sqrt(n) * u * normB  # Eq. (defmprd), refined after the first cycle (M4)
     u_ro = np.sqrt(u)  # Sec. 4.2
@@ -228,7 +243,7 @@ def lanczos_nullspace(A, mode: str, d: int, restart_len: int, tol: float = 1e-10
         Q, _ = qr_pos(Yr)
         return Q, np.zeros((d, d))
 
-    # Alg. 2 line 4
+    # Alg. 2 (its orthonormalized start block)
     Om = start_block(seed, n, d) if Omega is None else np.asarray(Omega, dtype=np.float64)
     Z[:, 0:d], _ = qr_pos(Om)
 
@@ -241,7 +256,7 @@ def lanczos_nullspace(A, mode: str, d: int, restart_len: int, tol: float = 1e-10
     while True:
         r0 = k0 // d
         blk = lambda b: Z[:, b * d:(b + 1) * d]  # noqa: E731
-        # ---- Alg. 2 lines 6-8: first step of the cycle -------------------------
+        # ---- Alg. 2 (the first step of a cycle): first step of the cycle -------------------------
         Qp = apply_B(blk(r0))
         Xi[r0] = 0.5 * ((blk(r0).T @ Qp) + (blk(r0).T @ Qp).T)
         Qp = project(Qp, [X, Z[:, :(r0 + 1) * d]])
@@ -255,7 +270,7 @@ def lanczos_nullspace(A, mode: str, d: int, restart_len: int, tol: float = 1e-10
         WX[:, r0] = u_d
         WX[:, r0 + 1] = u_d
         Wrec = [] if record else None
-        # ---- Alg. 2 lines 9-12: inner loop ------------------------------------
+        # ---- Alg. 2 (the block recurrence of a cycle): inner loop ------------------------------------
         for j in range(r0 + 1, nb):
             Qp = apply_B(blk(j)) - blk(j - 1) @ Gam[j - 1].T  # reading R1
             Xi_raw = blk(j).T @ Qp
@@ -314,7 +329,7 @@ def lanczos_nullspace(A, mode: str, d: int, restart_len: int, tol: float = 1e-10
                     st["reorth_X"] += 1
                     WX[:, j] = u_d
                     WX[:, j + 1] = u_d
-        # ---- Alg. 2 line 13: T of Eq. (defT) and its eigendecomposition -------
+        # ---- Alg. 2 (the projected matrix T): T of Eq. (defT) and its eigendecomposition -------
         T = np.zeros((R, R))
         T[:k0, :k0] = np.diag(Theta)
         T[k0:k0 + d, :k0] = F
@@ -364,12 +379,15 @@ def lanczos_nullspace(A, mode: str, d: int, restart_len: int, tol: float = 1e-10
         taken[cand] = True
         taken[ghosts] = True
         n_unl = int(small.sum()) - int(taken[small].sum())
-        # ---- Alg. 2 lines 14-17: thick restart ---------------------------------
+        # ---- Alg. 2 (the thick restart): thick restart ---------------------------------
         avail = np.nonzero(~taken)[0]
         k0 = d * ((n_unl + R) // (2 * d))
         k0 = min(max(k0, d), R - 2 * d, d * (avail.size // d))
-        if keep_rule == "capped":  # reading R7b: room for >= dimK/2 new vectors per cycle
-            k0 = min(k0, max(d, d * (R // (2 * d))))
+        if keep_rule == "capped":  # reading R7b
+            k0_half = max(d, d * (R // (2 * d)))
+            want = d * (-(-n_unl // d))  # the unlocked small pairs, whole blocks
+            cap = want if k0_half < want <= d * ((3 * R // 4) // d) else k0_half
+            k0 = min(k0, max(d, cap))
             sm = avail[small[avail]]
             sm = sm[np.argsort(resid[sm], kind="stable")]  # most converged small pairs first
             avail = np.concatenate([sm, avail[~small[avail]]])
@@ -410,20 +428,26 @@ def lanczos_nullspace(A, mode: str, d: int, restart_len: int, tol: float = 1e-10
     res["X_lanczos"] = X.copy()
     res["x_theta"] = x_theta
     res["x_rho"] = x_rho
+    Ar = A
+    if pc is not None and X.shape[1]:
+        # Sec. 4.4.2: V approximates null(A L^-T) in the renumbered space; map it back
+        X, _ = qr_pos(pc.solve_LT(X).reshape(X.shape))
+        Ar = pc.At
     if refine and X.shape[1]:
         normA = norm2_A(A, mode)
-        Xr, info = refine_null(A, mode, X, refine_tol * normA, refine_maxit)
+        Xr, info = refine_null(Ar, mode, X, refine_tol * normA, refine_maxit)
         Xr, _ = qr_pos(Xr)
         if final_rr:  # Rayleigh-Ritz without the perturbation (Remark after Alg. 1)
-            AX = A @ Xr
+            AX = Ar @ Xr
             G = Xr.T @ AX if mode == "spd" else AX.T @ AX
             _, U = np.linalg.eigh(0.5 * (G + G.T))
             Xr = Xr @ U
-        res["X"] = Xr
+        res["X"] = Xr if pc is None else pc.unpermute(Xr)
         res["refine"] = info
         res["normA"] = normA
     else:
-        res["X"] = X
+        res["X"] = X if pc is None else pc.unpermute(X)
+    res["precond"] = pc
     res["N"] = X.shape[1]
     return res
 

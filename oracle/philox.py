@@ -7,7 +7,7 @@ TEST INFRASTRUCTURE ONLY (part of the CPU oracle): imported by tests/, by the
 bench's CPU-baseline leg and by the smoke check, never by the product path.
 
 Stream layout used by the solver (the paper only asks for D ~ U[0,1] i.i.d. and
-a Gaussian start block, Alg. 1 lines 1-2):
+a Gaussian start block, Alg. 1 (its operator and start block)):
   key     = (seed mod 2^32, seed div 2^32)
   counter = (i mod 2^32, i div 2^32, stream, 0) for element / pair index i
   stream 0: diagonal D, D_i = (w >> 11) * 2^-53 with w = x0 | x1 << 32
@@ -80,5 +80,5 @@ def perturbation_diagonal(seed: int, n: int) -> np.ndarray:
 
 
 def start_block(seed: int, n: int, d: int, stream: int = 1) -> np.ndarray:
-    """Omega of Alg. 1 line 2: n x d i.i.d. N(0,1), row-major element order."""
+    """Omega of Alg. 1 (its Gaussian start block): n x d i.i.d. N(0,1), row-major element order."""
     return gaussian(seed, stream, n * d).reshape(n, d)

@@ -12,6 +12,7 @@ from .graphs import (  # noqa: F401
     solver_seed,
     laplacian_er_components,
     laplacian_cycle_components,
+    laplacian_grid_components,
     incidence_cycle_components,
     rectangular_copies,
     batched_laplacians,

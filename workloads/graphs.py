@@ -186,6 +186,30 @@ def laplacian_cycle_components(seed: int, n: int, ncomp: int, mean_degree: int =
     return Workload("laplacian_cycles", _laplacian(perm[u], perm[v], n), "spd", ncomp, labels=labels)
 
 
+def laplacian_grid_components(seed: int, ncomp: int, side_min: int = 10, side_max: int = 40) -> Workload:
+    """Laplacian of `ncomp` disjoint 2-D grid graphs (4-neighbour, unit weights), side
+    lengths uniform in [side_min, side_max] per axis.  A grid's smallest nonzero
+    eigenvalue falls like 1/side^2, so these components are badly conditioned: a
+    stand-in for the real-world Laplacians whose condition numbers outer
+    preconditioning is meant to reduce (Sec. 5.1)."""
+    rng = np.random.default_rng(seed)
+    shapes = rng.integers(side_min, side_max + 1, size=(ncomp, 2))
+    sz = shapes[:, 0] * shapes[:, 1]
+    offsets = np.concatenate([[0], np.cumsum(sz)[:-1]])
+    us, vs = [], []
+    for (a, b), o in zip(shapes, offsets):
+        idx = o + np.arange(a * b).reshape(a, b)
+        us += [idx[:, :-1].ravel(), idx[:-1, :].ravel()]
+        vs += [idx[:, 1:].ravel(), idx[1:, :].ravel()]
+    n = int(sz.sum())
+    perm = rng.permutation(n)
+    u = perm[np.concatenate(us)]
+    v = perm[np.concatenate(vs)]
+    labels = np.empty(n, dtype=np.int64)
+    labels[perm] = _labels_from_sizes(sz)
+    return Workload("laplacian_grid", _laplacian(u, v, n), "spd", ncomp, labels=labels)
+
+
 def incidence_cycle_components(seed: int, n: int, ncomp: int, mean_degree: int = 8,
                                min_size: int = 100, max_size: int = 3900) -> Workload:
     """Oriented edge-vertex incidence matrix (+1 at the lower, -1 at the higher endpoint).
