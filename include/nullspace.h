@@ -108,6 +108,14 @@ typedef struct {
   int resume;          /* 1: ns_solve continues from the state in checkpoint_path instead of
                           drawing a start block; 0 = new solve (default)                  */
   const char* checkpoint_path; /* file of checkpoint_every / resume (NULL = none)          */
+  int precond;         /* NS_MODE_SPD only: 1 = outer preconditioning (Sec. 4.4.2), the
+                          method runs on B_R = L^-1 A~ L^-T + eps D with A~ = Pi^T A Pi
+                          (Pi: renumbering by a Jones-Plassmann colouring of A's graph,
+                          priorities from Philox stream 0x7FFFFFFF) and L the zero-fill
+                          incomplete Cholesky factor of A~ + precond_shift diag(A~); the
+                          basis is mapped back by Pi L^-T, re-orthonormalized and refined
+                          against A.  0 = none (default)                                */
+  double precond_shift;/* diagonal compensation of the factor (Eq. defichol: 0.1, default) */
 } ns_opts;
 
 /* Kernel of the thick-restart product Z V_Z (ns_opts.gemm, ns_restart_product). */
@@ -154,7 +162,7 @@ typedef struct ns_handle ns_handle;
 void ns_default_opts(ns_opts* o);
 
 /* ns_create -- copy A (m x n CSR) to the device, build A^T (normal mode) by a
- * stable counting sort, bound ||B|| and draw D (Alg. 2 line 1, Eq. defB).  The
+ * stable counting sort, bound ||B|| and draw D (Alg. 2 (its perturbed operator), Eq. defB).  The
  * problem statement of Sec. 1.1: a sparse A is given, its null space is sought.
  *   rowptr  : m+1 int64, rowptr[0] = 0, non-decreasing, rowptr[m] = nnz
  *   colind  : nnz int32 in [0, n)
@@ -191,7 +199,7 @@ ns_status ns_create(ns_handle** out, int64_t m, int64_t n, const int64_t* rowptr
  * NS_ERR_NUMERICAL (a reorthogonalized block lost rank), or an error.
  * May be called again on the same handle (new solve, same D and start seed).
  * Checkpoints (opts checkpoint_every, resume, checkpoint_path): at a thick restart
- * (Alg. 2 line 17) the whole state of the iteration is the retained Ritz vectors
+ * (Alg. 2 (the restarted coupling F)) the whole state of the iteration is the retained Ritz vectors
  * and the next block, the projected matrix's arrow part, the W rows, the locked
  * vectors with their Ritz values and residuals, the counters and the SpMM
  * schedules.  A checkpoint holds exactly that (written to checkpoint_path + ".tmp",
@@ -219,6 +227,7 @@ typedef struct {
   double normA1, normAinf; /* ||A||_1, ||A||_inf of the handle (a check of the values) */
   int64_t matvecs, restarts, nullity; /* progress: B applications, restarts, locked   */
   int64_t k0;              /* retained Ritz vectors (the next cycle starts at block k0/d) */
+  double precond;          /* precond_shift of a preconditioned solve, 0 without          */
 } ns_checkpoint_info;
 
 /* ns_read_checkpoint -- read and verify a checkpoint file on the host (no device
@@ -277,7 +286,7 @@ ns_status ns_get_transpose(const ns_handle* h, int64_t* rowptr, int32_t* colind,
 ns_status ns_get_perturbation(const ns_handle* h, double* D);
 
 /* Draw the n x d start block Omega (row-major, Philox stream 1, Box-Muller) into
- * host memory, exactly as ns_solve draws it (Alg. 2 line 2). */
+ * host memory, exactly as ns_solve draws it (Alg. 2 (its Gaussian start block)). */
 ns_status ns_start_block(const ns_handle* h, int d, double* Omega);
 
 /* Y = B X (Eq. defB) for an n x d row-major block, 1 <= d <= 8.
@@ -295,6 +304,38 @@ ns_status ns_start_block(const ns_handle* h, int d, double* Omega);
  * A bounded device wait that expires gives NS_ERR_TIMEOUT (no hang). */
 ns_status ns_apply_B(ns_handle* h, int d, const double* X, double* Y, double eps,
                      int precision, int on_device, int schedule);
+
+/* ns_precond_build -- build (or reuse) the outer preconditioner of ns_solve's
+ * opts.precond (Sec. 4.4.2, Eq. defichol) on this handle, exposed so that each step
+ * can be checked on its own.  NS_MODE_SPD only (else NS_ERR_STATE).
+ *   Colouring: Jones-Plassmann rounds on the device; vertex v's priority is the
+ *   uniform draw v of Philox stream 0x7FFFFFFF (key: the handle's seed), ties by
+ *   index; in each round every uncoloured vertex that beats all its uncoloured
+ *   neighbours takes the smallest colour none of its coloured neighbours has.
+ *   Renumbering: perm[new] = old, vertices ordered by colour, then by index.
+ *   Factor: L, the zero-fill incomplete Cholesky factor of A~ + shift diag(A~),
+ *   A~ = Pi^T A Pi, computed on the device one colour at a time.
+ *   color   : n int32 (original numbering), may be NULL
+ *   perm    : n int64, may be NULL
+ *   nnz_L   : entries of L (diagonal included), may be NULL
+ *   ncolors : colours used, may be NULL
+ * A new shift refactors.  NS_ERR_NUMERICAL when a pivot is not positive (raise the
+ * shift); NS_ERR_INVALID_ARG for a negative or non-finite shift. */
+ns_status ns_precond_build(ns_handle* h, double shift, int32_t* color, int64_t* perm, int64_t* nnz_L,
+                           int32_t* ncolors);
+
+/* The factor L of the last ns_precond_build (or preconditioned ns_solve): CSR of the
+ * renumbered matrix, n + 1 rowptr, nnz_L colind (ascending in a row, the diagonal
+ * last) and vals, host arrays.  NS_ERR_STATE before a build. */
+ns_status ns_precond_factor(const ns_handle* h, int64_t* rowptr, int32_t* colind, double* vals);
+
+/* Y = B_R X = L^-1 A~ L^-T X + eps D X in the renumbered space (D indexed there as
+ * drawn), for an n x d row-major block, d in {1, 2, 4, 8}; host or device memory
+ * (on_device); precision NS_FP64 or NS_MIXED (FP32 values and arithmetic, Y
+ * widened).  The triangular solves take one launch per colour.  NS_ERR_STATE
+ * before ns_precond_build. */
+ns_status ns_apply_precond(ns_handle* h, int d, const double* X, double* Y, double eps, int precision,
+                           int on_device);
 
 /* ns_fma_peak -- measured FMA throughput of the current device, in TFLOP/s (two
  * flops per FMA), for precision NS_FP64 (the FP64 pipe) or NS_MIXED (the FP32
@@ -338,7 +379,7 @@ ns_status ns_trace_omega(ns_handle* h, int d, int restart_len, const ns_opts* op
 /* Eigen-decomposition of a symmetric k x k matrix (k <= 512) on the device with
  * the library's FP64 solver (Householder tridiagonalization in one CTA, Sturm
  * multisection and inverse iteration spread over the SMs),
- * the solver used for the projected matrix T of Alg. 2 line 13.
+ * the solver used for the projected matrix T of Alg. 2 (the projected matrix T).
  *   T     : k*k doubles, column-major, host memory (only the lower triangle is read)
  *   theta : k eigenvalues, ascending;  V : k*k column-major eigenvectors */
 ns_status ns_syev(int k, const double* T, double* theta, double* V);

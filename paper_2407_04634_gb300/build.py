@@ -17,7 +17,7 @@ import subprocess
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["k_sparse.cu", "k_dense.cu", "k_eig.cu", "k_batched.cu", "ns_api.cu", "ns_batch.cu", "ns_noalloc.cu", "k_peak.cu", "k_umma.cu", "k_dfproj.cu"]
+SOURCES = ["k_sparse.cu", "k_dense.cu", "k_eig.cu", "k_batched.cu", "ns_api.cu", "ns_batch.cu", "ns_noalloc.cu", "k_peak.cu", "k_umma.cu", "k_dfproj.cu", "k_precond.cu"]
 HEADERS = ["ns_common.cuh", "ns_kernels.cuh", "ns_batch.cuh", "ns_checkpoint.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",

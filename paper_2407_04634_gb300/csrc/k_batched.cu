@@ -275,7 +275,7 @@ __device__ int cta_jacobi_sweeps(F* A, F* V, int R, bool init_identity, double r
   return sweep;
 }
 
-// Projected eigenproblem of T (Alg. 2 line 13), FP64 result at a fraction of the
+// Projected eigenproblem of T (Alg. 2 (the projected matrix T)), FP64 result at a fraction of the
 // FP64 work of a cold FP64 Jacobi:
 //   1. Jacobi in FP32 on a rounded copy of T           -> V32 (orthogonal to ~1e-7)
 //   2. FP64: V = V32 (3I - V32^T V32)/2 (one Newton-Schulz step, orthonormal in FP64)
@@ -561,7 +561,7 @@ __device__ void solve_instance(const BatchArgs& a, int inst, float* ws32, double
   double theta_max = 0.0;
   while (true) {
     const int r0 = k0;
-    // ---- first step of the cycle (Alg. 2 lines 6-8) ----
+    // ---- first step of the cycle (Alg. 2 (the first step of a cycle)) ----
     {
       const float* q = Z + (int64_t)r0 * n;
       const double al = cta_sum(cta_apply<LANES>(rp, col, val, n, q, Dv, eps, nullptr, 0.f, qp), cr);
@@ -587,7 +587,7 @@ __device__ void solve_instance(const BatchArgs& a, int inst, float* ws32, double
       for (int k = tid; k < nlock; k += nt) S.wx[r0 % 3][k] = S.wx[(r0 + 1) % 3][k] = u_d;
       __syncthreads();
     }
-    // ---- inner steps (Alg. 2 lines 9-12) ----
+    // ---- inner steps (Alg. 2 (the block recurrence of a cycle)) ----
     for (int j = r0 + 1; j < R; ++j) {
       float* qj = Z + (int64_t)j * n;
       const float* qm = Z + (int64_t)(j - 1) * n;
@@ -672,7 +672,7 @@ __device__ void solve_instance(const BatchArgs& a, int inst, float* ws32, double
         PHASE(1);
       }
     }
-    // ---- restart (Alg. 2 lines 13-17) with locking ----
+    // ---- restart (Alg. 2 (the thick restart)) with locking ----
     PHASE(0);
     for (int t = tid; t < R * R; t += nt) {
       const int r = t / R, c = t % R;
@@ -745,11 +745,14 @@ __device__ void solve_instance(const BatchArgs& a, int inst, float* ws32, double
     }
     const int n_unl = S.nsmall - ncand;
     PHASE(3);
-    if (tid == 0) {  // retained set: capped at dimK/2, most converged small pairs first
+    if (tid == 0) {  // retained set (reading R7b), most converged small pairs first
       int nk = (n_unl + R) / 2;
       nk = max(nk, 1);
       nk = min(nk, R - 2);
-      nk = min(nk, R / 2);
+      {  // reading R7b: the unlocked small pairs when they fit in 3R/4, else R/2
+        const int cap = (n_unl > R / 2 && n_unl <= 3 * R / 4) ? n_unl : R / 2;
+        nk = min(nk, max(1, cap));
+      }
       int cnt = 0;
       // small, not candidates, by residual
       for (int pass = 0; pass < 2; ++pass) {
@@ -798,7 +801,7 @@ __device__ void solve_instance(const BatchArgs& a, int inst, float* ws32, double
       for (int c = 0; c < nk; ++c) Z[(int64_t)c * n + i] = Zt[(int64_t)c * n + i];
     }
     __syncthreads();
-    {  // Q_{l+1} against [X, Z_new] -> block nk (Alg. 2 line 16)
+    {  // Q_{l+1} against [X, Z_new] -> block nk (Alg. 2 (the re-orthogonalized next block))
       float* ql = Z + (int64_t)R * n;
       cta_cgs(ql, X, nlock, Z, nk, n, S.coef, cr);
       cta_cgs(ql, X, nlock, Z, nk, n, S.coef, cr);

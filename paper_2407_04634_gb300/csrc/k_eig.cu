@@ -1,4 +1,4 @@
-// Symmetric eigensolver for the projected matrix T of Alg. 2 line 13 (ascending
+// Symmetric eigensolver for the projected matrix T of Alg. 2 (the projected matrix T) (ascending
 // eigenvalues, orthonormal eigenvectors), FP64.
 //
 // FP64 runs at a small fraction of the FP32 rate on this GPU, so a serial

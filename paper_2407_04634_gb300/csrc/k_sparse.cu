@@ -1,5 +1,5 @@
 // Sparse kernels: CSR validation, transpose, norms and the SpMM products of the
-// operator B = A^T A + eps D (or A + eps D), Eq. (defB) and Alg. 1 line 1.
+// operator B = A^T A + eps D (or A + eps D), Eq. (defB) and Alg. 1 (its perturbed operator).
 #include <algorithm>
 
 #include "ns_common.cuh"
@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(kThreads) k_spmm_plain(Csr<T> M, const T* __re
   if (lane == 0 && row < M.nrows) store_row<T, D>(y + row * D, acc);
 }
 
-// Lanczos step product (Alg. 2 line 10):  Q' = M v + eps D x - Q_{j-1} Gamma_{j-1}^T
+// Lanczos step product (Alg. 2 (the block recurrence)):  Q' = M v + eps D x - Q_{j-1} Gamma_{j-1}^T
 // and Xi_j = sym(Q_j^T Q'); the block that finishes last reduces Xi_j.
 template <typename T, int D, int V>
 __global__ void __launch_bounds__(kThreads) k_spmm_lanczos(Csr<T> M, const T* __restrict__ v, StepOps<T> op,

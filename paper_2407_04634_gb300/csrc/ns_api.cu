@@ -127,6 +127,22 @@ struct ns_handle {
     float* sval32 = nullptr;
     int64_t entries = 0;
   } sell_A, sell_At;
+  // outer preconditioner P_R = Pi L of the SPD form (Sec. 4.4.2), built on first use
+  struct Pc {
+    bool built = false;
+    double alpha = -1.0;       // diagonal compensation the factor was computed with
+    int ncolors = 0;
+    std::vector<int64_t> cstart;  // first renumbered row of each colour (host), ncolors + 1
+    std::vector<int> color_h;     // colour of each original vertex (host)
+    std::vector<int64_t> perm_h;  // perm[new] = old (host)
+    std::vector<double> linit;    // L's initial values: tril(A~) with the uncompensated diagonal
+    int64_t nnzL = 0, nnzA = 0;
+    int64_t* perm = nullptr;
+    int64_t *arp = nullptr, *lrp = nullptr, *urp = nullptr, *umap = nullptr;
+    int *acol = nullptr, *lcol = nullptr, *ucol = nullptr;
+    double *aval = nullptr, *lval = nullptr, *uval = nullptr;
+    float *aval32 = nullptr, *lval32 = nullptr, *uval32 = nullptr;
+  } pc;
   // result
   bool solved = false;
   int64_t N = 0;
@@ -264,6 +280,183 @@ void build_sell(ns_handle* h, const int64_t* rowptr, const int* col, const doubl
   ck(cudaStreamSynchronize(h->stream), "sync");  // ptr (host) is read by the copy above
 }
 
+constexpr uint32_t kPriorityStream = 0x7FFFFFFFu;  // Philox stream of the colouring priorities
+
+// Outer preconditioner of the SPD form (Sec. 4.4.2, Eq. defichol): Jones-Plassmann
+// colouring of A's graph on the device (priorities: Philox stream kPriorityStream),
+// renumbering colour by colour, the patterns of A~ = Pi^T A Pi, L = tril(A~) and
+// L^T on the host, then IC(0) of A~ + alpha diag(A~) on the device, one launch
+// per colour.  The structure is built once per handle; a new alpha refactors.
+void build_precond(ns_handle* h, double alpha) {
+  auto& P = h->pc;
+  cudaStream_t s = h->stream;
+  const int64_t n = h->n, nnz = h->nnz;
+  if (!P.built) {
+    // ---- colouring ----
+    Buf prio(h, sizeof(double) * n), c0(h, sizeof(int) * n), c1(h, sizeof(int) * n), rem(h, 256);
+    rng_uniform<double>(h->seed, kPriorityStream, prio.as<double>(), n, s);
+    ck(cudaMemsetAsync(c0.p, 0xFF, sizeof(int) * n, s), "memset");
+    unsigned* rem_h = nullptr;
+    ck(cudaMallocHost(&rem_h, 64), "cudaMallocHost");
+    for (int64_t round = 0; round <= n; ++round) {  // every round colours the largest priority left
+      ck(cudaMemcpyAsync(c1.p, c0.p, sizeof(int) * n, cudaMemcpyDeviceToDevice, s), "copy");
+      ck(cudaMemsetAsync(rem.p, 0, sizeof(unsigned), s), "memset");
+      jp_round(h->rowptr, h->col, n, prio.as<double>(), c0.as<int>(), c1.as<int>(), rem.as<unsigned>(), s);
+      h->launches += 1;
+      ck(cudaMemcpyAsync(rem_h, rem.p, sizeof(unsigned), cudaMemcpyDeviceToHost, s), "d2h");
+      ck(cudaStreamSynchronize(s), "sync");
+      std::swap(c0, c1);
+      if (*rem_h == 0) break;
+    }
+    cudaFreeHost(rem_h);
+    ck_launch("colouring");
+    P.color_h.assign(n, 0);
+    ck(cudaMemcpyAsync(P.color_h.data(), c0.p, sizeof(int) * n, cudaMemcpyDeviceToHost, s), "d2h");
+    std::vector<int64_t> rp(n + 1);
+    std::vector<int> col(nnz);
+    std::vector<double> val(nnz);
+    ck(cudaMemcpyAsync(rp.data(), h->rowptr, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, s), "d2h");
+    if (nnz) {
+      ck(cudaMemcpyAsync(col.data(), h->col, sizeof(int) * nnz, cudaMemcpyDeviceToHost, s), "d2h");
+      ck(cudaMemcpyAsync(val.data(), h->val, sizeof(double) * nnz, cudaMemcpyDeviceToHost, s), "d2h");
+    }
+    ck(cudaStreamSynchronize(s), "sync");
+    // ---- renumbering: colour by colour, index order inside a colour ----
+    int nc = 0;
+    for (int64_t v = 0; v < n; ++v) {
+      if (P.color_h[v] < 0) throw Fail{NS_ERR_CUDA, "colouring left a vertex uncoloured"};
+      nc = std::max(nc, P.color_h[v] + 1);
+    }
+    P.ncolors = nc;
+    P.cstart.assign(nc + 1, 0);
+    for (int64_t v = 0; v < n; ++v) P.cstart[P.color_h[v] + 1] += 1;
+    for (int c = 0; c < nc; ++c) P.cstart[c + 1] += P.cstart[c];
+    P.perm_h.assign(n, 0);
+    std::vector<int64_t> iperm(n), fill(P.cstart.begin(), P.cstart.end() - 1);
+    for (int64_t v = 0; v < n; ++v) {
+      const int64_t i = fill[P.color_h[v]]++;
+      P.perm_h[i] = v;
+      iperm[v] = i;
+    }
+    // ---- A~ = Pi^T A Pi, L = tril(A~) (diagonal last), U = L^T (diagonal first) ----
+    std::vector<int64_t> arp(n + 1, 0), lrp(n + 1, 0), urp(n + 1, 0);
+    std::vector<int> acol;
+    std::vector<double> aval;
+    acol.reserve(nnz);
+    aval.reserve(nnz);
+    std::vector<std::pair<int, double>> row;
+    std::vector<int> lcol;
+    std::vector<double> lini;
+    std::vector<int64_t> diag_pos(n);
+    lcol.reserve(nnz / 2 + n);
+    lini.reserve(nnz / 2 + n);
+    acol.clear();
+    aval.clear();
+    for (int64_t i = 0; i < n; ++i) {
+      const int64_t v = P.perm_h[i];
+      row.clear();
+      for (int64_t e = rp[v]; e < rp[v + 1]; ++e) row.emplace_back((int)iperm[col[e]], val[e]);
+      std::sort(row.begin(), row.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
+      size_t k = 0;  // repeated columns are summed
+      for (size_t t = 0; t < row.size(); ++t) {
+        if (k && row[k - 1].first == row[t].first)
+          row[k - 1].second += row[t].second;
+        else
+          row[k++] = row[t];
+      }
+      row.resize(k);
+      double dg = 0.0;
+      for (const auto& pr : row) {
+        acol.push_back(pr.first);
+        aval.push_back(pr.second);
+        if (pr.first < i) {
+          lcol.push_back(pr.first);
+          lini.push_back(pr.second);
+        } else if (pr.first == i) {
+          dg += pr.second;
+        }
+      }
+      lcol.push_back((int)i);
+      lini.push_back(dg);
+      diag_pos[i] = (int64_t)lcol.size() - 1;
+      lrp[i + 1] = (int64_t)lcol.size();
+      arp[i + 1] = (int64_t)acol.size();
+    }
+    const int64_t nnzA = (int64_t)acol.size();
+    const int64_t nnzL = (int64_t)lcol.size();
+    // U rows: diagonal, then the L entries (j, i) with j > i in ascending j
+    std::vector<int64_t> ucount(n, 1);
+    for (int64_t j = 0; j < n; ++j)
+      for (int64_t p = lrp[j]; p < lrp[j + 1] - 1; ++p) ucount[lcol[p]] += 1;
+    for (int64_t i = 0; i < n; ++i) urp[i + 1] = urp[i] + ucount[i];
+    std::vector<int> ucol(nnzL);
+    std::vector<int64_t> umap(nnzL), ufill(urp.begin(), urp.end() - 1);
+    for (int64_t i = 0; i < n; ++i) {
+      ucol[ufill[i]] = (int)i;
+      umap[ufill[i]++] = diag_pos[i];
+    }
+    for (int64_t j = 0; j < n; ++j)
+      for (int64_t p = lrp[j]; p < lrp[j + 1] - 1; ++p) {
+        const int i = lcol[p];
+        ucol[ufill[i]] = (int)j;
+        umap[ufill[i]++] = p;
+      }
+    // ---- upload (col / val arrays padded for the TMA-staged SpMM) ----
+    auto up = [&](const void* src, size_t bytes, size_t alloc) {
+      void* d = dalloc_own(h, alloc);
+      ck(cudaMemsetAsync(d, 0, alloc, s), "memset");
+      if (bytes) ck(cudaMemcpyAsync(d, src, bytes, cudaMemcpyHostToDevice, s), "h2d");
+      return d;
+    };
+    P.nnzA = nnzA;
+    P.nnzL = nnzL;
+    P.perm = (int64_t*)up(P.perm_h.data(), sizeof(int64_t) * n, sizeof(int64_t) * n);
+    P.arp = (int64_t*)up(arp.data(), sizeof(int64_t) * (n + 1), sizeof(int64_t) * (n + 1));
+    P.acol = (int*)up(acol.data(), sizeof(int) * nnzA, sizeof(int) * csr_entries(nnzA));
+    P.aval = (double*)up(aval.data(), sizeof(double) * nnzA, sizeof(double) * csr_entries(nnzA));
+    P.lrp = (int64_t*)up(lrp.data(), sizeof(int64_t) * (n + 1), sizeof(int64_t) * (n + 1));
+    P.lcol = (int*)up(lcol.data(), sizeof(int) * nnzL, sizeof(int) * csr_entries(nnzL));
+    P.lval = (double*)up(nullptr, 0, sizeof(double) * csr_entries(nnzL));
+    P.urp = (int64_t*)up(urp.data(), sizeof(int64_t) * (n + 1), sizeof(int64_t) * (n + 1));
+    P.ucol = (int*)up(ucol.data(), sizeof(int) * nnzL, sizeof(int) * csr_entries(nnzL));
+    P.umap = (int64_t*)up(umap.data(), sizeof(int64_t) * nnzL, sizeof(int64_t) * std::max<int64_t>(nnzL, 1));
+    P.uval = (double*)up(nullptr, 0, sizeof(double) * csr_entries(nnzL));
+    ck(cudaStreamSynchronize(s), "sync");  // the host vectors above are read by the copies
+    P.linit = std::move(lini);
+    P.built = true;
+  }
+  if (P.alpha != alpha) {
+    // values: tril(A~) with the compensated diagonal, then IC(0) colour by colour
+    std::vector<double> v0 = P.linit;
+    std::vector<int64_t> lrp(n + 1);
+    ck(cudaMemcpyAsync(lrp.data(), P.lrp, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, s), "d2h");
+    ck(cudaStreamSynchronize(s), "sync");
+    for (int64_t i = 0; i < n; ++i) v0[lrp[i + 1] - 1] *= (1.0 + alpha);
+    Buf fail(h, 256);
+    ck(cudaMemsetAsync(fail.p, 0, 256, s), "memset");
+    ck(cudaMemcpyAsync(P.lval, v0.data(), sizeof(double) * P.nnzL, cudaMemcpyHostToDevice, s), "h2d");
+    for (int c = 0; c < P.ncolors; ++c) {
+      ic0_rows(P.lrp, P.lcol, P.lval, P.cstart[c], P.cstart[c + 1], fail.as<unsigned>(), s);
+      h->launches += 1;
+    }
+    gather_vals(P.lval, P.umap, P.uval, P.nnzL, s);
+    h->launches += 1;
+    unsigned f = 0;
+    ck(cudaMemcpyAsync(&f, fail.p, sizeof(unsigned), cudaMemcpyDeviceToHost, s), "d2h");
+    ck(cudaStreamSynchronize(s), "sync");
+    ck_launch("ic0");
+    P.alpha = alpha;
+    if (P.aval32) {  // FP32 copies follow the new factor
+      convert_d2f(P.lval, P.lval32, P.nnzL, s);
+      convert_d2f(P.uval, P.uval32, P.nnzL, s);
+    }
+    if (f) {
+      P.alpha = -1.0;
+      throw Fail{NS_ERR_NUMERICAL, "IC(0) met a non-positive pivot: raise precond_shift"};
+    }
+  }
+}
+
 void ensure_fp32(ns_handle* h) {
   // FP32 copies of A's values (already present when A came in as FP32), A^T's values and D
   if (!h->val32) {
@@ -277,6 +470,15 @@ void ensure_fp32(ns_handle* h) {
   if (!h->D32) {
     h->D32 = (float*)dalloc_own(h, sizeof(float) * (size_t)h->n);
     convert_d2f(h->D64, h->D32, h->n, h->stream);
+  }
+  auto& P = h->pc;
+  if (P.built && !P.aval32) {
+    P.aval32 = (float*)dalloc_own(h, sizeof(float) * csr_entries(P.nnzA));
+    P.lval32 = (float*)dalloc_own(h, sizeof(float) * csr_entries(P.nnzL));
+    P.uval32 = (float*)dalloc_own(h, sizeof(float) * csr_entries(P.nnzL));
+    convert_d2f(P.aval, P.aval32, P.nnzA, h->stream);
+    convert_d2f(P.lval, P.lval32, P.nnzL, h->stream);
+    convert_d2f(P.uval, P.uval32, P.nnzL, h->stream);
   }
   for (ns_handle::Sell* sl : {&h->sell_A, &h->sell_At})
     if (sl->sval && !sl->sval32) {
@@ -319,6 +521,17 @@ Csr<T> csr_At(ns_handle* h) {
   return c;
 }
 
+template <typename T>
+const T* pc_vals(const double* v64, const float* v32);
+template <>
+const double* pc_vals<double>(const double* v64, const float*) {
+  return v64;
+}
+template <>
+const float* pc_vals<float>(const double*, const float* v32) {
+  return v32;
+}
+
 // ---------------------------------------------------------------------------
 // the solver
 // ---------------------------------------------------------------------------
@@ -331,8 +544,10 @@ struct Solver {
   double eps, tol_eff, normB, u, u_d, u_ro, bd_tol;
   double ud_per_normB = 0.0;  // u_d = ud_per_normB * ||B|| (Eq. defmprd with readings M1, M4)
   ns_opts o;
-  Csr<T> A, At;
+  Csr<T> A, At;  // with the outer preconditioner, A is A~ = Pi^T A Pi
   const T* Dv;
+  const ns_handle::Pc* pc = nullptr;  // outer preconditioner (Sec. 4.4.2) or null
+  Buf tbuf;                           // L^-T x of the preconditioned product
   // buffers
   Buf zb[2], qp, ybuf, xbuf, lnew, cbuf, dpart, redpart, small, pin, umma_img;
   unsigned* umma_err = nullptr;  // set by the tensor-core restart product when a bounded wait gave up
@@ -380,6 +595,16 @@ struct Solver {
     bd_tol = 100.0 * u_d;
     A = csr_A<T>(h);
     if (h->mode == NS_MODE_NORMAL) At = csr_At<T>(h);
+    if (o.precond) {
+      pc = &h->pc;
+      A = Csr<T>{};
+      A.rowptr = pc->arp;
+      A.col = pc->acol;
+      A.val = pc_vals<T>(pc->aval, pc->aval32);
+      A.nrows = A.ncols = n;
+      A.nnz = pc->nnzA;
+      A.V = choose_lanes(n, pc->nnzA);
+    }
     Dv = Prec<T>::D(h);
     const size_t zbytes = sizeof(T) * (size_t)n * (R + D);
     zb[0] = Buf(h, zbytes);
@@ -387,7 +612,8 @@ struct Solver {
     Z[0] = zb[0].as<T>();
     Z[1] = zb[1].as<T>();
     qp = Buf(h, sizeof(T) * (size_t)n * D);
-    if (h->mode == NS_MODE_NORMAL) ybuf = Buf(h, sizeof(T) * (size_t)m * D);
+    if (h->mode == NS_MODE_NORMAL || pc) ybuf = Buf(h, sizeof(T) * (size_t)m * D);
+    if (pc) tbuf = Buf(h, sizeof(T) * (size_t)n * D);
     lnew = Buf(h, sizeof(T) * (size_t)n * R);
     cap = (int)std::min<int64_t>(n, std::max(64, R));
     xbuf = Buf(h, sizeof(T) * (size_t)n * cap);
@@ -442,7 +668,7 @@ struct Solver {
     ck(cudaMallocHost(&pin_d, sizeof(double) * (2 * (size_t)R + 64)), "cudaMallocHost");
     flags_h = reinterpret_cast<unsigned*>(pin_d + 2 * R + 32);
     if (from) {  // the schedules the checkpointed iteration ran with
-      A.V = checked_schedule(A, from->spmm_A, h->mode == NS_MODE_NORMAL);
+      A.V = checked_schedule(A, from->spmm_A, h->mode == NS_MODE_NORMAL || pc);
       if (h->mode == NS_MODE_NORMAL) At.V = checked_schedule(At, from->spmm_At, false);
     } else if (o.spmm_schedule > 0) {
       A.V = fixed_schedule(A, o.spmm_schedule);
@@ -450,7 +676,9 @@ struct Solver {
     } else {
       // SpMM schedule: lanes per row tuned on this matrix (operands: the basis buffers)
       ck(cudaMemsetAsync(Z[1], 0, zbytes, s), "memset");
-      if (h->mode == NS_MODE_SPD) {
+      if (pc) {  // A~ is applied by the plain SpMM between the two triangular solves
+        A.V = tune_lanes<T, D>(A, Z[1], ybuf.as<T>(), s);
+      } else if (h->mode == NS_MODE_SPD) {
         A.V = tune_lanczos(A, Z[1]);
       } else {
         A.V = tune_lanes<T, D>(A, Z[1], ybuf.as<T>(), s);
@@ -618,8 +846,21 @@ struct Solver {
       by += (double)h->nnz * (4 + sv) + (m + 1) * 8.0 + 2.0 * m * D * sv;
       fl += 2.0 * h->nnz * D;
     }
+    if (pc) {  // two triangular solves of L, nnz(L) entries and n rows each
+      by += 2.0 * pc->nnzL * (4 + sv) + 2.0 * (n + 1) * 8.0 + 4.0 * n * D * sv;
+      fl += 4.0 * pc->nnzL * D;
+    }
     PScope ps(&h->prof, P_APPLY, by, fl);
-    if (h->mode == NS_MODE_SPD) {
+    if (pc) {  // B_R x = L^-1 A~ L^-T x + eps D x (Sec. 4.4.2)
+      T* t = tbuf.as<T>();
+      T* u = ybuf.as<T>();
+      const int nc = pc->ncolors;
+      trsv_colors<T, D>(pc->urp, pc->ucol, pc_vals<T>(pc->uval, pc->uval32), pc->cstart.data(), nc, false, x, t, s);
+      spmm_plain<T, D>(A, t, u, s);
+      trsv_colors<T, D>(pc->lrp, pc->lcol, pc_vals<T>(pc->lval, pc->lval32), pc->cstart.data(), nc, true, u, u, s);
+      lanczos_epilogue<T, D>(u, n, op, red, s);
+      launches += 2 * nc + 2;
+    } else if (h->mode == NS_MODE_SPD) {
       spmm_lanczos<T, D>(A, x, op, red, s);
       launches += 1;
     } else {
@@ -721,18 +962,18 @@ struct Solver {
 
   void orthonormal_start() {
     T* q0 = blk(cur, 0);
-    rng_gauss<T>(h->seed, 1u, q0, n * D, s);  // Alg. 2 line 2
+    rng_gauss<T>(h->seed, 1u, q0, n * D, s);  // Alg. 2 (its Gaussian start block)
     launches += 1;
     gram_chol<T, D>(q0, D, D, n, R1, nullptr, flags, red, s);
     launches += 1;
-    cholqr_finish<D>(q0, D, R1, R2);  // Alg. 2 line 4
+    cholqr_finish<D>(q0, D, R1, R2);  // Alg. 2 (its orthonormalized start block)
     if (read_flags() & 1u) {
       clear_flags();
       replace_block(cur, 0);
     }
   }
 
-  // Alg. 2 lines 6-8: first step of a cycle
+  // Alg. 2: the first step of a cycle
   void first_step(int r0) {
     T* q = blk(cur, r0);
     apply_step(q, nullptr, nullptr, Xi + (size_t)r0 * D * D, nXi + r0);
@@ -766,7 +1007,7 @@ struct Solver {
     ck(cudaMemsetAsync(sminGam + j, 0, sizeof(double), s), "memset");
   }
 
-  // Alg. 2 lines 10-12 for block j (r0 < j < nb)
+  // Alg. 2 (the block recurrence of a cycle) for block j (r0 < j < nb)
   void inner_step(int j, int r0) {
     T* q = blk(cur, j);
     T* qn = blk(cur, j + 1);
@@ -893,7 +1134,7 @@ struct Solver {
   bool debug = getenv("NS_DEBUG") != nullptr;
   std::chrono::steady_clock::time_point t_start = std::chrono::steady_clock::now();
 
-  // ---- Alg. 2 lines 13-17 + locking + stopping rule; returns true to stop ----
+  // ---- Alg. 2 (the thick restart) + locking + stopping rule; returns true to stop ----
   bool restart(int& k0) {
     const int r0 = k0 / D;
     {
@@ -957,10 +1198,16 @@ struct Solver {
     nk = std::max(nk, D);
     nk = std::min(nk, R - 2 * D);
     nk = std::min(nk, D * ((int)avail.size() / D));
-    // at most dimK/2 retained pairs, so every cycle adds >= dimK/2 new vectors; the
-    // most converged small pairs are kept first (any subset of Ritz pairs keeps the
-    // Krylov-Schur decomposition exact)
-    nk = std::min(nk, std::max(D, D * (R / (2 * D))));
+    // reading R7b: the retained set is capped at the unlocked small pairs (whole
+    // blocks) when they fit in 3 dimK/4, else at dimK/2, so every cycle adds new
+    // vectors; the most converged small pairs are kept first (any subset of Ritz
+    // pairs keeps the Krylov-Schur decomposition exact)
+    {
+      const int half = std::max(D, D * (R / (2 * D)));
+      const int want = D * ((n_unl + D - 1) / D);
+      const int cap = (want > half && want <= D * ((3 * R / 4) / D)) ? want : half;
+      nk = std::min(nk, std::max(D, cap));
+    }
     {
       std::vector<int> sm, rest;
       for (int i : avail) (pin_theta[i] < 3.0 * eps ? sm : rest).push_back(i);
@@ -974,7 +1221,7 @@ struct Solver {
       PScope ps(&h->prof, P_GEMM, (double)n * (R + nk) * sizeof(T), 2.0 * n * R * nk);
       restart_product(nk, 0, nullptr, Z[other]);
     }
-    // Alg. 2 line 16: Q_{l+1} against [X, Z_new], moved to block nk/D of the new buffer
+    // Alg. 2 (the re-orthogonalized next block): Q_{l+1} against [X, Z_new], moved to block nk/D of the new buffer
     T* qlast = blk(cur, nb);
     clear_flags();
     project<D>(qlast, D, nlock, other, nk / D, true, R1, nullptr);
@@ -1052,6 +1299,7 @@ struct Solver {
     c.restarts = restarts;
     c.nullity = nlock;
     c.k0 = k0;
+    c.precond = pc ? pc->alpha : 0.0;
     return c;
   }
   // host scalars of the iteration, in file order
@@ -1191,6 +1439,23 @@ RefineOut refine(ns_handle* h, double* X, int64_t N, double normA, const ns_opts
   Csr<double> A64 = csr_A<double>(h);
   Csr<float> A32 = csr_A<float>(h), At32;
   if (normal) At32 = csr_At<float>(h);
+  if (o.precond) {  // the basis is in the renumbered space: refine against A~
+    const auto& P = h->pc;
+    A64 = Csr<double>{};
+    A64.rowptr = P.arp;
+    A64.col = P.acol;
+    A64.val = P.aval;
+    A64.nrows = A64.ncols = n;
+    A64.nnz = P.nnzA;
+    A64.V = choose_lanes(n, P.nnzA);
+    A32 = Csr<float>{};
+    A32.rowptr = P.arp;
+    A32.col = P.acol;
+    A32.val = P.aval32;
+    A32.nrows = A32.ncols = n;
+    A32.nnz = P.nnzA;
+    A32.V = A64.V;
+  }
   Buf bx(h, sizeof(double) * n * W), br64(h, sizeof(double) * nr * W), bd(h, sizeof(float) * n * W),
       bp(h, sizeof(float) * n * W), bq(h, sizeof(float) * nr * W), br(h, sizeof(float) * nr * W),
       bs(h, sizeof(float) * n * W), bred(h, sizeof(double) * (size_t)kMaxBlocks * 64 + 256), bsm(h, 8192);
@@ -1321,6 +1586,79 @@ RefineOut refine(ns_handle* h, double* X, int64_t N, double normA, const ns_opts
   return out;
 }
 
+// Sec. 4.4.2 post-processing: the locked vectors X approximate L^T null(A~), so
+// L^-T X spans null(A~).  Panel by panel (W columns): L^-T by colours, CGS2 against
+// the columns already done (compensated FP32-pair products), CholQR2; FP64, in the
+// renumbered space.  Rank loss is a numerical failure.
+template <int W>
+void pc_panel(ns_handle* h, const double* Xin, double* Xout, int c0, double* P, double* Q, double* cbuf,
+              double* dpart, double* sm, const Red& red, unsigned* flags_h) {
+  const auto& pc = h->pc;
+  const int64_t n = h->n;
+  cudaStream_t s = h->stream;
+  double *R1 = sm, *R2 = sm + 64;
+  unsigned* flags = reinterpret_cast<unsigned*>(sm + 128);
+  if ((size_t)c0 * W * sizeof(double) > 190 * 1024)
+    throw Fail{NS_ERR_INVALID_ARG, "too many null vectors for the preconditioned post-processing"};
+  cols_to_panel_t<double>(Xin, c0, W, n, Q, s);
+  trsv_colors<double, W>(pc.urp, pc.ucol, pc.uval, pc.cstart.data(), pc.ncolors, false, Q, P, s);
+  h->launches += 1 + pc.ncolors;
+  if (c0 == 0) {
+    gram_chol<double, W>(P, W, W, n, R1, nullptr, flags, red, s);
+    h->launches += 1;
+  } else {
+    VParts<double> V;
+    V.X = Xout;
+    V.kx = c0;
+    V.df = 1;
+    for (int pass = 0; pass < 2; ++pass) {
+      proj_dots<double, W>(V, P, nullptr, W, n, cbuf, dpart, s, kDotsAutoChunks);
+      ck((proj_update<double, W>(V, cbuf, P, nullptr, W, n, pass == 1 ? 1 : 0, R1, nullptr, flags, red, s)),
+         "proj_update shared-memory limit");
+      h->launches += 3;
+    }
+  }
+  scale_gram<double, W>(P, W, P, W, R1, n, R2, flags, red, s, W);
+  scale_gram<double, W>(P, W, P, W, R2, n, nullptr, flags, red, s, W);
+  panel_to_cols<double>(P, W, W, n, Xout, c0, s);
+  h->launches += 3;
+  ck(cudaMemcpyAsync(flags_h, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s), "d2h");
+  ck(cudaStreamSynchronize(s), "sync");
+  if (*flags_h & 1u) throw Fail{NS_ERR_NUMERICAL, "L^-T X lost rank (preconditioned post-processing)"};
+}
+
+void pc_postprocess(ns_handle* h, double* X, int64_t N, double* Xout) {
+  const int64_t n = h->n;
+  Buf P(h, sizeof(double) * n * 8), Q(h, sizeof(double) * n * 8), cbuf(h, sizeof(double) * (size_t)N * 16),
+      dpart(h, sizeof(double) * (size_t)ceil_div(std::max<int64_t>(n, 1), kDotsMinChunk) * N * 16),
+      red_part(h, sizeof(double) * (size_t)kMaxBlocks * 64 + 256), sm(h, 4096);
+  ck(cudaMemsetAsync(sm.p, 0, 4096, h->stream), "memset");
+  Red red;
+  red.part = red_part.as<double>();
+  red.ticket = reinterpret_cast<unsigned*>(sm.as<double>() + 256);
+  unsigned* flags_h = nullptr;
+  ck(cudaMallocHost(&flags_h, 64), "cudaMallocHost");
+  try {
+    for (int64_t c0 = 0; c0 < N;) {
+      const int64_t left = N - c0;
+      const int w = left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
+      double* a[4] = {P.as<double>(), Q.as<double>(), cbuf.as<double>(), dpart.as<double>()};
+      switch (w) {
+        case 8: pc_panel<8>(h, X, Xout, (int)c0, a[0], a[1], a[2], a[3], sm.as<double>(), red, flags_h); break;
+        case 4: pc_panel<4>(h, X, Xout, (int)c0, a[0], a[1], a[2], a[3], sm.as<double>(), red, flags_h); break;
+        case 2: pc_panel<2>(h, X, Xout, (int)c0, a[0], a[1], a[2], a[3], sm.as<double>(), red, flags_h); break;
+        default: pc_panel<1>(h, X, Xout, (int)c0, a[0], a[1], a[2], a[3], sm.as<double>(), red, flags_h); break;
+      }
+      c0 += w;
+    }
+  } catch (...) {
+    cudaFreeHost(flags_h);
+    throw;
+  }
+  cudaFreeHost(flags_h);
+  ck_launch("preconditioned post-processing");
+}
+
 }  // namespace
 
 // typed bodies of the C entry points
@@ -1344,7 +1682,8 @@ static ns_status solve_typed(ns_handle* h, int R, double tol, const ns_opts& o) 
       throw Fail{NS_ERR_INVALID_ARG, "checkpoint of another matrix or seed"};
     if (rec.precision != (std::is_same<T, float>::value ? NS_MIXED : NS_FP64) || rec.d != D ||
         rec.restart_len != R || rec.reorth != o.reorth || rec.gemm != o.gemm ||
-        rec.fp64_products != o.fp64_products || rec.eps != o.eps)
+        rec.fp64_products != o.fp64_products || rec.eps != o.eps ||
+        rec.precond != (o.precond ? o.precond_shift : 0.0))
       throw Fail{NS_ERR_INVALID_ARG, "checkpoint of a solve with other d, restart_len or opts"};
   }
   Solver<T, D> S(h, R, tol, o, o.resume ? &rec : nullptr);
@@ -1364,6 +1703,21 @@ static ns_status solve_typed(ns_handle* h, int R, double tol, const ns_opts& o) 
       convert_f2d(reinterpret_cast<const float*>(S.X()), h->basis, (int64_t)N * h->n, s);
   }
   double normA = (h->mode == NS_MODE_NORMAL) ? std::sqrt(std::max(S.theta_max, 0.0)) : S.theta_max;
+  if (o.precond) {
+    // the Ritz values are those of B_R: ||A||_2 is bounded by ||A||_inf instead
+    normA = h->normAinf;
+    if (N) {
+      double* Y = (double*)dalloc(h, h->basis_bytes);
+      try {
+        pc_postprocess(h, h->basis, N, Y);
+      } catch (...) {
+        dfree(h, Y, h->basis_bytes);
+        throw;
+      }
+      dfree(h, h->basis, h->basis_bytes);
+      h->basis = Y;
+    }
+  }
   RefineOut ro;
   if (o.refine && N) {
     {
@@ -1406,6 +1760,11 @@ static ns_status solve_typed(ns_handle* h, int R, double tol, const ns_opts& o) 
       std::swap(h->basis, X2);
       orth1 = 0.375 * (*mx_h) * (*mx_h) * N;  // predicted second-order remainder
       if (*mx_h <= 1e-6) break;
+    }
+    if (o.precond) {  // rows back to the original numbering
+      unpermute_cols(h->basis, h->pc.perm, h->n, (int)N, X2, s);
+      h->launches += 1;
+      std::swap(h->basis, X2);
     }
     ck(cudaStreamSynchronize(s), "sync");
     ck_launch("reorthonormalize");
@@ -1467,7 +1826,7 @@ static void trace_omega_typed(ns_handle* h, int R, const ns_opts& o, double* W) 
 }
 
 template <typename T, int D>
-static void apply_B_typed(ns_handle* h, const T* x, T* y, double eps, Red red, int schedule) {
+static void apply_B_typed(ns_handle* h, const T* x, T* y, double eps, Red red, int schedule, bool pre = false) {
   StepOps<T> op;
   op.x = x;
   op.Dv = Prec<T>::D(h);
@@ -1479,7 +1838,24 @@ static void apply_B_typed(ns_handle* h, const T* x, T* y, double eps, Red red, i
   Csr<T> A = csr_A<T>(h);
   Csr<T> At = h->mode == NS_MODE_SPD ? A : csr_At<T>(h);
   if (schedule >= 0) A.V = At.V = schedule;
-  if (h->mode == NS_MODE_SPD) {
+  if (pre) {  // B_R x = L^-1 A~ L^-T x + eps D x, renumbered space
+    const auto& P = h->pc;
+    Csr<T> Ap;
+    Ap.rowptr = P.arp;
+    Ap.col = P.acol;
+    Ap.val = pc_vals<T>(P.aval, P.aval32);
+    Ap.nrows = Ap.ncols = h->n;
+    Ap.nnz = P.nnzA;
+    Ap.V = choose_lanes(h->n, P.nnzA);
+    Buf t(h, sizeof(T) * h->n * D), u(h, sizeof(T) * h->n * D);
+    trsv_colors<T, D>(P.urp, P.ucol, pc_vals<T>(P.uval, P.uval32), P.cstart.data(), P.ncolors, false, x, t.as<T>(),
+                      h->stream);
+    spmm_plain<T, D>(Ap, t.as<T>(), u.as<T>(), h->stream);
+    trsv_colors<T, D>(P.lrp, P.lcol, pc_vals<T>(P.lval, P.lval32), P.cstart.data(), P.ncolors, true, u.as<T>(),
+                      u.as<T>(), h->stream);
+    lanczos_epilogue<T, D>(u.as<T>(), h->n, op, red, h->stream);
+    ck(cudaStreamSynchronize(h->stream), "sync");
+  } else if (h->mode == NS_MODE_SPD) {
     spmm_lanczos<T, D>(A, x, op, red, h->stream);
   } else {
     Buf yb(h, sizeof(T) * h->m * D);
@@ -1625,6 +2001,8 @@ void ns_default_opts(ns_opts* o) {
   o->checkpoint_every = 0;
   o->resume = 0;
   o->checkpoint_path = nullptr;
+  o->precond = 0;
+  o->precond_shift = 0.1;
 }
 
 static ns_status set_err(ns_handle* h, ns_status st, const std::string& msg) {
@@ -1752,7 +2130,7 @@ ns_status ns_create(ns_handle** out, int64_t m, int64_t n, const int64_t* rowptr
       for (int64_t r = 0; r < n; ++r) h->maxrow_At = std::max(h->maxrow_At, rpt[r + 1] - rpt[r]);
     }
     h->D64 = (double*)dalloc_own(h, sizeof(double) * n);
-    rng_uniform<double>(seed, 0u, h->D64, n, s);  // Alg. 2 line 1: D ~ U[0,1]
+    rng_uniform<double>(seed, 0u, h->D64, n, s);  // Alg. 2 (its perturbed operator): D ~ U[0,1]
     double nr[2] = {0.0, 0.0};
     ck(cudaMemcpyAsync(nr, norms, sizeof(double) * 2, cudaMemcpyDeviceToHost, s), "d2h");
     ck(cudaStreamSynchronize(s), "sync");
@@ -1802,12 +2180,16 @@ ns_status ns_solve(ns_handle* h, int d, int restart_len, double tol, const ns_op
     if (o.checkpoint_every < 0 || !(o.resume == 0 || o.resume == 1) ||
         ((o.checkpoint_every > 0 || o.resume) && (!o.checkpoint_path || !*o.checkpoint_path)))
       return set_err(h, NS_ERR_INVALID_ARG, "checkpoint_every >= 0, resume 0 or 1, both need checkpoint_path");
+    if (!(o.precond == 0 || o.precond == 1) || (o.precond && h->mode != NS_MODE_SPD) ||
+        (o.precond && !(o.precond_shift >= 0.0 && std::isfinite(o.precond_shift))))
+      return set_err(h, NS_ERR_INVALID_ARG, "precond: 0 or 1, NS_MODE_SPD only, precond_shift >= 0");
   }
   h->err.clear();
   h->solved = false;
   h->launches = 0;
   try {
     ns_status st;
+    if (o.precond) build_precond(h, o.precond_shift);
     if (o.precision == NS_MIXED) {
       ensure_fp32(h);
       switch (d) {
@@ -1997,6 +2379,86 @@ ns_status ns_apply_B(ns_handle* h, int d, const double* X, double* Y, double eps
     ck(cudaStreamSynchronize(h->stream), "sync");
     if (spmm_wait_timeouts(true)) throw Fail{NS_ERR_TIMEOUT, "a bounded device wait of the SpMM expired"};
   } catch (const Fail& f) {
+    return set_err(h, f.st, f.msg);
+  }
+  return NS_OK;
+}
+
+ns_status ns_precond_build(ns_handle* h, double shift, int32_t* color, int64_t* perm, int64_t* nnz_L,
+                           int32_t* ncolors) {
+  if (!h) return NS_ERR_INVALID_ARG;
+  if (h->mode != NS_MODE_SPD) return set_err(h, NS_ERR_STATE, "outer preconditioning needs NS_MODE_SPD");
+  if (!(shift >= 0.0 && std::isfinite(shift))) return set_err(h, NS_ERR_INVALID_ARG, "shift must be >= 0");
+  try {
+    build_precond(h, shift);
+    const auto& P = h->pc;
+    if (color) std::copy(P.color_h.begin(), P.color_h.end(), color);
+    if (perm) std::copy(P.perm_h.begin(), P.perm_h.end(), perm);
+    if (nnz_L) *nnz_L = P.nnzL;
+    if (ncolors) *ncolors = P.ncolors;
+  } catch (const Fail& f) {
+    cudaGetLastError();
+    return set_err(h, f.st, f.msg);
+  }
+  return NS_OK;
+}
+
+ns_status ns_precond_factor(const ns_handle* h, int64_t* rowptr, int32_t* colind, double* vals) {
+  if (!h || !rowptr) return NS_ERR_INVALID_ARG;
+  const auto& P = h->pc;
+  if (!P.built || P.alpha < 0.0) return NS_ERR_STATE;
+  cudaStream_t s = h->stream;
+  if (cudaMemcpyAsync(rowptr, P.lrp, sizeof(int64_t) * (h->n + 1), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return NS_ERR_CUDA;
+  if (P.nnzL) {
+    if (!colind || !vals) return NS_ERR_INVALID_ARG;
+    cudaMemcpyAsync(colind, P.lcol, sizeof(int) * P.nnzL, cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(vals, P.lval, sizeof(double) * P.nnzL, cudaMemcpyDeviceToHost, s);
+  }
+  return cudaStreamSynchronize(s) == cudaSuccess ? NS_OK : NS_ERR_CUDA;
+}
+
+ns_status ns_apply_precond(ns_handle* h, int d, const double* X, double* Y, double eps, int precision,
+                           int on_device) {
+  if (!h || !X || !Y || !(d == 1 || d == 2 || d == 4 || d == 8)) return NS_ERR_INVALID_ARG;
+  if (!(precision == NS_FP64 || precision == NS_MIXED)) return set_err(h, NS_ERR_INVALID_ARG, "precision");
+  if (!h->pc.built || h->pc.alpha < 0.0) return set_err(h, NS_ERR_STATE, "no preconditioner: ns_precond_build first");
+  try {
+    const size_t cnt = (size_t)h->n * d;
+    Buf xb(h, sizeof(double) * cnt), yb(h, sizeof(double) * cnt), rp(h, sizeof(double) * kMaxBlocks * 64 + 256),
+        tk(h, 256);
+    ck(cudaMemsetAsync(tk.p, 0, 256, h->stream), "memset");
+    Red red;
+    red.part = rp.as<double>();
+    red.ticket = tk.as<unsigned>();
+    ck(cudaMemcpyAsync(xb.p, X, sizeof(double) * cnt, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                       h->stream),
+       "copy X");
+    if (precision == NS_MIXED) {
+      ensure_fp32(h);
+      Buf xf(h, sizeof(float) * cnt), yf(h, sizeof(float) * cnt);
+      convert_d2f(xb.as<double>(), xf.as<float>(), (int64_t)cnt, h->stream);
+      switch (d) {
+        case 1: apply_B_typed<float, 1>(h, xf.as<float>(), yf.as<float>(), eps, red, -1, true); break;
+        case 2: apply_B_typed<float, 2>(h, xf.as<float>(), yf.as<float>(), eps, red, -1, true); break;
+        case 4: apply_B_typed<float, 4>(h, xf.as<float>(), yf.as<float>(), eps, red, -1, true); break;
+        default: apply_B_typed<float, 8>(h, xf.as<float>(), yf.as<float>(), eps, red, -1, true); break;
+      }
+      convert_f2d(yf.as<float>(), yb.as<double>(), (int64_t)cnt, h->stream);
+    } else {
+      switch (d) {
+        case 1: apply_B_typed<double, 1>(h, xb.as<double>(), yb.as<double>(), eps, red, -1, true); break;
+        case 2: apply_B_typed<double, 2>(h, xb.as<double>(), yb.as<double>(), eps, red, -1, true); break;
+        case 4: apply_B_typed<double, 4>(h, xb.as<double>(), yb.as<double>(), eps, red, -1, true); break;
+        default: apply_B_typed<double, 8>(h, xb.as<double>(), yb.as<double>(), eps, red, -1, true); break;
+      }
+    }
+    ck(cudaMemcpyAsync(Y, yb.p, sizeof(double) * cnt, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                       h->stream),
+       "copy Y");
+    ck(cudaStreamSynchronize(h->stream), "sync");
+  } catch (const Fail& f) {
+    cudaGetLastError();
     return set_err(h, f.st, f.msg);
   }
   return NS_OK;

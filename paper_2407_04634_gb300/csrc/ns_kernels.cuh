@@ -257,4 +257,26 @@ void gram64(const double* X, int64_t n, int N, double* G, double* part, cudaStre
 void lowdin_update(const double* X, int64_t n, int N, const double* G, double* Xout, cudaStream_t s);
 // *out = max |G - I|
 void max_offdiag(const double* G, int N, double* out, cudaStream_t s);
+// ---- outer preconditioning (k_precond.cu) ----
+// one Jones-Plassmann colouring round (colours from cin, new ones written to cout,
+// which starts as a copy of cin); *remaining counts vertices left uncoloured
+void jp_round(const int64_t* rowptr, const int* col, int64_t n, const double* prio, const int* cin, int* cout,
+              unsigned* remaining, cudaStream_t s);
+// IC(0) of rows r0..r1 (one colour) of L (CSR, diagonal last, values initialised from
+// tril(A~) with the compensated diagonal); *fail |= 1 on a non-positive pivot
+void ic0_rows(const int64_t* rp, const int* col, double* val, int64_t r0, int64_t r1, unsigned* fail,
+              cudaStream_t s);
+void gather_vals(const double* src, const int64_t* map, double* dst, int64_t count, cudaStream_t s);
+// x = L^-1 b (lower: diagonal last, colours ascending) or U^-1 b (upper: diagonal first,
+// colours descending) on n x D row-major blocks; cstart: host array of ncolors + 1
+template <typename T, int D>
+void trsv_colors(const int64_t* rp, const int* col, const T* val, const int64_t* cstart, int ncolors, bool lower,
+                 const T* b, T* x, cudaStream_t s);
+// out = w + eps D x - qprev gprev^T, Xi = sym(x^T out) for a product w formed elsewhere
+template <typename T, int D>
+void lanczos_epilogue(const T* w, int64_t n, const StepOps<T>& op, const Red& red, cudaStream_t s);
+void unpermute_cols(const double* in, const int64_t* perm, int64_t n, int ncols, double* out, cudaStream_t s);
+template <typename T>
+void cols_to_panel_t(const T* X, int c0, int w, int64_t n, T* P, cudaStream_t s);
+
 }  // namespace ns

@@ -39,7 +39,8 @@ class NsOpts(C.Structure):
                 ("refine_tol", C.c_double), ("refine_maxit", C.c_int), ("refine_chunk", C.c_int),
                 ("use_graphs", C.c_int), ("profile", C.c_int), ("batch_block", C.c_int), ("gemm", C.c_int),
                 ("fp64_products", C.c_int), ("spmm_schedule", C.c_int), ("checkpoint_every", C.c_int),
-                ("resume", C.c_int), ("checkpoint_path", C.c_char_p)]
+                ("resume", C.c_int), ("checkpoint_path", C.c_char_p), ("precond", C.c_int),
+                ("precond_shift", C.c_double)]
 
 
 class NsStats(C.Structure):
@@ -58,7 +59,7 @@ class NsCheckpointInfo(C.Structure):
     _fields_ = [(f, C.c_int64) for f in ("version", "m", "n", "nnz", "mode", "precision", "d", "restart_len",
                                          "reorth", "gemm", "fp64_products", "spmm_A", "spmm_At")] + \
                [("seed", C.c_uint64)] + [(f, C.c_double) for f in ("eps", "tol_eff", "normA1", "normAinf")] + \
-               [(f, C.c_int64) for f in ("matvecs", "restarts", "nullity", "k0")]
+               [(f, C.c_int64) for f in ("matvecs", "restarts", "nullity", "k0")] + [("precond", C.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -102,6 +103,9 @@ SIGNATURES = {
     "ns_trace_omega": (C.c_int, [_P, C.c_int, C.c_int, C.POINTER(NsOpts), _P]),
     "ns_syev": (C.c_int, [C.c_int, _P, _P, _P]),
     "ns_fma_peak": (C.c_int, [C.c_int, C.POINTER(C.c_double)]),
+    "ns_precond_build": (C.c_int, [_P, C.c_double, _P, _P, C.POINTER(C.c_int64), C.POINTER(C.c_int32)]),
+    "ns_precond_factor": (C.c_int, [_P, _P, _P, _P]),
+    "ns_apply_precond": (C.c_int, [_P, C.c_int, _P, _P, C.c_double, C.c_int, C.c_int]),
     "ns_restart_product": (C.c_int, [C.c_int64, C.c_int, C.c_int, _P, _P, _P, C.c_int, C.c_int, C.c_int, C.c_int,
                                      _P]),
     "ns_project": (C.c_int, [C.c_int64, C.c_int, C.c_int, _P, _P, _P, C.c_int]),
@@ -298,6 +302,33 @@ class Handle:
         Y = np.zeros_like(X)
         self._check(self.lib.ns_apply_B(self.h, d, _ptr(X), _ptr(Y), float(eps), PRECISION[precision], 0,
                                         int(schedule)), "ns_apply_B")
+        return Y
+
+    def precond_build(self, shift: float = 0.1) -> dict:
+        """Outer preconditioner (colouring, renumbering, IC(0) factor); returns
+        color (original numbering), perm (perm[new] = old), ncolors and nnz_L."""
+        color = np.zeros(self.n, dtype=np.int32)
+        perm = np.zeros(self.n, dtype=np.int64)
+        nnzL = C.c_int64()
+        nc = C.c_int32()
+        self._check(self.lib.ns_precond_build(self.h, float(shift), _ptr(color), _ptr(perm), C.byref(nnzL),
+                                              C.byref(nc)), "ns_precond_build")
+        return dict(color=color, perm=perm, nnz_L=int(nnzL.value), ncolors=int(nc.value))
+
+    def precond_factor(self, nnz_L: int):
+        """The factor L (CSR arrays rowptr, colind, vals) of the renumbered matrix."""
+        rp = np.zeros(self.n + 1, dtype=np.int64)
+        ci = np.zeros(max(nnz_L, 1), dtype=np.int32)
+        va = np.zeros(max(nnz_L, 1), dtype=np.float64)
+        self._check(self.lib.ns_precond_factor(self.h, _ptr(rp), _ptr(ci), _ptr(va)), "ns_precond_factor")
+        return rp, ci[:nnz_L], va[:nnz_L]
+
+    def apply_precond(self, X: np.ndarray, eps: float, precision: str = "fp64") -> np.ndarray:
+        """Y = L^-1 A~ L^-T X + eps D X in the renumbered space."""
+        X = np.ascontiguousarray(X, dtype=np.float64)
+        Y = np.zeros_like(X)
+        self._check(self.lib.ns_apply_precond(self.h, X.shape[1], _ptr(X), _ptr(Y), float(eps),
+                                              PRECISION[precision], 0), "ns_apply_precond")
         return Y
 
     def trace_omega(self, d: int, restart_len: int, **opts) -> np.ndarray:

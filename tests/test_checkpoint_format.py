@@ -29,7 +29,7 @@ def record(ns, **kw):
     r = ns.NsCheckpointInfo()
     vals = dict(version=1, m=5, n=4, nnz=9, mode=0, precision=0, d=2, restart_len=12, reorth=0, gemm=0,
                 fp64_products=0, spmm_A=8, spmm_At=4, seed=77, eps=1e-3, tol_eff=1e-10, normA1=3.5, normAinf=2.25,
-                matvecs=48, restarts=2, nullity=1, k0=4)
+                matvecs=48, restarts=2, nullity=1, k0=4, precond=0.0)
     vals.update(kw)
     for k, v in vals.items():
         setattr(r, k, v)
@@ -50,7 +50,7 @@ def ns(lib):
 
 
 def test_record_layout_is_all_eight_byte_fields(ns):
-    assert ctypes.sizeof(ns.NsCheckpointInfo) == 8 * len(ns.NsCheckpointInfo._fields_) == 8 * 22
+    assert ctypes.sizeof(ns.NsCheckpointInfo) == 8 * len(ns.NsCheckpointInfo._fields_) == 8 * 23
 
 
 @pytest.mark.parametrize("payload_len", [0, 8, 13, 1000])
@@ -69,7 +69,7 @@ def test_every_corruption_is_an_io_error(ns, tmp_path):
     cases = {
         "flipped": body[:100] + bytes([body[100] ^ 1]) + body[101:],
         "magic": b"NSCKPT02" + body[8:],
-        "version": b"NSCKPT01" + record(ns, version=2) + body[8 + 176:],
+        "version": b"NSCKPT01" + record(ns, version=2) + body[8 + 184:],
     }
     for name, b in cases.items():
         # the flipped body keeps the good body's checksum; the others carry their own
