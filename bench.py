@@ -85,6 +85,10 @@ WORKLOADS = {
     # configuration 5: 4,096 independent Laplacians in one persistent launch (batched form)
     "batched": dict(cfg=5, mode="spd", d=1, restart=40, precision="mixed", cpu_scale=0.01, ref_scale=0.005,
                     tol=1e-5),
+    # not a benchmark configuration: 500 2-D grid Laplacians (sides 15-30, ~2.6e5 nodes),
+    # badly conditioned, solved with the outer IC(0) preconditioner (Sec. 4.4.2)
+    "grid": dict(cfg=6, mode="spd", d=1, restart=120, precision="fp64", cpu_scale=0.02, ref_scale=0.01,
+                 precond=1),
 }
 
 
@@ -108,7 +112,8 @@ def workload_params(args):
     return dict(name=args.workload, cfg=wl["cfg"], mode=wl["mode"], scale=args.scale,
                 d=args.d or wl["d"], restart=wl["restart"], tol=wl.get("tol", 1e-10),
                 precision=args.precision or wl["precision"], solver_seed=1000 + wl["cfg"] - 1,
-                cpu_scale=wl["cpu_scale"], ref_scale=wl["ref_scale"])
+                cpu_scale=wl["cpu_scale"], ref_scale=wl["ref_scale"],
+                precond=args.precond if args.precond is not None else wl.get("precond", 0))
 
 
 def build_workload(p):
@@ -123,13 +128,16 @@ def describe(p, w):
             "incidence": "oriented edge-vertex incidence matrix (mean degree 8, uniform component sizes), "
                          "normal form A^T A+eps*D",
             "copies": "rectangular sparse N(0,1) matrix, 12 nnz/row, planted sign-flipped column copies, "
-                      "normal form A^T A+eps*D"}[p["name"]]
+                      "normal form A^T A+eps*D",
+            "grid": "graph Laplacian of 2-D grid components (sides 15-30), SPD form"}[p["name"]]
+    if p.get("precond"):
+        kind += ", outer IC(0) preconditioning B_R = L^-1 A~ L^-T + eps*D (diagcomp 0.1)"
     vec = 4 if p["precision"] == "mixed" else 8
     return {"workload": f"{kind}; m={A.m:,} n={A.n:,} nnz={A.nnz:,}, nullity {w.nullity}; "
                         f"{p['precision'].upper()} path, d={p['d']}, restart {p['restart']}, tol {p['tol']:g}",
             "m": int(A.m), "n": int(A.n), "nnz": int(A.nnz), "nullity": int(w.nullity), "d": p["d"],
             "restart_len": p["restart"], "tol": p["tol"], "eps": 1e-3, "precision": p["precision"],
-            "mode": p["mode"],
+            "mode": p["mode"], "precond": int(p.get("precond", 0)),
             "l2": "inputs larger than L2 (Lanczos basis %.2f GB, locked set up to %.2f GB, matrix %.2f GB)"
                   % (A.n * (p["restart"] + p["d"]) * vec * 2 / 1e9, A.n * w.nullity * vec / 1e9,
                      A.nnz * (4 + vec) / 1e9)}
@@ -198,7 +206,7 @@ from oracle import lanczos_nullspace
 w, _ = make_config({cfg}, {scale})
 A = w.A.to_scipy()
 t = time.perf_counter()
-r = lanczos_nullspace(A, {mode!r}, {d}, {restart}, tol={tol}, seed={sseed})
+r = lanczos_nullspace(A, {mode!r}, {d}, {restart}, tol={tol}, seed={sseed}, precond={precond})
 dt = time.perf_counter() - t
 res = float(np.linalg.norm(A @ r.X) / r.normA) if r.N else 0.0
 print(json.dumps(dict(N=int(r.N), expect=int(w.nullity), n=int(A.shape[1]), seconds=dt,
@@ -228,7 +236,8 @@ def run_oracle_sample(p, scale):
                CUDA_VISIBLE_DEVICES="")
     snippet = BATCH_ORACLE_SNIPPET if p["cfg"] == 5 else ORACLE_SNIPPET
     code = snippet.format(root=ROOT, cfg=p["cfg"], scale=scale, mode=p["mode"], d=p["d"],
-                          restart=p["restart"], tol=p["tol"], sseed=p["solver_seed"])
+                          restart=p["restart"], tol=p["tol"], sseed=p["solver_seed"],
+                          precond=0.1 if p.get("precond") else None)
     out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
     if out.returncode != 0:
         raise RuntimeError(out.stderr[-2000:])
@@ -376,7 +385,7 @@ def d_sweep(ns, h, w, p, args, local):
     rows = []
     for d in (1, 2, 4, 8):
         def one():
-            return h.solve(d, R, p["tol"], check=False, precision=precision)
+            return h.solve(d, R, p["tol"], check=False, precision=precision, precond=p["precond"])
         one()
         torch.cuda.synchronize()
         clocks = ClockSampler(local)
@@ -392,7 +401,7 @@ def d_sweep(ns, h, w, p, args, local):
                      "ms": e0.elapsed_time(e1), "nullity": r.nullity, "valid": ok,
                      "t_lanczos_ms": r.stats.get("t_lanczos_ms"), "sm_mhz": clk.get("sm_mhz"),
                      "reasons": clk.get("reasons")})
-    rule = h.solve(0, R, p["tol"], check=False, precision=precision).stats.get("d")
+    rule = h.solve(0, R, p["tol"], check=False, precision=precision, precond=p["precond"]).stats.get("d")
     print(json.dumps({"sweep": "block size d at fixed dim K", "dim_K": R, "precision": precision,
                       "rule_d": rule, "rows": rows,
                       "config": describe(p, w)}), flush=True)
@@ -630,6 +639,8 @@ def main():
                     help="FP64 path's Gram-Schmidt products: 0 compensated FP32 pairs (default), 1 FP64 FMA")
     ap.add_argument("--scale", type=float, default=1.0, help="workload scale (< 1 is for profiling only)")
     ap.add_argument("--kernel-probe", action="store_true", help="launch a few hot kernels, no bench line")
+    ap.add_argument("--precond", type=int, default=None, choices=[0, 1],
+                    help="SPD workloads: outer IC(0) preconditioning (default: on for grid, off otherwise)")
     ap.add_argument("--d-sweep", action="store_true",
                     help="block sizes 1, 2, 4, 8 at a fixed dim K (Sec. 5.3.1), one line, no bench line")
     ap.add_argument("--loop-sample", type=int, default=32,
@@ -684,6 +695,7 @@ def main():
         profile of the last solve, clocks)."""
         def one_step(profile=0):
             return h.solve(p["d"], p["restart"], p["tol"], check=False, precision=precision, profile=profile,
+                           precond=p["precond"],
                            fp64_products=args.fp64_products)
         for _ in range(args.warmup):
             one_step()
@@ -803,7 +815,7 @@ def main():
     e2e_units = 0
     for _ in range(args.e2e_steps):
         he = ns.Handle(rp.numpy(), ci.numpy(), va.numpy(), A.m, A.n, p["solver_seed"], p["mode"])
-        r = he.solve(p["d"], p["restart"], p["tol"], check=False, precision=p["precision"])
+        r = he.solve(p["d"], p["restart"], p["tol"], check=False, precision=p["precision"], precond=p["precond"])
         if valid(r):
             he.lib.ns_basis(he.h, ns.C.c_void_p(out.data_ptr()), A.n, 0)
             e2e_units += r.nullity

@@ -33,7 +33,7 @@ def handle(ns, w, seed):
 
 
 TWINS = {
-    "grid": lambda: laplacian_grid_components(41, 12, 10, 40),
+    "grid": lambda: laplacian_grid_components(41, 12, 10, 30),
     "er_config1": lambda: laplacian_er_components(42, 20, 100, 0.05),
     "cycles_config2": lambda: laplacian_cycle_components(43, 30000, 15, 8, "powerlaw", 50),
 }

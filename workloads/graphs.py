@@ -364,11 +364,14 @@ CONFIGS = {
     3: dict(d=4, restart=160, tol=1e-10, precision="mixed"),
     4: dict(d=2, restart=150, tol=1e-10, precision="mixed"),
     5: dict(d=1, restart=40, tol=1e-5, precision="mixed"),
+    # not one of the five benchmark configurations: badly conditioned grid Laplacians
+    # for the outer preconditioning (Sec. 4.4.2, Sec. 5.1)
+    6: dict(d=1, restart=120, tol=1e-10, precision="fp64"),
 }
 
 
 def make_config(c: int, scale: float = 1.0):
-    """Benchmark configuration c (1..5).  scale < 1 shrinks sizes and component
+    """Benchmark configuration c (1..5; 6 = 500 grid Laplacians, sides 15-30).  scale < 1 shrinks sizes and component
     counts proportionally (reduced-size twins used by the parity tests)."""
     seed = config_seed(c - 1)
     p = dict(CONFIGS[c])
@@ -387,6 +390,8 @@ def make_config(c: int, scale: float = 1.0):
         w = rectangular_copies(seed, m, n, max(2, int(300 * scale)))
     elif c == 5:
         return batched_laplacians(seed, max(1, int(4096 * scale))), p
+    elif c == 6:
+        w = laplacian_grid_components(seed, max(2, int(500 * scale)), 15, 30)
     else:
         raise ValueError(c)
     w.params = p
