@@ -175,7 +175,7 @@ def lanczos_nullspace(A, mode: str, d: int, restart_len: int, tol: float = 1e-10
                       u: float = U_FP64, D: np.ndarray | None = None,
                       Omega: np.ndarray | None = None, record: bool = False,
                       probe=None, keep_rule: str = "capped", ud_rule: str = "ritz",
-                      precond: float | None = None) -> Result:
+                      precond: float | None = None, inner: bool = False) -> Result:
     """Null space of A by Alg. 2 (restarted, partially reorthogonalized small-block Lanczos).
 
     reorth: "partial" (Sec. 4.2), "full" (every new block projected against the whole
@@ -188,6 +188,9 @@ def lanczos_nullspace(A, mode: str, d: int, restart_len: int, tol: float = 1e-10
     precond=alpha (spd mode) runs the method on B_R = L^-1 A~ L^-T + eps D, the outer
     preconditioning of Sec. 4.4.2 with the IC(0) factor L of A~ + alpha diag(A~)
     (oracle.precond), and maps the basis back by Pi L^-T before the refinement.
+    inner=True (normal mode) runs it on B_L = A^T P_L^-1 A + eps D with P_L = diag(A A^T),
+    the inner preconditioning of Sec. 4.4.1 (oracle.precond.inner_scaled); same null
+    space; the refinement runs on the scaled rows S A too (reading P5).
     """
     A = sp.csr_matrix(A, dtype=np.float64)
     n = A.shape[1]
@@ -197,7 +200,14 @@ def lanczos_nullspace(A, mode: str, d: int, restart_len: int, tol: float = 1e-10
     if D is None:
         D = perturbation_diagonal(seed, n)
     pc = None
-    if precond is not None:
+    As = None
+    if inner:
+        from .precond import inner_scaled
+        if mode != "normal" or precond is not None:
+            raise ValueError("inner preconditioning is for the normal form")
+        As = inner_scaled(A)
+        op = Operator(As, mode, eps, D)
+    elif precond is not None:
         from .precond import Preconditioner, PrecondOperator
         if mode != "spd":
             raise ValueError("outer preconditioning is for the spd form")
@@ -428,13 +438,13 @@ def lanczos_nullspace(A, mode: str, d: int, restart_len: int, tol: float = 1e-10
     res["X_lanczos"] = X.copy()
     res["x_theta"] = x_theta
     res["x_rho"] = x_rho
-    Ar = A
+    Ar = A if As is None else As  # the scaled rows also balance the refinement's residual
     if pc is not None and X.shape[1]:
         # Sec. 4.4.2: V approximates null(A L^-T) in the renumbered space; map it back
         X, _ = qr_pos(pc.solve_LT(X).reshape(X.shape))
         Ar = pc.At
     if refine and X.shape[1]:
-        normA = norm2_A(A, mode)
+        normA = norm2_A(A if As is None else As, mode)
         Xr, info = refine_null(Ar, mode, X, refine_tol * normA, refine_maxit)
         Xr, _ = qr_pos(Xr)
         if final_rr:  # Rayleigh-Ritz without the perturbation (Remark after Alg. 1)

@@ -1,4 +1,5 @@
-"""Outer preconditioning for the SPD (graph Laplacian) form (Sec. 4.4.2, Sec. 5.1).
+"""Outer preconditioning for the SPD (graph Laplacian) form (Sec. 4.4.2, Sec. 5.1),
+and inner preconditioning for the normal form (Sec. 4.4.1).
 
 TEST INFRASTRUCTURE ONLY, like the rest of this package.
 
@@ -189,3 +190,13 @@ def effective_condition(M: np.ndarray, nullity: int) -> float:
     nullity (dense; small matrices only)."""
     w = np.linalg.eigvalsh(0.5 * (M + M.T))
     return float(w[-1] / w[nullity])
+
+
+def inner_scaled(A: sp.csr_matrix) -> sp.csr_matrix:
+    """Inner preconditioning (Sec. 4.4.1) with P_L = diag(A A^T): A^T P_L^-1 A equals
+    (S A)^T (S A) with S = diag(1 / ||a_i||_2) (0 for a zero row, the pseudo-inverse).
+    null(S A) = null(A) because S is invertible on the nonzero rows."""
+    A = sp.csr_matrix(A, dtype=np.float64)
+    q = np.asarray(A.multiply(A).sum(axis=1)).ravel()
+    s = np.where(q > 0, 1.0 / np.sqrt(np.where(q > 0, q, 1.0)), 0.0)
+    return sp.csr_matrix(sp.diags(s) @ A)

@@ -128,3 +128,38 @@ def test_preconditioned_solve_finds_the_components():
     assert np.abs(pre.X.T @ pre.X - np.eye(pre.N)).max() <= 1e-12
     assert np.linalg.norm(A @ pre.X) <= 1e-9 * abs(A).sum(axis=1).max()
     assert pre.stats["matvecs"] < plain.stats["matvecs"]
+
+
+# ---------------------------------------------------------- inner (Sec. 4.4.1) ---
+
+def test_inner_scaling_keeps_the_null_space_and_balances_rows():
+    """S A has unit rows (P_L = diag(A A^T)), the planted copy-pair null space of the
+    badly scaled matrix is exactly its null space, and the effective condition of
+    the normal matrix drops."""
+    from oracle import copy_pair_basis
+    from oracle.precond import inner_scaled
+    from workloads import rectangular_copies_scaled
+    w = rectangular_copies_scaled(5, 600, 400, 4, 3.0)
+    A = w.A.to_scipy()
+    As = inner_scaled(A)
+    rn = np.sqrt(np.asarray(As.multiply(As).sum(axis=1)).ravel())
+    assert np.allclose(rn[rn > 0], 1.0, rtol=1e-14)
+    U = copy_pair_basis(400, w.copy_pairs)
+    assert np.abs(As @ U).max() <= 1e-14
+    assert np.abs(A @ U).max() <= 1e-12 * abs(A).max()
+    Gd, Gs = (A.T @ A).toarray(), (As.T @ As).toarray()
+    assert effective_condition(Gs, w.nullity) < effective_condition(Gd, w.nullity) / 10
+
+
+def test_inner_preconditioned_solve_on_badly_scaled_rows():
+    """Rows scaled over 3 decades: the plain method does not find the null space within
+    its budget, the inner-preconditioned one finds all of it."""
+    from oracle import copy_pair_basis
+    from workloads import rectangular_copies_scaled
+    w = rectangular_copies_scaled(23, 4500, 3000, 6, 3.0)
+    A = w.A.to_scipy()
+    pre = lanczos_nullspace(A, "normal", 2, 60, tol=1e-10, seed=9, inner=True)
+    assert pre.N == 6
+    assert principal_sine(pre.X, copy_pair_basis(3000, w.copy_pairs)) <= 1e-8
+    plain = lanczos_nullspace(A, "normal", 2, 60, tol=1e-10, seed=9, max_matvec=10 * pre.stats["matvecs"])
+    assert plain.N < 6

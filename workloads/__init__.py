@@ -15,6 +15,7 @@ from .graphs import (  # noqa: F401
     laplacian_grid_components,
     incidence_cycle_components,
     rectangular_copies,
+    rectangular_copies_scaled,
     batched_laplacians,
     diag_example,
     tiny_planted,

@@ -304,6 +304,20 @@ def rectangular_copies(seed: int, m: int, n: int, ncopies: int, nnz_per_row: int
     return Workload("rectangular_copies", CSR.from_scipy(M), "normal", ncopies, copy_pairs=pairs)
 
 
+def rectangular_copies_scaled(seed: int, m: int, n: int, ncopies: int, decades: float = 3.0) -> Workload:
+    """rectangular_copies with every row multiplied by 10^u, u uniform in
+    [-decades/2, decades/2]: a copied column stays a copy (both entries of a row get
+    the same factor), so the planted null space is unchanged while A^T A becomes
+    badly scaled -- the case inner preconditioning with diag(A A^T) is meant for."""
+    w = rectangular_copies(seed, m, n, ncopies)
+    rng = np.random.default_rng(seed + 7919)
+    f = 10.0 ** rng.uniform(-decades / 2, decades / 2, size=w.A.m)
+    A = w.A.to_scipy()
+    w.A = CSR.from_scipy(sp.coo_matrix(sp.diags(f) @ A))
+    w.name = "copies_scaled"
+    return w
+
+
 def batched_laplacians(seed: int, count: int, n_min: int = 200, n_max: int = 20000,
                        mean_degree: int = 6, max_comp: int = 8) -> list[Workload]:
     """Independent cycle-union Laplacians, n log-uniform in [n_min, n_max], 1..max_comp components."""
