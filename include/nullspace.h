@@ -114,7 +114,10 @@ typedef struct {
                           priorities from Philox stream 0x7FFFFFFF) and L the zero-fill
                           incomplete Cholesky factor of A~ + precond_shift diag(A~); the
                           basis is mapped back by Pi L^-T, re-orthonormalized and refined
-                          against A.  0 = none (default)                                */
+                          against A.  NS_MODE_NORMAL only: 2 = inner preconditioning
+                          (Sec. 4.4.1), B_L = A^T P_L^-1 A + eps D with P_L = diag(A A^T),
+                          applied as the row scaling (S A)^T (S A), S = P_L^-1/2 (0 on a zero
+                          row); same null space, refinement against A.  0 = none (default) */
   double precond_shift;/* diagonal compensation of the factor (Eq. defichol: 0.1, default) */
 } ns_opts;
 
@@ -227,7 +230,7 @@ typedef struct {
   double normA1, normAinf; /* ||A||_1, ||A||_inf of the handle (a check of the values) */
   int64_t matvecs, restarts, nullity; /* progress: B applications, restarts, locked   */
   int64_t k0;              /* retained Ritz vectors (the next cycle starts at block k0/d) */
-  double precond;          /* precond_shift of a preconditioned solve, 0 without          */
+  double precond;          /* precond_shift of an outer-preconditioned solve, -1 inner, 0 none */
 } ns_checkpoint_info;
 
 /* ns_read_checkpoint -- read and verify a checkpoint file on the host (no device
@@ -329,11 +332,18 @@ ns_status ns_precond_build(ns_handle* h, double shift, int32_t* color, int64_t* 
  * last) and vals, host arrays.  NS_ERR_STATE before a build. */
 ns_status ns_precond_factor(const ns_handle* h, int64_t* rowptr, int32_t* colind, double* vals);
 
+/* ns_inner_precond -- build (or reuse) the inner preconditioner of opts.precond = 2
+ * (Sec. 4.4.1) on a NS_MODE_NORMAL handle (else NS_ERR_STATE): P_L = diag(A A^T), kept
+ * as the row scaling s_i = 1/||a_i||_2 (0 for a zero row) and the scaled copies S A
+ * and A^T S.  row_scale: m doubles (host) receiving s, may be NULL. */
+ns_status ns_inner_precond(ns_handle* h, double* row_scale);
+
 /* Y = B_R X = L^-1 A~ L^-T X + eps D X in the renumbered space (D indexed there as
- * drawn), for an n x d row-major block, d in {1, 2, 4, 8}; host or device memory
- * (on_device); precision NS_FP64 or NS_MIXED (FP32 values and arithmetic, Y
+ * drawn) on a NS_MODE_SPD handle, or Y = B_L X = A^T P_L^-1 A X + eps D X on a
+ * NS_MODE_NORMAL handle; an n x d row-major block, d in {1, 2, 4, 8}; host or device
+ * memory (on_device); precision NS_FP64 or NS_MIXED (FP32 values and arithmetic, Y
  * widened).  The triangular solves take one launch per colour.  NS_ERR_STATE
- * before ns_precond_build. */
+ * before ns_precond_build / ns_inner_precond. */
 ns_status ns_apply_precond(ns_handle* h, int d, const double* X, double* Y, double eps, int precision,
                            int on_device);
 

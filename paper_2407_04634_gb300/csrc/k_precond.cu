@@ -250,6 +250,41 @@ void cols_to_panel_t(const T* X, int c0, int w, int64_t n, T* P, cudaStream_t s)
   if (n > 0) k_cols_to_panel_t<T><<<rows_grid(n), kThreads, 0, s>>>(X, c0, w, n, P);
 }
 
+// ---------------------------------------------------------------------------
+// Inner preconditioning of the normal form (Sec. 4.4.1) with P_L = diag(A A^T):
+// s_i = 1 / ||a_i||_2 per row of A (0 for a zero row), then S A (each entry times
+// its row's s) and A^T S (each entry of A^T times the s of its column, which is the
+// row of A it came from).
+// ---------------------------------------------------------------------------
+__global__ void k_row_inv_norms(const int64_t* __restrict__ rowptr, const double* __restrict__ val, int64_t m,
+                                double* __restrict__ s) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    double q = 0.0;
+    for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) q = fma(val[e], val[e], q);
+    s[i] = q > 0.0 ? 1.0 / sqrt(q) : 0.0;
+  }
+}
+__global__ void k_scale_rows(const int64_t* __restrict__ rowptr, const double* __restrict__ val, int64_t m,
+                             const double* __restrict__ s, double* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    const double si = s[i];
+    for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) out[e] = val[e] * si;
+  }
+}
+__global__ void k_scale_by_col(const int* __restrict__ col, const double* __restrict__ val, int64_t nnz,
+                               const double* __restrict__ s, double* __restrict__ out) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = val[e] * s[col[e]];
+}
+void inner_scaling(const int64_t* rowptr, const double* val, int64_t m, const int* col_t, const double* val_t,
+                   int64_t nnz, double* s, double* val_s, double* val_t_s, cudaStream_t st) {
+  if (m > 0) {
+    k_row_inv_norms<<<rows_grid(m), kThreads, 0, st>>>(rowptr, val, m, s);
+    k_scale_rows<<<rows_grid(m), kThreads, 0, st>>>(rowptr, val, m, s, val_s);
+  }
+  if (nnz > 0) k_scale_by_col<<<rows_grid(nnz), kThreads, 0, st>>>(col_t, val_t, nnz, s, val_t_s);
+}
+
 #define NS_INST_PC(T, D)                                                                                           \
   template void trsv_colors<T, D>(const int64_t*, const int*, const T*, const int64_t*, int, bool, const T*, T*, \
                                   cudaStream_t);                                                                 \

@@ -143,6 +143,14 @@ struct ns_handle {
     double *aval = nullptr, *lval = nullptr, *uval = nullptr;
     float *aval32 = nullptr, *lval32 = nullptr, *uval32 = nullptr;
   } pc;
+  // inner preconditioner P_L = diag(A A^T) of the normal form (Sec. 4.4.1), built on first use
+  struct Inner {
+    bool built = false;
+    double* s = nullptr;                       // 1 / ||a_i||_2 per row of A (0 for a zero row)
+    double *val = nullptr, *val_t = nullptr;   // S A and A^T S (A's and A^T's CSR order)
+    float *val32 = nullptr, *val_t32 = nullptr;
+    double normA1 = 0.0, normAinf = 0.0;       // ||S A||_1, ||S A||_inf
+  } inner;
   // result
   bool solved = false;
   int64_t N = 0;
@@ -457,6 +465,38 @@ void build_precond(ns_handle* h, double alpha) {
   }
 }
 
+// Inner preconditioner of the normal form (Sec. 4.4.1): P_L = diag(A A^T), applied as
+// the row scaling S = P_L^-1/2 (the pseudo-inverse for zero rows), so that
+// A^T P_L^-1 A = (S A)^T (S A).  Its null space is A's.
+void build_inner(ns_handle* h) {
+  auto& I = h->inner;
+  if (I.built) return;
+  cudaStream_t s = h->stream;
+  const int64_t m = h->m, n = h->n, nnz = h->nnz;
+  I.s = (double*)dalloc_own(h, sizeof(double) * std::max<int64_t>(m, 1));
+  I.val = (double*)dalloc_own(h, sizeof(double) * csr_entries(nnz));
+  I.val_t = (double*)dalloc_own(h, sizeof(double) * csr_entries(nnz));
+  ck(cudaMemsetAsync(I.val, 0, sizeof(double) * csr_entries(nnz), s), "memset");
+  ck(cudaMemsetAsync(I.val_t, 0, sizeof(double) * csr_entries(nnz), s), "memset");
+  inner_scaling(h->rowptr, h->val, m, h->col_t, h->val_t, nnz, I.s, I.val, I.val_t, s);
+  Buf rp(h, sizeof(double) * (size_t)kMaxBlocks * 64 + 256), sm(h, 4096);
+  ck(cudaMemsetAsync(sm.p, 0, 4096, s), "memset");
+  Red red;
+  red.part = rp.as<double>();
+  red.ticket = reinterpret_cast<unsigned*>(sm.as<char>() + 1024);
+  double* norms = reinterpret_cast<double*>(sm.as<char>() + 2048);
+  csr_max_abs_row_sum(h->rowptr, I.val, m, norms, red, s);
+  csr_max_abs_row_sum(h->rowptr_t, I.val_t, n, norms + 1, red, s);
+  h->launches += 5;
+  double nr[2] = {0.0, 0.0};
+  ck(cudaMemcpyAsync(nr, norms, sizeof(nr), cudaMemcpyDeviceToHost, s), "d2h");
+  ck(cudaStreamSynchronize(s), "sync");
+  ck_launch("inner preconditioner");
+  I.normAinf = nr[0];
+  I.normA1 = nr[1];
+  I.built = true;
+}
+
 void ensure_fp32(ns_handle* h) {
   // FP32 copies of A's values (already present when A came in as FP32), A^T's values and D
   if (!h->val32) {
@@ -470,6 +510,13 @@ void ensure_fp32(ns_handle* h) {
   if (!h->D32) {
     h->D32 = (float*)dalloc_own(h, sizeof(float) * (size_t)h->n);
     convert_d2f(h->D64, h->D32, h->n, h->stream);
+  }
+  auto& I = h->inner;
+  if (I.built && !I.val32) {
+    I.val32 = (float*)dalloc_own(h, sizeof(float) * csr_entries(h->nnz));
+    I.val_t32 = (float*)dalloc_own(h, sizeof(float) * csr_entries(h->nnz));
+    convert_d2f(I.val, I.val32, h->nnz, h->stream);
+    convert_d2f(I.val_t, I.val_t32, h->nnz, h->stream);
   }
   auto& P = h->pc;
   if (P.built && !P.aval32) {
@@ -595,7 +642,16 @@ struct Solver {
     bd_tol = 100.0 * u_d;
     A = csr_A<T>(h);
     if (h->mode == NS_MODE_NORMAL) At = csr_At<T>(h);
-    if (o.precond) {
+    if (o.precond == 2) {  // B_L = (S A)^T (S A) + eps D (Sec. 4.4.1); the CSR schedules only
+      const auto& I = h->inner;
+      A.val = pc_vals<T>(I.val, I.val32);
+      At.val = pc_vals<T>(I.val_t, I.val_t32);
+      A.sptr = At.sptr = nullptr;
+      normB = I.normA1 * I.normAinf + eps;
+      u_d = ud_per_normB * normB;
+      bd_tol = 100.0 * u_d;
+    }
+    if (o.precond == 1) {
       pc = &h->pc;
       A = Csr<T>{};
       A.rowptr = pc->arp;
@@ -1299,7 +1355,7 @@ struct Solver {
     c.restarts = restarts;
     c.nullity = nlock;
     c.k0 = k0;
-    c.precond = pc ? pc->alpha : 0.0;
+    c.precond = pc ? pc->alpha : (o.precond == 2 ? -1.0 : 0.0);
     return c;
   }
   // host scalars of the iteration, in file order
@@ -1439,7 +1495,16 @@ RefineOut refine(ns_handle* h, double* X, int64_t N, double normA, const ns_opts
   Csr<double> A64 = csr_A<double>(h);
   Csr<float> A32 = csr_A<float>(h), At32;
   if (normal) At32 = csr_At<float>(h);
-  if (o.precond) {  // the basis is in the renumbered space: refine against A~
+  if (o.precond == 2) {  // reading P5: the scaled rows S A (same null space, balanced residual)
+    const auto& I = h->inner;
+    A64.val = I.val;
+    A32.val = I.val32;
+    At32.val = I.val_t32;
+    A64.sptr = A32.sptr = At32.sptr = nullptr;
+    if (A64.V == kSchedSell || A64.V == kSchedTma) A64.V = A32.V = 8;
+    if (At32.V == kSchedSell || At32.V == kSchedTma) At32.V = 8;
+  }
+  if (o.precond == 1) {  // the basis is in the renumbered space: refine against A~
     const auto& P = h->pc;
     A64 = Csr<double>{};
     A64.rowptr = P.arp;
@@ -1683,7 +1748,7 @@ static ns_status solve_typed(ns_handle* h, int R, double tol, const ns_opts& o) 
     if (rec.precision != (std::is_same<T, float>::value ? NS_MIXED : NS_FP64) || rec.d != D ||
         rec.restart_len != R || rec.reorth != o.reorth || rec.gemm != o.gemm ||
         rec.fp64_products != o.fp64_products || rec.eps != o.eps ||
-        rec.precond != (o.precond ? o.precond_shift : 0.0))
+        rec.precond != (o.precond == 1 ? o.precond_shift : o.precond == 2 ? -1.0 : 0.0))
       throw Fail{NS_ERR_INVALID_ARG, "checkpoint of a solve with other d, restart_len or opts"};
   }
   Solver<T, D> S(h, R, tol, o, o.resume ? &rec : nullptr);
@@ -1703,7 +1768,8 @@ static ns_status solve_typed(ns_handle* h, int R, double tol, const ns_opts& o) 
       convert_f2d(reinterpret_cast<const float*>(S.X()), h->basis, (int64_t)N * h->n, s);
   }
   double normA = (h->mode == NS_MODE_NORMAL) ? std::sqrt(std::max(S.theta_max, 0.0)) : S.theta_max;
-  if (o.precond) {
+  if (o.precond == 2) normA = std::sqrt(h->inner.normA1 * h->inner.normAinf);  // bound on ||S A||_2
+  if (o.precond == 1) {
     // the Ritz values are those of B_R: ||A||_2 is bounded by ||A||_inf instead
     normA = h->normAinf;
     if (N) {
@@ -1761,7 +1827,7 @@ static ns_status solve_typed(ns_handle* h, int R, double tol, const ns_opts& o) 
       orth1 = 0.375 * (*mx_h) * (*mx_h) * N;  // predicted second-order remainder
       if (*mx_h <= 1e-6) break;
     }
-    if (o.precond) {  // rows back to the original numbering
+    if (o.precond == 1) {  // rows back to the original numbering
       unpermute_cols(h->basis, h->pc.perm, h->n, (int)N, X2, s);
       h->launches += 1;
       std::swap(h->basis, X2);
@@ -1826,7 +1892,7 @@ static void trace_omega_typed(ns_handle* h, int R, const ns_opts& o, double* W) 
 }
 
 template <typename T, int D>
-static void apply_B_typed(ns_handle* h, const T* x, T* y, double eps, Red red, int schedule, bool pre = false) {
+static void apply_B_typed(ns_handle* h, const T* x, T* y, double eps, Red red, int schedule, int pre = 0) {
   StepOps<T> op;
   op.x = x;
   op.Dv = Prec<T>::D(h);
@@ -1838,7 +1904,13 @@ static void apply_B_typed(ns_handle* h, const T* x, T* y, double eps, Red red, i
   Csr<T> A = csr_A<T>(h);
   Csr<T> At = h->mode == NS_MODE_SPD ? A : csr_At<T>(h);
   if (schedule >= 0) A.V = At.V = schedule;
-  if (pre) {  // B_R x = L^-1 A~ L^-T x + eps D x, renumbered space
+  if (pre == 2) {  // B_L x = (S A)^T (S A) x + eps D x (Sec. 4.4.1)
+    A.val = pc_vals<T>(h->inner.val, h->inner.val32);
+    At.val = pc_vals<T>(h->inner.val_t, h->inner.val_t32);
+    A.sptr = At.sptr = nullptr;
+    if (A.V == kSchedSell) A.V = At.V = 8;
+  }
+  if (pre == 1) {  // B_R x = L^-1 A~ L^-T x + eps D x, renumbered space
     const auto& P = h->pc;
     Csr<T> Ap;
     Ap.rowptr = P.arp;
@@ -2180,16 +2252,19 @@ ns_status ns_solve(ns_handle* h, int d, int restart_len, double tol, const ns_op
     if (o.checkpoint_every < 0 || !(o.resume == 0 || o.resume == 1) ||
         ((o.checkpoint_every > 0 || o.resume) && (!o.checkpoint_path || !*o.checkpoint_path)))
       return set_err(h, NS_ERR_INVALID_ARG, "checkpoint_every >= 0, resume 0 or 1, both need checkpoint_path");
-    if (!(o.precond == 0 || o.precond == 1) || (o.precond && h->mode != NS_MODE_SPD) ||
-        (o.precond && !(o.precond_shift >= 0.0 && std::isfinite(o.precond_shift))))
-      return set_err(h, NS_ERR_INVALID_ARG, "precond: 0 or 1, NS_MODE_SPD only, precond_shift >= 0");
+    if (!(o.precond >= 0 && o.precond <= 2) || (o.precond == 1 && h->mode != NS_MODE_SPD) ||
+        (o.precond == 2 && h->mode != NS_MODE_NORMAL) ||
+        (o.precond == 1 && !(o.precond_shift >= 0.0 && std::isfinite(o.precond_shift))))
+      return set_err(h, NS_ERR_INVALID_ARG,
+                     "precond: 0, 1 (outer, NS_MODE_SPD, precond_shift >= 0) or 2 (inner, NS_MODE_NORMAL)");
   }
   h->err.clear();
   h->solved = false;
   h->launches = 0;
   try {
     ns_status st;
-    if (o.precond) build_precond(h, o.precond_shift);
+    if (o.precond == 1) build_precond(h, o.precond_shift);
+    if (o.precond == 2) build_inner(h);
     if (o.precision == NS_MIXED) {
       ensure_fp32(h);
       switch (d) {
@@ -2403,6 +2478,20 @@ ns_status ns_precond_build(ns_handle* h, double shift, int32_t* color, int64_t* 
   return NS_OK;
 }
 
+ns_status ns_inner_precond(ns_handle* h, double* row_scale) {
+  if (!h) return NS_ERR_INVALID_ARG;
+  if (h->mode != NS_MODE_NORMAL) return set_err(h, NS_ERR_STATE, "inner preconditioning needs NS_MODE_NORMAL");
+  try {
+    build_inner(h);
+    if (row_scale && h->m)
+      ck(cudaMemcpy(row_scale, h->inner.s, sizeof(double) * h->m, cudaMemcpyDeviceToHost), "d2h");
+  } catch (const Fail& f) {
+    cudaGetLastError();
+    return set_err(h, f.st, f.msg);
+  }
+  return NS_OK;
+}
+
 ns_status ns_precond_factor(const ns_handle* h, int64_t* rowptr, int32_t* colind, double* vals) {
   if (!h || !rowptr) return NS_ERR_INVALID_ARG;
   const auto& P = h->pc;
@@ -2422,7 +2511,10 @@ ns_status ns_apply_precond(ns_handle* h, int d, const double* X, double* Y, doub
                            int on_device) {
   if (!h || !X || !Y || !(d == 1 || d == 2 || d == 4 || d == 8)) return NS_ERR_INVALID_ARG;
   if (!(precision == NS_FP64 || precision == NS_MIXED)) return set_err(h, NS_ERR_INVALID_ARG, "precision");
-  if (!h->pc.built || h->pc.alpha < 0.0) return set_err(h, NS_ERR_STATE, "no preconditioner: ns_precond_build first");
+  const int kind = h->mode == NS_MODE_SPD ? 1 : 2;
+  if (kind == 1 && (!h->pc.built || h->pc.alpha < 0.0))
+    return set_err(h, NS_ERR_STATE, "no preconditioner: ns_precond_build first");
+  if (kind == 2 && !h->inner.built) return set_err(h, NS_ERR_STATE, "no preconditioner: ns_inner_precond first");
   try {
     const size_t cnt = (size_t)h->n * d;
     Buf xb(h, sizeof(double) * cnt), yb(h, sizeof(double) * cnt), rp(h, sizeof(double) * kMaxBlocks * 64 + 256),
@@ -2439,18 +2531,18 @@ ns_status ns_apply_precond(ns_handle* h, int d, const double* X, double* Y, doub
       Buf xf(h, sizeof(float) * cnt), yf(h, sizeof(float) * cnt);
       convert_d2f(xb.as<double>(), xf.as<float>(), (int64_t)cnt, h->stream);
       switch (d) {
-        case 1: apply_B_typed<float, 1>(h, xf.as<float>(), yf.as<float>(), eps, red, -1, true); break;
-        case 2: apply_B_typed<float, 2>(h, xf.as<float>(), yf.as<float>(), eps, red, -1, true); break;
-        case 4: apply_B_typed<float, 4>(h, xf.as<float>(), yf.as<float>(), eps, red, -1, true); break;
-        default: apply_B_typed<float, 8>(h, xf.as<float>(), yf.as<float>(), eps, red, -1, true); break;
+        case 1: apply_B_typed<float, 1>(h, xf.as<float>(), yf.as<float>(), eps, red, -1, kind); break;
+        case 2: apply_B_typed<float, 2>(h, xf.as<float>(), yf.as<float>(), eps, red, -1, kind); break;
+        case 4: apply_B_typed<float, 4>(h, xf.as<float>(), yf.as<float>(), eps, red, -1, kind); break;
+        default: apply_B_typed<float, 8>(h, xf.as<float>(), yf.as<float>(), eps, red, -1, kind); break;
       }
       convert_f2d(yf.as<float>(), yb.as<double>(), (int64_t)cnt, h->stream);
     } else {
       switch (d) {
-        case 1: apply_B_typed<double, 1>(h, xb.as<double>(), yb.as<double>(), eps, red, -1, true); break;
-        case 2: apply_B_typed<double, 2>(h, xb.as<double>(), yb.as<double>(), eps, red, -1, true); break;
-        case 4: apply_B_typed<double, 4>(h, xb.as<double>(), yb.as<double>(), eps, red, -1, true); break;
-        default: apply_B_typed<double, 8>(h, xb.as<double>(), yb.as<double>(), eps, red, -1, true); break;
+        case 1: apply_B_typed<double, 1>(h, xb.as<double>(), yb.as<double>(), eps, red, -1, kind); break;
+        case 2: apply_B_typed<double, 2>(h, xb.as<double>(), yb.as<double>(), eps, red, -1, kind); break;
+        case 4: apply_B_typed<double, 4>(h, xb.as<double>(), yb.as<double>(), eps, red, -1, kind); break;
+        default: apply_B_typed<double, 8>(h, xb.as<double>(), yb.as<double>(), eps, red, -1, kind); break;
       }
     }
     ck(cudaMemcpyAsync(Y, yb.p, sizeof(double) * cnt, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,

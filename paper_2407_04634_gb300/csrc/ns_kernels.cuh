@@ -276,6 +276,10 @@ void trsv_colors(const int64_t* rp, const int* col, const T* val, const int64_t*
 template <typename T, int D>
 void lanczos_epilogue(const T* w, int64_t n, const StepOps<T>& op, const Red& red, cudaStream_t s);
 void unpermute_cols(const double* in, const int64_t* perm, int64_t n, int ncols, double* out, cudaStream_t s);
+// inner preconditioning with P_L = diag(A A^T): s = 1/||a_i|| (0 for a zero row),
+// val_s = S A (A's CSR order), val_t_s = A^T S (A^T's CSR order, col_t its columns)
+void inner_scaling(const int64_t* rowptr, const double* val, int64_t m, const int* col_t, const double* val_t,
+                   int64_t nnz, double* s, double* val_s, double* val_t_s, cudaStream_t st);
 template <typename T>
 void cols_to_panel_t(const T* X, int c0, int w, int64_t n, T* P, cudaStream_t s);
 

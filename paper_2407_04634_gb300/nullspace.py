@@ -105,6 +105,7 @@ SIGNATURES = {
     "ns_fma_peak": (C.c_int, [C.c_int, C.POINTER(C.c_double)]),
     "ns_precond_build": (C.c_int, [_P, C.c_double, _P, _P, C.POINTER(C.c_int64), C.POINTER(C.c_int32)]),
     "ns_precond_factor": (C.c_int, [_P, _P, _P, _P]),
+    "ns_inner_precond": (C.c_int, [_P, _P]),
     "ns_apply_precond": (C.c_int, [_P, C.c_int, _P, _P, C.c_double, C.c_int, C.c_int]),
     "ns_restart_product": (C.c_int, [C.c_int64, C.c_int, C.c_int, _P, _P, _P, C.c_int, C.c_int, C.c_int, C.c_int,
                                      _P]),
@@ -323,8 +324,15 @@ class Handle:
         self._check(self.lib.ns_precond_factor(self.h, _ptr(rp), _ptr(ci), _ptr(va)), "ns_precond_factor")
         return rp, ci[:nnz_L], va[:nnz_L]
 
+    def inner_precond(self) -> np.ndarray:
+        """Inner preconditioner (normal form): the row scaling s_i = 1/||a_i|| of P_L^-1/2."""
+        s = np.zeros(max(self.m, 1), dtype=np.float64)
+        self._check(self.lib.ns_inner_precond(self.h, _ptr(s)), "ns_inner_precond")
+        return s[:self.m]
+
     def apply_precond(self, X: np.ndarray, eps: float, precision: str = "fp64") -> np.ndarray:
-        """Y = L^-1 A~ L^-T X + eps D X in the renumbered space."""
+        """Y = L^-1 A~ L^-T X + eps D X in the renumbered space (SPD handle), or
+        Y = A^T P_L^-1 A X + eps D X (normal handle)."""
         X = np.ascontiguousarray(X, dtype=np.float64)
         Y = np.zeros_like(X)
         self._check(self.lib.ns_apply_precond(self.h, X.shape[1], _ptr(X), _ptr(Y), float(eps),

@@ -1,4 +1,4 @@
-"""Outer preconditioning on the GPU (Sec. 4.4.2) against the oracle.
+"""Outer (Sec. 4.4.2) and inner (Sec. 4.4.1) preconditioning on the GPU against the oracle.
 
 Colouring and renumbering are integer work: bit-exact.  The IC(0) factor: the
 same pattern exactly, values within 1e-13 relative (the same operations in the same
@@ -143,3 +143,49 @@ def test_preconditioned_resume_is_bit_identical(ns, tmp_path):
     r2 = h2.solve(1, 60, 1e-10, precond=1, resume=1, checkpoint_path=path)
     assert r2.stats["matvecs"] == r0.stats["matvecs"]
     assert np.array_equal(h2.basis(), X0)
+
+
+# ------------------------------------------------------ inner (Sec. 4.4.1) ---
+
+def test_inner_scaling_and_operator_match_the_oracle(ns):
+    from oracle import Operator
+    from oracle.precond import inner_scaled
+    from workloads import rectangular_copies_scaled
+    w = rectangular_copies_scaled(51, 3000, 2000, 5, 3.0)
+    A = w.A.to_scipy()
+    h = handle(ns, w, 4)
+    s = h.inner_precond()
+    q = np.asarray(A.multiply(A).sum(axis=1)).ravel()
+    assert np.abs(s - 1.0 / np.sqrt(q)).max() <= 1e-15 * np.abs(s).max()
+    D = h.perturbation()
+    ref = Operator(inner_scaled(A), "normal", 1e-3, D)
+    for precision, d, tol in (("fp64", 2, 1e-13), ("mixed", 4, 1e-5)):
+        X = np.random.default_rng(d).standard_normal((w.A.n, d))
+        Y = h.apply_precond(X, 1e-3, precision)
+        Yr = ref.apply(X)
+        assert np.abs(Y - Yr).max() <= tol * np.abs(Yr).max(), precision
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_inner_preconditioned_solve_matches_the_oracle(ns, precision):
+    from oracle import copy_pair_basis
+    from workloads import rectangular_copies_scaled
+    w = rectangular_copies_scaled(23, 4500, 3000, 6, 3.0)
+    ref = lanczos_nullspace(w.A.to_scipy(), "normal", 2, 60, tol=1e-10, seed=9, inner=True)
+    h = handle(ns, w, 9)
+    r = h.solve(2, 60, 1e-10, precision=precision, precond=2)
+    assert r.nullity == ref.N == 6
+    X = h.basis()
+    bar = 1e-6 if precision == "fp64" else 1e-5
+    assert principal_sine(X, copy_pair_basis(3000, w.copy_pairs)) <= bar
+    assert principal_sine(X, ref.X) <= bar
+    plain = h.solve(2, 60, 1e-10, check=False, precision=precision, max_matvec=10 * r.stats["matvecs"])
+    assert plain.nullity < 6  # the badly scaled rows stall the plain method within that budget
+
+
+def test_inner_precond_options_are_checked(ns):
+    g = TWINS["grid"]()
+    hg = handle(ns, g, 1)
+    assert hg.solve(1, 60, 1e-10, check=False, precond=2).status == ns.NS_ERR_INVALID_ARG  # SPD handle
+    with pytest.raises(ns.NullspaceError):
+        hg.inner_precond()
