@@ -61,6 +61,8 @@ Readings of points the paper leaves open (the CUDA path takes the same readings)
       locked nothing.  Before the first lock there is no speed estimate; then the
       smallest Ritz value must also have converged (residual within the lock
       tolerance) at or above 3 eps, the direct test Sec. 4.3 starts from;
+  L1  eps = 0 (the large-block variant of Sec. 5.3.2, d >= N, no perturbation): the null
+      Ritz values sit at rounding level, so "below 3 eps" becomes theta <= tol ||B||;
   R12 breakdown (sigma_min(Gamma) <= 100 u_d): the block is replaced by a fresh
       Gaussian block (Philox stream 2+k) orthogonalized against [X, Z], and
       Gamma is set to zero;
@@ -357,7 +359,8 @@ def lanczos_nullspace(A, mode: str, d: int, restart_len: int, tol: float = 1e-10
             normB_est = min(normB, 1.1 * st["theta_max"])
             u_d = d * np.sqrt(n) * u * normB_est
             bd_tol = 100.0 * u_d
-        small = theta < 3 * eps
+        # Remark cormain: Ritz values below 3 eps count as null; reading L1 for eps = 0
+        small = theta < 3 * eps if eps > 0 else theta <= tol * normB_est
         if record and restart:
             st.setdefault("cycles", []).append(dict(T=T, Z=Z[:, :R].copy(), Qnext=Z[:, R:R + d].copy(),
                                                     Gamma_last=Gam[nb - 1].copy(), X=X.copy(),
@@ -423,7 +426,7 @@ def lanczos_nullspace(A, mode: str, d: int, restart_len: int, tol: float = 1e-10
             s = float(R)
         s = max(s, float(R))
         since = st["matvecs"] - (ev[-1][0] if ev else 0)
-        settled = bool(ev) or (theta[0] >= 3.0 * eps and resid[0] <= tol * normB_est)
+        settled = bool(ev) or (not small[0] and resid[0] <= tol * normB_est)
         if n_unl == 0 and nlock == 0 and since > stop_factor * s and settled:
             converged = True
             break

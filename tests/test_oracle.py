@@ -375,3 +375,20 @@ def test_slow_start_waits_for_the_first_lock():
         assert principal_sine(r.X, copy_pair_basis(4000, w.copy_pairs)) <= 1e-8
         mv[d] = r.stats["matvecs"]
     assert mv[8] > mv[2]
+
+
+def test_unperturbed_block_lanczos_needs_block_size_at_least_the_nullity():
+    """Sec. 5.3.2: without the perturbation (eps = 0) the null eigenvalue is N-fold and a
+    block Krylov space holds at most d vectors of its eigenspace, so d < N misses null
+    vectors while the large-block variant d >= N finds them all (reading L1 counts the
+    rounding-level Ritz values as null)."""
+    w = rectangular_copies(23, 4500, 3000, 6)
+    A = w.A.to_scipy()
+    big = lanczos_nullspace(A, "normal", 8, 64, tol=1e-10, seed=9, eps=0.0)
+    assert big.N == 6
+    assert principal_sine(big.X, copy_pair_basis(3000, w.copy_pairs)) <= 1e-8
+    for d in (1, 2):
+        small = lanczos_nullspace(A, "normal", d, 16 if d == 2 else 60, tol=1e-10, seed=9, eps=0.0)
+        assert small.N < 6, d
+    pert = lanczos_nullspace(A, "normal", 2, 16, tol=1e-10, seed=9, eps=1e-3)
+    assert pert.N == 6
