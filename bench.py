@@ -415,6 +415,33 @@ def d_sweep(ns, h, w, p, args, local):
                       "config": describe(p, w)}), flush=True)
 
 
+def large_block(ns, h, w, p, args, local):
+    """Small-block (perturbed, the workload's d) against the large-block variant of
+    Sec. 5.3.2 (eps = 0, d = 8 >= N; Table tabCHLB) on a workload with nullity <= 8: one
+    untimed and one timed solve each (CUDA events on the current stream)."""
+    import torch
+    if w.nullity > 8:
+        raise SystemExit("--large-block needs a nullity <= 8 (the kernels' largest block); use a small --scale")
+    precision = args.precision or p["precision"]
+    stream = torch.cuda.current_stream()
+    rows = []
+    for name, d, R, eps in (("small-block", p["d"], p["restart"], 1e-3), ("large-block", 8, 64, 0.0)):
+        def one():
+            return h.solve(d, R, p["tol"], check=False, precision=precision, eps=eps)
+        one()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = one()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        rows.append({"variant": name, "d": d, "restart_len": R, "eps": eps, "status": ns.STATUS.get(r.status),
+                     "nullity": r.nullity, "matvecs": r.stats.get("matvecs"), "restarts": r.stats.get("restarts"),
+                     "ms": e0.elapsed_time(e1), "refine_resid_max": r.stats.get("refine_resid_max")})
+    print(json.dumps({"comparison": "small-block vs large-block (Sec. 5.3.2)", "precision": precision,
+                      "rows": rows, "config": describe(p, w)}), flush=True)
+
+
 def kernel_probe(ns, h, w, p):
     """A handful of hot-kernel launches on the workload's inputs (for ncu captures):
     three B-applies in each precision and every SpMM schedule, the thick-restart
@@ -649,6 +676,8 @@ def main():
     ap.add_argument("--kernel-probe", action="store_true", help="launch a few hot kernels, no bench line")
     ap.add_argument("--precond", type=int, default=None, choices=[0, 1],
                     help="SPD workloads: outer IC(0) preconditioning (default: on for grid, off otherwise)")
+    ap.add_argument("--large-block", action="store_true",
+                    help="small-block vs the unperturbed large-block variant (nullity <= 8), one line, no bench line")
     ap.add_argument("--d-sweep", action="store_true",
                     help="block sizes 1, 2, 4, 8 at a fixed dim K (Sec. 5.3.1), one line, no bench line")
     ap.add_argument("--loop-sample", type=int, default=32,
@@ -689,6 +718,9 @@ def main():
         return
     if args.d_sweep:
         d_sweep(ns, h, w, p, args, local)
+        return
+    if args.large_block:
+        large_block(ns, h, w, p, args, local)
         return
 
     alu = alu_peaks(ns, local)

@@ -1213,10 +1213,15 @@ struct Solver {
     const double normB_est = std::min(normB, 1.1 * theta_max);
     u_d = ud_per_normB * normB_est;
     bd_tol = 100.0 * u_d;
+    // Ritz values counted as null (Remark cormain: below 3 eps); unperturbed (eps = 0, the
+    // large-block variant of Sec. 5.3.2) the null Ritz values sit at rounding level: reading L1
+    // counts theta <= tol ||B|| instead
+    const double small_lim = eps > 0.0 ? 3.0 * eps : tol_eff * normB_est;
+    auto small = [&](double th) { return eps > 0.0 ? th < small_lim : th <= small_lim; };
     std::vector<int> cand;
     int nsmall = 0;
     for (int i = 0; i < R; ++i) {
-      if (pin_theta[i] < 3.0 * eps) {
+      if (small(pin_theta[i])) {
         ++nsmall;
         if (pin_res[i] <= tol_eff * normB_est) cand.push_back(i);
       }
@@ -1266,7 +1271,7 @@ struct Solver {
     }
     {
       std::vector<int> sm, rest;
-      for (int i : avail) (pin_theta[i] < 3.0 * eps ? sm : rest).push_back(i);
+      for (int i : avail) (small(pin_theta[i]) ? sm : rest).push_back(i);
       std::stable_sort(sm.begin(), sm.end(), [&](int a, int b) { return pin_res[a] < pin_res[b]; });
       avail = sm;
       avail.insert(avail.end(), rest.begin(), rest.end());
@@ -1319,7 +1324,7 @@ struct Solver {
     // before the first lock there is no speed estimate: the smallest Ritz value must
     // also have converged at or above 3 eps (the direct test of Sec. 4.3)
     const bool settled =
-        !events.empty() || (pin_theta[0] >= 3.0 * eps && pin_res[0] <= tol_eff * normB_est);
+        !events.empty() || (!small(pin_theta[0]) && pin_res[0] <= tol_eff * normB_est);
     if (n_unl == 0 && nlocked_now == 0 && (double)since > o.stop_factor * sv && settled) return true;
     return false;
   }
