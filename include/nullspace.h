@@ -378,7 +378,9 @@ ns_status ns_restart_product(int64_t n, int d, int R, const double* Z, const dou
  * computes it, exposed so that it can be checked on its own.  Runs the first
  * Lanczos cycle of ns_solve on this handle (start block, steps 1 .. nb-1 with the
  * reorthogonalizations they trigger; no restart, no locking) with the same d,
- * restart_len and opts (eps, precision, reorth), and records every new W column.
+ * restart_len and opts (checked as ns_solve checks them; a preconditioner named in
+ * opts is built and its operator traced; checkpoint options are ignored), and
+ * records every new W column.
  *   W : (nb+1) x (nb+1) doubles, column-major, host memory, nb = restart_len / d.
  *       Entry (b, c), b < c, c >= 2, is w_{b,c} as the recurrence produced it,
  *       before the reset to u_d that a reorthogonalization makes; columns 0 and 1

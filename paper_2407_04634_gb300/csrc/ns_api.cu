@@ -2231,16 +2231,8 @@ static int block_size_rule(int restart_len) {
   return 1;
 }
 
-ns_status ns_solve(ns_handle* h, int d, int restart_len, double tol, const ns_opts* opts) {
-  if (!h) return NS_ERR_INVALID_ARG;
-  if (d == 0) d = block_size_rule(restart_len);
-  if (!(d == 1 || d == 2 || d == 4 || d == 8)) return set_err(h, NS_ERR_INVALID_ARG, "d must be 0, 1, 2, 4 or 8");
-  if (restart_len % d || restart_len < 3 * d || restart_len > 512)
-    return set_err(h, NS_ERR_INVALID_ARG, "restart_len must be a multiple of d in [3d, 512]");
-  if (!(tol > 0.0)) return set_err(h, NS_ERR_INVALID_ARG, "tol must be positive");
-  ns_opts o;
-  ns_default_opts(&o);
-  if (opts) o = *opts;
+// option checks shared by ns_solve and ns_trace_omega (everything the Solver reads)
+static ns_status validate_opts(ns_handle* h, const ns_opts& o, int restart_len) {
   if (!(o.eps >= 0.0) || o.stop_factor <= 0.0) return set_err(h, NS_ERR_INVALID_ARG, "bad opts");
   if (!(o.precision == NS_FP64 || o.precision == NS_MIXED) || !(o.fp64_products == 0 || o.fp64_products == 1))
     return set_err(h, NS_ERR_INVALID_ARG, "precision must be NS_FP64 or NS_MIXED; fp64_products 0 or 1");
@@ -2262,6 +2254,23 @@ ns_status ns_solve(ns_handle* h, int d, int restart_len, double tol, const ns_op
         (o.precond == 1 && !(o.precond_shift >= 0.0 && std::isfinite(o.precond_shift))))
       return set_err(h, NS_ERR_INVALID_ARG,
                      "precond: 0, 1 (outer, NS_MODE_SPD, precond_shift >= 0) or 2 (inner, NS_MODE_NORMAL)");
+  }
+  return NS_OK;
+}
+
+ns_status ns_solve(ns_handle* h, int d, int restart_len, double tol, const ns_opts* opts) {
+  if (!h) return NS_ERR_INVALID_ARG;
+  if (d == 0) d = block_size_rule(restart_len);
+  if (!(d == 1 || d == 2 || d == 4 || d == 8)) return set_err(h, NS_ERR_INVALID_ARG, "d must be 0, 1, 2, 4 or 8");
+  if (restart_len % d || restart_len < 3 * d || restart_len > 512)
+    return set_err(h, NS_ERR_INVALID_ARG, "restart_len must be a multiple of d in [3d, 512]");
+  if (!(tol > 0.0)) return set_err(h, NS_ERR_INVALID_ARG, "tol must be positive");
+  ns_opts o;
+  ns_default_opts(&o);
+  if (opts) o = *opts;
+  {
+    const ns_status vs = validate_opts(h, o, restart_len);
+    if (vs != NS_OK) return vs;
   }
   h->err.clear();
   h->solved = false;
@@ -2593,8 +2602,15 @@ ns_status ns_trace_omega(ns_handle* h, int d, int restart_len, const ns_opts* op
   ns_opts o;
   ns_default_opts(&o);
   if (opts) o = *opts;
-  if (!(o.eps >= 0.0)) return set_err(h, NS_ERR_INVALID_ARG, "bad opts");
+  {
+    const ns_status vs = validate_opts(h, o, restart_len);
+    if (vs != NS_OK) return vs;
+  }
+  o.checkpoint_every = 0;  // the first cycle only: no restart, nothing to save or resume
+  o.resume = 0;
   try {
+    if (o.precond == 1) build_precond(h, o.precond_shift);
+    if (o.precond == 2) build_inner(h);
     if (o.precision == NS_MIXED) {
       ensure_fp32(h);
       switch (d) {
