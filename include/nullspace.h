@@ -117,7 +117,9 @@ typedef struct {
                           against A.  NS_MODE_NORMAL only: 2 = inner preconditioning
                           (Sec. 4.4.1), B_L = A^T P_L^-1 A + eps D with P_L = diag(A A^T),
                           applied as the row scaling (S A)^T (S A), S = P_L^-1/2 (0 on a zero
-                          row); same null space, refinement against A.  0 = none (default) */
+                          row); same null space, refinement against S A.  0 = none
+                          (default).  With precond = 1 the post-processing projects in one
+                          pass against up to about 3,000 columns (larger N: NS_ERR_INVALID_ARG) */
   double precond_shift;/* diagonal compensation of the factor (Eq. defichol: 0.1, default) */
 } ns_opts;
 
@@ -483,7 +485,7 @@ ns_status ns_batch_create(ns_batch** out, int64_t count, const int64_t* n, const
  * and every n_i >= restart_len + 34 (the basis, its next vector and up to 32
  * locked vectors must fit); tol > 0 (lock when the Ritz residual is at most
  * max(tol, 1e-5) ||B_i||, FP32 vectors).  From opts (NULL = defaults) it reads
- * eps, max_matvec (<= 0: min(100 n_i + 50 restart_len, 1e6) per instance),
+ * eps (> 0: the null test is theta < 3 eps; no unperturbed variant here), max_matvec (<= 0: min(100 n_i + 50 restart_len, 1e6) per instance),
  * stop_factor, refine_tol (||A x|| <= refine_tol * ||A_i||_2), refine_maxit;
  * precision is ignored (the batched form is always the mixed one); use_graphs
  * >= 0 (default) replays the captured graph {queue reset, persistent launch},

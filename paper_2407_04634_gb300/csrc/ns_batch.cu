@@ -264,7 +264,8 @@ ns_status ns_batch_solve(ns_batch* h, int d, int restart_len, double tol, const 
   ns_opts o;
   ns_default_opts(&o);
   if (opts) o = *opts;
-  if (!(o.eps >= 0.0) || !(o.stop_factor > 0.0) || !(o.refine_tol > 0.0) || o.refine_maxit < 0)
+  // eps > 0: the batched kernel counts Ritz values below 3 eps as null (no unperturbed variant)
+  if (!(o.eps > 0.0) || !(o.stop_factor > 0.0) || !(o.refine_tol > 0.0) || o.refine_maxit < 0)
     return bset_err(h, NS_ERR_INVALID_ARG, "bad opts");
   if (!(o.batch_block == 0 || o.batch_block == 128 || o.batch_block == 256))
     return bset_err(h, NS_ERR_INVALID_ARG, "batch_block must be 0, 128 or 256");
