@@ -163,3 +163,34 @@ def test_inner_preconditioned_solve_on_badly_scaled_rows():
     assert principal_sine(pre.X, copy_pair_basis(3000, w.copy_pairs)) <= 1e-8
     plain = lanczos_nullspace(A, "normal", 2, 60, tol=1e-10, seed=9, max_matvec=10 * pre.stats["matvecs"])
     assert plain.N < 6
+
+
+@pytest.mark.parametrize("variant", ["outer", "inner"])
+def test_omega_bounds_hold_for_the_preconditioned_operators(variant):
+    """Sec. 4.2's W recurrence bounds the true ||Q_k^T Q_{l+1}|| for any symmetric
+    operator it is run on: every W entry of the (partially reorthogonalized) run still
+    dominates the true inner products, locked rows included, for B_R (outer, reading P2's
+    first-cycle bound) and for B_L (inner)."""
+    from workloads import rectangular_copies_scaled
+    worst = [0.0]
+    seen = [0]
+
+    def probe(j, Z, X, col, colX, dd):
+        Qn = Z[:, (j + 1) * dd:(j + 2) * dd]
+        for b in range(j + 1):
+            true = np.linalg.norm(Z[:, b * dd:(b + 1) * dd].T @ Qn, 2)
+            if col[b] < 1e-3:
+                worst[0] = max(worst[0], true / col[b])
+        if X.shape[1]:
+            worst[0] = max(worst[0], float(np.max(np.abs(X.T @ Qn).max(axis=1) / colX)))
+            seen[0] += 1
+
+    if variant == "outer":
+        w = laplacian_grid_components(3, 6, 8, 16)
+        r = lanczos_nullspace(w.A.to_scipy(), "spd", 1, 30, seed=9, probe=probe, refine=False, precond=0.1)
+    else:
+        w = rectangular_copies_scaled(5, 900, 600, 4, 3.0)
+        r = lanczos_nullspace(w.A.to_scipy(), "normal", 2, 60, seed=9, probe=probe, refine=False, inner=True)
+    assert r.N == w.nullity
+    assert seen[0] > 0
+    assert worst[0] <= 1.0, worst[0]
